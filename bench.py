@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark: zone-updates/s of the RK2 finite-volume step on the oblique
+3D Riemann problem at 256^3 (Sod states split by the plane normal to
+(1,1,1) through the cube centre, gamma 1.4, outflow, CFL 0.4).
+
+One step = ComputeTimeStep (CFL min-reduction, one 32-byte device-to-host
+read) + the full RK2 step (prim, three sweeps and a ghost fill per substep);
+one zone-update = one interior cell advanced by one step.  The timed region
+starts from the initial state already resident in HBM and covers K steps of
+the workload.  Prints one JSON line (rank 0).
+
+  python bench.py [--steps K] [--warmup W] [--precision fp64|fp64_fma]
+  python bench.py --impl reference      # the CPU oracle on a bounded sample
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "zone-updates/s per RK2 step at 256^3 (FP64 vs FP32) and % of HBM roofline"
+CFL = 0.4
+N = 256
+SM_COUNT = 152
+# FP64 issue rate measured on this GPU: 2 DFMA lane-operations per SM per
+# clock (598 G DFMA/s over 152 SMs at ~1.92 GHz); 2 flops per DFMA.
+DFMA_PER_SM_CLK = 2.0
+# Algorithmic FP64 flops of the method (divide and square root count one
+# each), from the operation counts of the definition:
+#   per face: two sides x (cons 11 + sound speed 3 + flux 6) + wave bounds 4
+#             + HLL denominator and product 3 + 5 components x 7 = 82
+#   per cell and axis: differences 5 + limited slopes 5x4 + face states 5x4
+#             + one face 82 = 127
+#   divergence: x 2, y 3, z 3 per component; z sweep adds dt* (1) and the
+#             RK combine (stage 1: 1 add, stage 2: 2 adds + 1 multiply).
+FLOPS_SWEEP = {"sweep_x": 127 + 5 * 2, "sweep_y": 127 + 5 * 3,
+               "sweep_z": 127 + 5 * 3 + 5 * 1 + 5 * 2}     # z: stage average of RK
+FLOPS_PRIM = 12          # per ghosted cell
+FLOPS_DT = 23            # per interior cell
+# Algorithmic HBM bytes per zone-update for a fused step with in-place
+# stage 2: stage 1 reads U^n, writes U^1 (80 B); stage 2 reads U^1, U^n and
+# writes U^{n+1} (120 B).
+BYTES_PER_ZONE_UPDATE = 200
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        sm, smax = [], None
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                smax = float(r[1])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if r[4 + k].lower() == "active":
+                    reasons.add(name)
+        loaded = [s for s in sm if smax and s > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _dist():
+    """(rank, world, local_rank) from torchrun's environment; init the group."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = os.environ.get("FV_BENCH_BACKEND", "nccl")
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x: float, world: int, device) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(seconds_target: float = 10.0):
+    """The oracle as it stands, single-threaded, on a bounded sample of the
+    workload: a 256 x 256 x S slab of the oblique problem through its
+    centre (outflow at the cut), timed over whole RK2 steps."""
+    import numpy as np
+
+    import oracle
+    from paper_1812_07977_gb300 import problems
+
+    S = 8
+    U = problems.riemann_oblique(N, N, N)[:, N // 2 - S // 2:N // 2 + S // 2]
+    m = oracle.mesh(N, N, S, lz=S / N)
+    Ug = oracle.ghosted_from_interior(m, np.ascontiguousarray(U))
+    cells = N * N * S
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        dt, _, _ = oracle.reduce_dt(m, Ug, CFL)
+        oracle.step(m, Ug, dt)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_target or steps >= 50:
+            break
+    return {"value": cells * steps / el, "unit": "zone-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} RK2 steps (with ComputeTimeStep) of a 256x256x{S} slab through "
+                      f"the centre of the 256^3 oblique problem, one thread, {el:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on the arm's workload, each step a
+    bounded sample (a 256 x 256 x 4 slab of the same mesh)."""
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    from paper_1812_07977_gb300 import problems
+
+    S = 4
+    U = problems.riemann_oblique(N, N, N)[:, N // 2 - S // 2:N // 2 + S // 2]
+    m = oracle.mesh(N, N, S, lz=S / N)
+    Ug = oracle.ghosted_from_interior(m, np.ascontiguousarray(U))
+    for _ in range(args.warmup):
+        dt, _, _ = oracle.reduce_dt(m, Ug, CFL)
+        oracle.step(m, Ug, dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        dt, _, _ = oracle.reduce_dt(m, Ug, CFL)
+        oracle.step(m, Ug, dt)
+    el = time.perf_counter() - t0
+    cells = N * N * S
+    value = cells * args.steps / el
+    sample = f"each step: one RK2 step of a 256x256x{S} slab of the 256^3 oblique problem"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "zone-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "oblique Riemann 256^3 (sampled slab)", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "zone-updates/s", "cores": 1,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "zone-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1812_07977_gb300 import problems
+    from paper_1812_07977_gb300.fv import Mesh
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    zones = n ** 3
+    U0 = problems.riemann_oblique(n, n, n)
+    U0_dev = torch.from_numpy(U0).to(dev)
+    m = Mesh(n, n, n, precision=args.precision)
+
+    def step():
+        dt = m.reduce_dt(CFL)
+        m.step(dt)
+
+    # warm-up, then restart the workload from its initial state
+    m.set_state(U0_dev)
+    for _ in range(args.warmup):
+        step()
+    m.set_state(U0_dev)
+    torch.cuda.synchronize()
+    m.profile(True)
+    m.read_profile()
+
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+    _barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        step()
+    ev1.record()
+    torch.cuda.synchronize()
+    _barrier(world)
+    clocks = sampler.stop() if rank == 0 else None
+    ms = ev0.elapsed_time(ev1)
+    prof = m.read_profile()
+    m.profile(False)
+    ms_max = _max_over_ranks(ms, world, dev)
+    value = world * zones * args.steps / (ms_max / 1e3)
+
+    # end to end through the public API with host buffers: each step copies
+    # the state in from pinned host memory and the result back out
+    host = torch.from_numpy(U0.copy()).pin_memory()
+    m.set_state(host)
+    step()
+    m.get_state(host)
+    host.copy_(torch.from_numpy(U0))
+    _barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        m.set_state(host)
+        step()
+        m.get_state(host)
+    torch.cuda.synchronize()
+    e2e_s = _max_over_ranks(time.perf_counter() - t0, world, dev)
+    state_bytes = 5 * zones * 8
+    e2e = {"value": world * zones * args.e2e_steps / e2e_s, "unit": "zone-updates/s",
+           "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes + 32,
+           "steps": args.e2e_steps}
+    m.close()
+
+    if rank != 0:
+        return 0
+
+    # roofline of the dominant kernel class (the three sweeps)
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp64_peak = DFMA_PER_SM_CLK * 2.0 * SM_COUNT * sm_max * 1e6 / 1e12        # TFLOP/s
+    sweep_ms = sum(prof[c][0] for c in FLOPS_SWEEP)
+    sweep_launches = sum(prof[c][1] for c in FLOPS_SWEEP)
+    sweep_flops = sum(FLOPS_SWEEP[c] * zones * prof[c][1] for c in FLOPS_SWEEP)
+    achieved = sweep_flops / (sweep_ms / 1e3) / 1e12 if sweep_ms > 0 else None
+    roofline = {"bound": "alu", "kernel": "k_sweep (x, y, z)", "achieved": achieved,
+                "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak if achieved else None, "traffic": args.traffic,
+                "peak_source": "FP64 issue rate 2 DFMA/SM/clk (measured) x 152 SMs x "
+                               f"{sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz), of measured",
+                "flops_per_launch": sweep_flops / max(sweep_launches, 1),
+                "avg_launch_ms": sweep_ms / max(sweep_launches, 1)}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_achieved = BYTES_PER_ZONE_UPDATE * zones * args.steps / (ms / 1e3) / 1e9
+    launches = sum(v[1] for v in prof.values())
+    total_flops_step = (sum(FLOPS_SWEEP.values()) * 2 + FLOPS_DT) * zones + \
+        2 * FLOPS_PRIM * (n + 4) ** 3
+    line = {
+        "metric": METRIC, "value": value, "unit": "zone-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "oblique Riemann problem 256^3 (Sod states, plane normal "
+                               "(1,1,1), gamma 1.4, outflow, CFL 0.4), steps 1..K",
+                   "precision": args.precision, "cells": zones,
+                   "l2": "inputs larger than L2 (0.70 GB per ghosted state, 2.8 GB resident)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "hbm_roofline": {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": hbm_achieved / hbm,
+                         "bytes_per_zone_update": BYTES_PER_ZONE_UPDATE,
+                         "note": "whole step vs the algorithmic minimum traffic, of measured"},
+        "fp64_flop_rate_whole_step_tflops": total_flops_step * args.steps / (ms / 1e3) / 1e12,
+        "kernel_ms_per_step": {c: v[0] / args.steps for c, v in prof.items()},
+        "gpu_launches": launches,
+        "e2e": e2e,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp64_fma"])
+    ap.add_argument("--n", type=int, default=N)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per sweep launch from an ncu capture of this kernel")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

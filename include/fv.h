@@ -1,0 +1,190 @@
+/*
+ * fv.h -- C ABI of the GB300 finite-volume Euler step.
+ *
+ * One explicit second-order Runge-Kutta step of the 3D ideal-gas Euler
+ * equations on a uniform Cartesian mesh with two ghost layers, as in the
+ * RiemannProblem of Budiardja & Cardall, "Targeting GPUs with OpenMP
+ * Directives on Summit" (Sec. 3, Algorithm 1 "Fluid Evolution" and
+ * Algorithm 2 "Fluid Evolution with Accelerator").  Every stage runs in this
+ * library's own CUDA kernels for sm_103a on one GPU; there is no CPU path.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * State layout (the paper's StorageForm column remapped to rank 3 with two
+ * ghost layers, Sec. 3): five conserved fields q = 0..4 = (rho, rho*vx,
+ * rho*vy, rho*vz, E), each stored contiguously (structure of arrays).  The
+ * caller exchanges INTERIOR states only: a dense array of 5*nz*ny*nx doubles
+ * indexed [q][k][j][i] with i (x) fastest.  The ghost cells are owned by the
+ * library.
+ *
+ * Ownership: the library allocates and frees all device memory of a mesh.
+ * The caller owns every buffer it passes (host or device pointer) and keeps
+ * it valid for the duration of the call.
+ *
+ * Streams: all work of a mesh is enqueued on the CUDA stream given at
+ * creation (NULL = the legacy default stream), on the device that was
+ * current at creation.  Calls marked "asynchronous" return once the work is
+ * enqueued; calls marked "synchronising" wait for the stream.
+ *
+ * Errors: every call returns an fv_status.  FV_OK on success; on failure a
+ * human-readable detail is available from fv_last_error() on the same host
+ * thread.  Device-side conditions found while computing (a cell average with
+ * rho <= 0, p <= 0 or NaN) are latched on the device and reported as
+ * FV_ERR_NONPHYSICAL by the next synchronising call.  A handle is unusable
+ * after fv_destroy_mesh; passing it again gives FV_ERR_BAD_HANDLE.
+ * Calls on one mesh must not be made concurrently from several host threads.
+ */
+#ifndef FV_H
+#define FV_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define FV_API __attribute__((visibility("default")))
+#else
+#define FV_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fv_mesh_s* fv_mesh_t;
+
+typedef enum {
+  FV_OK = 0,
+  FV_ERR_INVALID_ARG = 1,   /* bad size, pointer, enum value or call order */
+  FV_ERR_OOM = 2,           /* device or pinned host allocation failed */
+  FV_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed */
+  FV_ERR_NONPHYSICAL = 4,   /* a cell average had rho <= 0, p <= 0 or NaN */
+  FV_ERR_TIMEOUT = 5,       /* reserved: a bounded device wait gave up */
+  FV_ERR_BAD_HANDLE = 6     /* NULL, destroyed or foreign mesh handle */
+} fv_status;
+
+typedef enum { FV_BC_OUTFLOW = 0, FV_BC_PERIODIC = 1 } fv_bc;
+
+/* Arithmetic of the step.
+ *  FV_PREC_FP64      FP64, every operation rounded separately in the order
+ *                    of the method's definition (no fused multiply-add):
+ *                    bitwise reproducible against a plain IEEE FP64 code.
+ *  FV_PREC_FP64_FMA  FP64 with fused multiply-add contraction: the same
+ *                    method, a few ulp per operation away from FV_PREC_FP64.
+ */
+typedef enum { FV_PREC_FP64 = 0, FV_PREC_FP64_FMA = 1 } fv_precision;
+
+typedef struct {
+  int nx, ny, nz;       /* interior cells per axis, each >= 1 */
+  double lx, ly, lz;    /* domain extents (> 0); origin at 0; dx = lx / nx */
+  double gamma;         /* ideal-gas ratio of specific heats, > 1 */
+  double theta;         /* limiter: 0 first order, 1 minmod, 2 monotonised
+                           central; any value in [0, 2] */
+  int bc[3];            /* fv_bc per axis x, y, z */
+  int precision;        /* fv_precision */
+} fv_mesh_desc;
+
+/* Allocate a mesh and its device state (Sec. 2.1: StorageForm's
+ * AllocateDevice; the persistent device copy of FluidCurrent and the work
+ * storage initialised by Algorithm 2).  `cuda_stream` is a cudaStream_t (NULL =
+ * default stream).  The state is zero until fv_set_state.  Synchronous.
+ * Errors: INVALID_ARG (desc out of range, out == NULL), OOM, CUDA. */
+FV_API fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream,
+                         fv_mesh_t* out);
+
+/* Free all memory of the mesh after its stream has drained.  NULL is
+ * accepted and ignored.  Errors: BAD_HANDLE. */
+FV_API fv_status fv_destroy_mesh(fv_mesh_t m);
+
+/* Copy an interior conserved state in and fill the ghost layers (Sec. 2.1
+ * UpdateDevice, then the initial GhostExchange of Algorithm 1).  `U` holds
+ * 5*nz*ny*nx doubles [q][k][j][i]; on_device != 0 means a device pointer on
+ * the mesh's device, else a host pointer (pinned host memory is fastest).
+ * Clears the latched non-physical counters and any pending RK stage.
+ * Synchronising for host pointers, asynchronous for device pointers. */
+FV_API fv_status fv_set_state(fv_mesh_t m, const double* U, int on_device);
+
+/* Copy the current interior state out (Sec. 2.1 UpdateHost); same layout
+ * as fv_set_state.  Between fv_substep(1) and fv_substep(2) the current
+ * state is the first RK stage.  Synchronising.  Errors: NONPHYSICAL if a
+ * non-physical cell was latched since the last fv_set_state. */
+FV_API fv_status fv_get_state(fv_mesh_t m, double* U, int on_device);
+
+/* Copy the full ghosted state out: 5 * (nz+4)*(ny+4)*(nx+4) doubles
+ * [q][k+2][j+2][i+2].  Synchronising. */
+FV_API fv_status fv_get_ghosted_state(fv_mesh_t m, double* U, int on_device);
+
+/* ComputeTimeStep (Algorithm 1): *dt_out = cfl / max over interior
+ * cells of sum_d (|v_d| + c) / dx_d with c = sqrt(gamma p / rho).  The
+ * maximum is exact (order-free).  Only valid at a step boundary.
+ * Synchronising (one 24-byte device-to-host read).  Errors: INVALID_ARG
+ * (cfl <= 0, dt_out NULL, stage pending), NONPHYSICAL. */
+FV_API fv_status fv_reduce_dt(fv_mesh_t m, double cfl, double* dt_out);
+
+/* One RK2 step (the loop body of Algorithm 1): FluidOld = FluidCurrent;
+ * substep 1 FluidCurrent = FluidOld + dt L(FluidOld); GhostExchange;
+ * substep 2 FluidCurrent = 0.5 (FluidOld + FluidCurrent + dt L(FluidCurrent));
+ * GhostExchange.  L is the flux divergence of primitive-variable
+ * slope-limited reconstruction with HLL face fluxes.  The caller picks dt
+ * (normally from fv_reduce_dt, clamped to the end time).  Asynchronous.
+ * Errors: INVALID_ARG (dt not finite or < 0, stage pending), CUDA. */
+FV_API fv_status fv_step(fv_mesh_t m, double dt);
+
+/* Half of fv_step: stage 1 (requires a step boundary) or stage 2 (requires
+ * stage 1 done).  fv_substep(m,1,dt); fv_substep(m,2,dt) == fv_step(m,dt).
+ * Asynchronous. */
+FV_API fv_status fv_substep(fv_mesh_t m, int stage, double dt);
+
+/* GhostExchange alone (Algorithm 1) on the current state:
+ * each ghost cell takes the value of its source cell, axis by axis x, y, z
+ * (outflow: nearest interior cell; periodic: index modulo n).  The step
+ * already does this; exposed for tests and custom loops.  Asynchronous. */
+FV_API fv_status fv_fill_ghosts(fv_mesh_t m);
+
+/* Per-field sum over interior cells times the cell volume (dx*dy)*dz, by a
+ * fixed pairwise tree (values in (k, j, i) order, zero-padded to a power of
+ * two, neighbours added level by level): bitwise reproducible.
+ * out[5].  Synchronising. */
+FV_API fv_status fv_conserved_sums(fv_mesh_t m, double out[5]);
+
+/* Counters latched since the last fv_set_state: interior cells found
+ * non-physical, and faces whose reconstructed state had rho <= 0 or p <= 0
+ * and fell back to first order.  Either pointer may be NULL.
+ * Synchronising. */
+FV_API fv_status fv_get_counters(fv_mesh_t m, long long* nonphysical_cells,
+                          long long* fallback_faces);
+
+/* Kernel classes of the profiling hooks below. */
+typedef enum {
+  FV_KERNEL_PRIM = 0,     /* conserved -> primitive */
+  FV_KERNEL_SWEEP_X = 1,  /* differences, reconstruction, HLL fluxes, update: x */
+  FV_KERNEL_SWEEP_Y = 2,  /* the same along y */
+  FV_KERNEL_SWEEP_Z = 3,  /* the same along z, with the RK combine */
+  FV_KERNEL_GHOST = 4,    /* ghost fill */
+  FV_KERNEL_DT = 5,       /* CFL time-step reduction */
+  FV_KERNEL_OTHER = 6,    /* state copies and conservation sums */
+  FV_KERNEL_NCLASS = 7
+} fv_kernel_class;
+
+/* Per-kernel timing on (on != 0) or off.  While on, every kernel launch of
+ * the mesh is bracketed by two CUDA events recorded on the mesh's stream;
+ * this adds no synchronisation.  Not part of the paper: measurement support
+ * (the role of its TimerForm instrumentation, Sec. 4). */
+FV_API fv_status fv_profile_enable(fv_mesh_t m, int on);
+
+/* Read and reset the profile: ms[c] = device milliseconds spent in kernels
+ * of class c since the last read (timed launches only), launches[c] = number
+ * of kernel launches of class c (always counted).  Arrays of
+ * FV_KERNEL_NCLASS entries; either may be NULL.  Synchronising. */
+FV_API fv_status fv_profile_read(fv_mesh_t m, double* ms, long long* launches);
+
+/* Mesh facts: interior sizes and the byte size of one device state. */
+FV_API fv_status fv_mesh_info(fv_mesh_t m, int dims[3], size_t* state_bytes);
+
+FV_API const char* fv_status_string(fv_status s);
+
+/* Detail of the last failed call on this host thread ("" if none). */
+FV_API const char* fv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

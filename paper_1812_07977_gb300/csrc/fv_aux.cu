@@ -1,0 +1,267 @@
+// fv_aux.cu -- ghost fill (GhostExchange), CFL time step (ComputeTimeStep),
+// conservation sums, and the interior <-> ghosted copies of set/get state.
+// Built without FMA contraction: the time step's arithmetic is the method's
+// definition operation by operation.
+#include "fv_device.cuh"
+#include "fv_internal.h"
+
+using namespace fvd;
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxBlocks = 152 * 8;
+
+inline unsigned grid_for(long long n) {
+  long long b = (n + kThreads - 1) / kThreads;
+  if (b < 1) b = 1;
+  return (unsigned)(b < kMaxBlocks ? b : kMaxBlocks);
+}
+
+// ---------------------------------------------------------------- ghosts
+// The axis-by-axis fill (x, then y, then z, each over the full ghosted
+// extent of the other axes) leaves every ghost cell equal to the interior
+// cell (src_x(i), src_y(j), src_z(k)), so each ring cell is written once,
+// straight from its source.  Ring cells are enumerated as the z slabs
+// (4 full planes), the y slabs of the interior planes, and the x slabs of
+// the interior rows.
+__global__ void __launch_bounds__(kThreads)
+k_fill_ghosts(double* __restrict__ U, Params P) {
+  const long long X = P.nx + 4, Y = P.ny + 4;
+  const long long nz_slab = 4 * Y * X;
+  const long long ny_slab = 4 * (long long)P.nz * X;
+  const long long nx_slab = 4 * (long long)P.nz * P.ny;
+  const long long total = nz_slab + ny_slab + nx_slab;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    if (t < nz_slab) {
+      const long long s = t / (Y * X), r = t - s * (Y * X);
+      k = s < 2 ? (int)s - 2 : P.nz + (int)s - 2;
+      j = (int)(r / X) - 2;
+      i = (int)(r % X) - 2;
+    } else if (t < nz_slab + ny_slab) {
+      const long long u = t - nz_slab;
+      const long long kk = u / (4 * X), r = u - kk * (4 * X);
+      const int s = (int)(r / X);
+      k = (int)kk;
+      j = s < 2 ? s - 2 : P.ny + s - 2;
+      i = (int)(r % X) - 2;
+    } else {
+      const long long u = t - nz_slab - ny_slab;
+      const long long row = u / 4;
+      const int s = (int)(u - row * 4);
+      k = (int)(row / P.ny);
+      j = (int)(row % P.ny);
+      i = s < 2 ? s - 2 : P.nx + s - 2;
+    }
+    const int si = ghost_source(i, P.nx, P.bc[0]);
+    const int sj = ghost_source(j, P.ny, P.bc[1]);
+    const int sk = ghost_source(k, P.nz, P.bc[2]);
+    const long long dst = (k + 2) * P.sz + (j + 2) * P.sy + (i + 2);
+    const long long src = (sk + 2) * P.sz + (sj + 2) * P.sy + (si + 2);
+#pragma unroll
+    for (int q = 0; q < NF; ++q) U[q * P.nfield + dst] = U[q * P.nfield + src];
+  }
+}
+
+// ---------------------------------------------------------------- time step
+// s = ((|vx|+c)/dx + (|vy|+c)/dy) + (|vz|+c)/dz per interior cell; the
+// maximum over cells is exact in any order.  Non-negative doubles order
+// like their bit patterns, so the grid-wide maximum is an integer atomicMax.
+// A NaN s never wins, as in a plain `if (s > smax)` loop.
+__global__ void __launch_bounds__(kThreads)
+k_reduce_dt(const double* __restrict__ U, Params P, DevCounters* ctr) {
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  double smax = 0.0;
+  unsigned long long bad = 0;
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < n;
+       m += (long long)gridDim.x * blockDim.x) {
+    const long long k = m / ((long long)P.nx * P.ny);
+    const long long r = m - k * ((long long)P.nx * P.ny);
+    const long long j = r / P.nx, i = r - j * P.nx;
+    const long long g = (k + 2) * P.sz + (j + 2) * P.sy + (i + 2);
+    double u[NF];
+#pragma unroll
+    for (int q = 0; q < NF; ++q) u[q] = U[q * P.nfield + g];
+    const Prim w = cons_to_prim(u, P);
+    if (!(is_pos(w.r) && is_pos(w.p))) ++bad;
+    const double c = sqrt(P.gamma * w.p / w.r);
+    const double s = ((fabs(w.vx) + c) * P.inv_d[0] + (fabs(w.vy) + c) * P.inv_d[1]) +
+                     (fabs(w.vz) + c) * P.inv_d[2];
+    if (s > smax) smax = s;
+  }
+  unsigned long long sb = (unsigned long long)__double_as_longlong(smax);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, sb, o);
+    sb = v > sb ? v : sb;
+  }
+  __shared__ unsigned long long warp_max[kThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) warp_max[wid] = sb;
+  if (bad) atomicAdd(&ctr->np_dt, bad);
+  __syncthreads();
+  if (wid == 0) {
+    sb = lane < kThreads / 32 ? warp_max[lane] : 0ULL;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, sb, o);
+      sb = v > sb ? v : sb;
+    }
+    if (lane == 0) atomicMax(&ctr->smax_bits, sb);
+  }
+}
+
+// ---------------------------------------------------------------- copies
+__global__ void __launch_bounds__(kThreads)
+k_scatter(const double* __restrict__ dense, double* __restrict__ U, Params P) {
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < NF * n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long q = t / n, m = t - q * n;
+    const long long k = m / ((long long)P.nx * P.ny);
+    const long long r = m - k * ((long long)P.nx * P.ny);
+    const long long j = r / P.nx, i = r - j * P.nx;
+    U[q * P.nfield + (k + 2) * P.sz + (j + 2) * P.sy + (i + 2)] = dense[t];
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_gather(const double* __restrict__ U, double* __restrict__ dense, Params P) {
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < NF * n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long q = t / n, m = t - q * n;
+    const long long k = m / ((long long)P.nx * P.ny);
+    const long long r = m - k * ((long long)P.nx * P.ny);
+    const long long j = r / P.nx, i = r - j * P.nx;
+    dense[t] = U[q * P.nfield + (k + 2) * P.sz + (j + 2) * P.sy + (i + 2)];
+  }
+}
+
+// ---------------------------------------------------------------- sums
+// Fixed pairwise tree over the interior values of each field in (k, j, i)
+// order, zero-padded to a power of two P2: level by level a[m] = a[2m] +
+// a[2m+1].  A block reduces an aligned chunk of kChunk = 2 * kThreads
+// values to one partial -- exactly the tree's level log2(kChunk) node -- and
+// further passes reduce the partials the same way, so the result equals the
+// whole tree's root bit for bit.
+constexpr int kChunk = 2 * kThreads;
+
+__device__ __forceinline__ void block_tree(double* s, int tid) {
+  // s holds kThreads level-1 values; finish the tree in shared memory
+  for (int len = kThreads; len > 1; len >>= 1) {
+    __syncthreads();
+    double v = 0.0;
+    if (tid < len / 2) v = s[2 * tid] + s[2 * tid + 1];
+    __syncthreads();
+    if (tid < len / 2) s[tid] = v;
+  }
+  __syncthreads();
+}
+
+// First pass: values straight from the ghosted state; grid = (chunks, 5).
+__global__ void __launch_bounds__(kThreads)
+k_sum_state(const double* __restrict__ U, Params P, long long padded, double* __restrict__ out,
+            long long out_stride) {
+  __shared__ double s[kThreads];
+  const int q = blockIdx.y, tid = threadIdx.x;
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  const long long base = (long long)blockIdx.x * kChunk + 2 * tid;
+  double v[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const long long m = base + e;
+    v[e] = 0.0;
+    if (m < n) {
+      const long long k = m / ((long long)P.nx * P.ny);
+      const long long r = m - k * ((long long)P.nx * P.ny);
+      const long long j = r / P.nx, i = r - j * P.nx;
+      v[e] = U[q * P.nfield + (k + 2) * P.sz + (j + 2) * P.sy + (i + 2)];
+    }
+  }
+  s[tid] = v[0] + v[1];
+  block_tree(s, tid);
+  if (tid == 0) out[q * out_stride + blockIdx.x] = s[0];
+  (void)padded;
+}
+
+// Later passes: `count` values per field (a power of two, or fewer than
+// kChunk padded with zeros) -> count / kChunk partials per field.
+__global__ void __launch_bounds__(kThreads)
+k_sum_partials(const double* __restrict__ in, long long count, long long in_stride,
+               double* __restrict__ out, long long out_stride) {
+  __shared__ double s[kThreads];
+  const int q = blockIdx.y, tid = threadIdx.x;
+  const long long base = (long long)blockIdx.x * kChunk + 2 * tid;
+  const double a = base < count ? in[q * in_stride + base] : 0.0;
+  const double b = base + 1 < count ? in[q * in_stride + base + 1] : 0.0;
+  s[tid] = a + b;
+  block_tree(s, tid);
+  if (tid == 0) out[q * out_stride + blockIdx.x] = s[0];
+}
+
+long long next_pow2(long long n) {
+  long long p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+cudaError_t launch_fill_ghosts(double* U, const Params& P, cudaStream_t s) {
+  const long long X = P.nx + 4, Y = P.ny + 4;
+  const long long total = 4 * Y * X + 4 * (long long)P.nz * X + 4 * (long long)P.nz * P.ny;
+  k_fill_ghosts<<<grid_for(total), kThreads, 0, s>>>(U, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_dt(const double* U, const Params& P, DevCounters* ctr, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(&ctr->smax_bits, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_reduce_dt<<<grid_for((long long)P.nx * P.ny * P.nz), kThreads, 0, s>>>(U, P, ctr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_interior(const double* dense, double* U, const Params& P,
+                                    cudaStream_t s) {
+  k_scatter<<<grid_for(NF * (long long)P.nx * P.ny * P.nz), kThreads, 0, s>>>(dense, U, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_interior(const double* U, double* dense, const Params& P,
+                                   cudaStream_t s) {
+  k_gather<<<grid_for(NF * (long long)P.nx * P.ny * P.nz), kThreads, 0, s>>>(U, dense, P);
+  return cudaGetLastError();
+}
+
+size_t sums_work_doubles(const Params& P) {
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  const long long chunks = (next_pow2(n) + kChunk - 1) / kChunk;
+  return (size_t)(2 * NF * chunks + NF);
+}
+
+cudaError_t launch_pairwise_sums(const double* U, const Params& P, double* work, double* out5,
+                                 cudaStream_t s) {
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  const long long padded = next_pow2(n);
+  long long count = (padded + kChunk - 1) / kChunk;  // partials after pass 1
+  const long long stride = count;
+  double* a = work;
+  double* b = work + NF * stride;
+  // pass 1 over the padded range: blocks beyond n read zeros only
+  k_sum_state<<<dim3((unsigned)count, NF), kThreads, 0, s>>>(U, P, padded, count == 1 ? out5 : a,
+                                                             count == 1 ? 1 : stride);
+  while (count > 1) {
+    const long long next = (count + kChunk - 1) / kChunk;
+    k_sum_partials<<<dim3((unsigned)next, NF), kThreads, 0, s>>>(a, count, stride,
+                                                                 next == 1 ? out5 : b,
+                                                                 next == 1 ? 1 : stride);
+    double* t = a;
+    a = b;
+    b = t;
+    count = next;
+  }
+  return cudaGetLastError();
+}

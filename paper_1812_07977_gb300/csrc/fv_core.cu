@@ -1,0 +1,535 @@
+// fv_core.cu -- the C ABI of include/fv.h: mesh handles, validation, buffer
+// ownership, stream ordering and error reporting.  All arithmetic runs in the
+// kernels of fv_step_kernels.cu and fv_aux.cu.
+#include "fv.h"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <unordered_set>
+#include <vector>
+
+#include "fv_internal.h"
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
+  va_end(ap);
+}
+
+std::mutex g_registry_mutex;
+std::unordered_set<const void*> g_registry;  // live mesh handles
+
+}  // namespace
+
+struct fv_mesh_s {
+  fv_mesh_desc desc;
+  fvd::Params P;
+  cudaStream_t stream;
+  int device;
+  size_t state_doubles;     // 5 * nfield
+  size_t dense_doubles;     // 5 * nx * ny * nz
+  StepBuffers buf;
+  double* sums_work;        // pairwise-sum partials
+  double* sums_out;         // 5 device doubles
+  DevCounters* host_ctr;    // pinned mirror of the device counters
+  double* host_sums;        // pinned, 5 doubles
+  int stage_pending;        // 1 after fv_substep(1) until fv_substep(2)
+  // profiling
+  bool prof_on;
+  std::vector<cudaEvent_t> event_pool;
+  struct Timed { int cls; cudaEvent_t a, b; };
+  std::vector<Timed> pending;
+  long long launches[FV_KERNEL_NCLASS];
+};
+
+namespace {
+
+// Makes the mesh's device current for the scope of one call.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+fv_status cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return FV_ERR_CUDA;
+}
+
+fv_status check_handle(fv_mesh_t m) {
+  if (!m) {
+    set_error("NULL mesh handle");
+    return FV_ERR_BAD_HANDLE;
+  }
+  std::lock_guard<std::mutex> lk(g_registry_mutex);
+  if (!g_registry.count(m)) {
+    set_error("mesh handle %p is not live (destroyed or foreign)", (void*)m);
+    return FV_ERR_BAD_HANDLE;
+  }
+  return FV_OK;
+}
+
+fv_status validate_desc(const fv_mesh_desc* d) {
+  if (!d) {
+    set_error("desc is NULL");
+    return FV_ERR_INVALID_ARG;
+  }
+  const int n[3] = {d->nx, d->ny, d->nz};
+  const double l[3] = {d->lx, d->ly, d->lz};
+  for (int a = 0; a < 3; ++a) {
+    if (n[a] < 1 || n[a] > (1 << 14)) {
+      set_error("cell count %d on axis %d outside [1, 16384]", n[a], a);
+      return FV_ERR_INVALID_ARG;
+    }
+    if (!(l[a] > 0.0) || !std::isfinite(l[a])) {
+      set_error("extent %g on axis %d must be finite and > 0", l[a], a);
+      return FV_ERR_INVALID_ARG;
+    }
+    if (d->bc[a] != FV_BC_OUTFLOW && d->bc[a] != FV_BC_PERIODIC) {
+      set_error("boundary condition %d on axis %d unknown", d->bc[a], a);
+      return FV_ERR_INVALID_ARG;
+    }
+  }
+  const long long cells = (long long)(d->nx + 4) * (d->ny + 4) * (d->nz + 4);
+  if (cells > (1LL << 31)) {
+    set_error("mesh of %lld ghosted cells exceeds the 2^31 limit", cells);
+    return FV_ERR_INVALID_ARG;
+  }
+  if (!(d->gamma > 1.0) || !std::isfinite(d->gamma)) {
+    set_error("gamma %g must be finite and > 1", d->gamma);
+    return FV_ERR_INVALID_ARG;
+  }
+  if (!(d->theta >= 0.0 && d->theta <= 2.0)) {
+    set_error("theta %g outside [0, 2]", d->theta);
+    return FV_ERR_INVALID_ARG;
+  }
+  if (d->precision != FV_PREC_FP64 && d->precision != FV_PREC_FP64_FMA) {
+    set_error("precision %d unknown", d->precision);
+    return FV_ERR_INVALID_ARG;
+  }
+  return FV_OK;
+}
+
+fvd::Params make_params(const fv_mesh_desc* d) {
+  fvd::Params P;
+  P.nx = d->nx;
+  P.ny = d->ny;
+  P.nz = d->nz;
+  P.sy = d->nx + 4;
+  P.sz = (long long)(d->nx + 4) * (d->ny + 4);
+  P.nfield = P.sz * (d->nz + 4);
+  P.gamma = d->gamma;
+  P.gm1 = d->gamma - 1.0;
+  P.igm1 = 1.0 / (d->gamma - 1.0);
+  P.theta = d->theta;
+  // cell widths and their inverses exactly as the method defines them
+  const double dx = d->lx / d->nx, dy = d->ly / d->ny, dz = d->lz / d->nz;
+  P.inv_d[0] = 1.0 / dx;
+  P.inv_d[1] = 1.0 / dy;
+  P.inv_d[2] = 1.0 / dz;
+  for (int a = 0; a < 3; ++a) P.bc[a] = d->bc[a];
+  return P;
+}
+
+void free_mesh(fv_mesh_s* m) {
+  for (auto& t : m->pending) {
+    m->event_pool.push_back(t.a);
+    m->event_pool.push_back(t.b);
+  }
+  for (cudaEvent_t e : m->event_pool) cudaEventDestroy(e);
+  cudaFree(m->buf.U);
+  cudaFree(m->buf.U1);
+  cudaFree(m->buf.W);
+  cudaFree(m->buf.ACC);
+  cudaFree(m->buf.ctr);
+  cudaFree(m->sums_work);
+  cudaFree(m->sums_out);
+  cudaFreeHost(m->host_ctr);
+  cudaFreeHost(m->host_sums);
+  delete m;
+}
+
+// Reads the device counters (and the dt maximum) into host_ctr; syncs.
+fv_status read_counters(fv_mesh_t m) {
+  cudaError_t e = cudaMemcpyAsync(m->host_ctr, m->buf.ctr, sizeof(DevCounters),
+                                  cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reading device counters");
+  return FV_OK;
+}
+
+fv_status nonphysical_status(fv_mesh_t m) {
+  if (m->host_ctr->np_step || m->host_ctr->np_dt) {
+    set_error("non-physical state: %llu cell detections in the step, %llu in the time step",
+              m->host_ctr->np_step, m->host_ctr->np_dt);
+    return FV_ERR_NONPHYSICAL;
+  }
+  return FV_OK;
+}
+
+cudaEvent_t take_event(fv_mesh_t m) {
+  if (!m->event_pool.empty()) {
+    cudaEvent_t e = m->event_pool.back();
+    m->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Launches one kernel (or a short fixed sequence) of class `cls`, counting
+// it and, while profiling is on, bracketing it with events on the stream.
+template <class F>
+cudaError_t timed(fv_mesh_t m, int cls, int nlaunch, F&& launch) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (m->prof_on) {
+    a = take_event(m);
+    b = take_event(m);
+    if (a && b) cudaEventRecord(a, m->stream);
+  }
+  cudaError_t e = launch();
+  m->launches[cls] += nlaunch;
+  if (m->prof_on && a && b) {
+    cudaEventRecord(b, m->stream);
+    m->pending.push_back({cls, a, b});
+  } else {
+    if (a) m->event_pool.push_back(a);
+    if (b) m->event_pool.push_back(b);
+  }
+  return e;
+}
+
+cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
+  const bool fma = m->desc.precision == FV_PREC_FP64_FMA;
+  const double* src = stage == 1 ? m->buf.U : m->buf.U1;
+  cudaError_t e = timed(m, FV_KERNEL_PRIM, 1, [&] {
+    return fma ? fv_fp64_fma::launch_prim(src, m->buf, m->P, m->stream)
+               : fv_fp64_exact::launch_prim(src, m->buf, m->P, m->stream);
+  });
+  for (int axis = 0; axis < 3 && e == cudaSuccess; ++axis) {
+    e = timed(m, FV_KERNEL_SWEEP_X + axis, 1, [&] {
+      return fma ? fv_fp64_fma::launch_sweep(axis, stage, m->buf, m->P, dt, m->stream)
+                 : fv_fp64_exact::launch_sweep(axis, stage, m->buf, m->P, dt, m->stream);
+    });
+  }
+  if (e != cudaSuccess) return e;
+  double* dst = stage == 1 ? m->buf.U1 : m->buf.U;
+  return timed(m, FV_KERNEL_GHOST, 1,
+               [&] { return launch_fill_ghosts(dst, m->P, m->stream); });
+}
+
+}  // namespace
+
+extern "C" {
+
+fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t* out) {
+  if (!out) {
+    set_error("out is NULL");
+    return FV_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  fv_status st = validate_desc(desc);
+  if (st != FV_OK) return st;
+  fv_mesh_s* m = new fv_mesh_s();
+  std::memset(&m->buf, 0, sizeof m->buf);
+  m->desc = *desc;
+  m->P = make_params(desc);
+  m->stream = (cudaStream_t)cuda_stream;
+  m->stage_pending = 0;
+  m->prof_on = false;
+  for (int c = 0; c < FV_KERNEL_NCLASS; ++c) m->launches[c] = 0;
+  cudaError_t e = cudaGetDevice(&m->device);
+  if (e != cudaSuccess) {
+    delete m;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  m->state_doubles = (size_t)fvd::NF * m->P.nfield;
+  m->dense_doubles = (size_t)fvd::NF * desc->nx * desc->ny * desc->nz;
+  const size_t sb = m->state_doubles * sizeof(double);
+  const size_t db = m->dense_doubles * sizeof(double);
+  const size_t wb = sums_work_doubles(m->P) * sizeof(double);
+  if ((e = cudaMalloc(&m->buf.U, sb)) != cudaSuccess ||
+      (e = cudaMalloc(&m->buf.U1, sb)) != cudaSuccess ||
+      (e = cudaMalloc(&m->buf.W, sb)) != cudaSuccess ||
+      (e = cudaMalloc(&m->buf.ACC, db)) != cudaSuccess ||
+      (e = cudaMalloc(&m->buf.ctr, sizeof(DevCounters))) != cudaSuccess ||
+      (e = cudaMalloc(&m->sums_work, wb)) != cudaSuccess ||
+      (e = cudaMalloc(&m->sums_out, 5 * sizeof(double))) != cudaSuccess ||
+      (e = cudaMallocHost(&m->host_ctr, sizeof(DevCounters))) != cudaSuccess ||
+      (e = cudaMallocHost(&m->host_sums, 5 * sizeof(double))) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("allocating %.3f GB of mesh storage: %s", (3.0 * sb + db) / 1e9,
+              cudaGetErrorString(e));
+    free_mesh(m);
+    return e == cudaErrorMemoryAllocation ? FV_ERR_OOM : FV_ERR_CUDA;
+  }
+  if ((e = cudaMemsetAsync(m->buf.U, 0, sb, m->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(m->buf.U1, 0, sb, m->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(m->buf.ctr, 0, sizeof(DevCounters), m->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(m->stream)) != cudaSuccess) {
+    free_mesh(m);
+    return cuda_fail(e, "initialising mesh storage");
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_registry_mutex);
+    g_registry.insert(m);
+  }
+  *out = m;
+  return FV_OK;
+}
+
+fv_status fv_destroy_mesh(fv_mesh_t m) {
+  if (!m) return FV_OK;
+  {
+    std::lock_guard<std::mutex> lk(g_registry_mutex);
+    if (!g_registry.erase(m)) {
+      set_error("mesh handle %p is not live (destroyed or foreign)", (void*)m);
+      return FV_ERR_BAD_HANDLE;
+    }
+  }
+  DeviceGuard g(m->device);
+  cudaStreamSynchronize(m->stream);
+  free_mesh(m);
+  return FV_OK;
+}
+
+fv_status fv_set_state(fv_mesh_t m, const double* U, int on_device) {
+  fv_status st = check_handle(m);
+  if (st != FV_OK) return st;
+  if (!U) {
+    set_error("U is NULL");
+    return FV_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(m->device);
+  cudaError_t e;
+  const double* src = U;
+  if (!on_device) {  // stage through the accumulator, which is free between steps
+    e = cudaMemcpyAsync(m->buf.ACC, U, m->dense_doubles * sizeof(double),
+                        cudaMemcpyHostToDevice, m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copying the state to the device");
+    src = m->buf.ACC;
+  }
+  e = timed(m, FV_KERNEL_OTHER, 1,
+            [&] { return launch_scatter_interior(src, m->buf.U, m->P, m->stream); });
+  if (e != cudaSuccess) return cuda_fail(e, "scatter kernel");
+  e = timed(m, FV_KERNEL_GHOST, 1, [&] { return launch_fill_ghosts(m->buf.U, m->P, m->stream); });
+  if (e != cudaSuccess) return cuda_fail(e, "ghost-fill kernel");
+  if ((e = cudaMemsetAsync(m->buf.ctr, 0, sizeof(DevCounters), m->stream)) != cudaSuccess)
+    return cuda_fail(e, "clearing counters");
+  m->stage_pending = 0;
+  if (!on_device && (e = cudaStreamSynchronize(m->stream)) != cudaSuccess)
+    return cuda_fail(e, "fv_set_state");
+  return FV_OK;
+}
+
+static fv_status get_state_impl(fv_mesh_t m, double* U, int on_device, bool ghosted) {
+  fv_status st = check_handle(m);
+  if (st != FV_OK) return st;
+  if (!U) {
+    set_error("U is NULL");
+    return FV_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(m->device);
+  const double* cur = m->stage_pending ? m->buf.U1 : m->buf.U;
+  cudaError_t e;
+  if (ghosted) {
+    e = cudaMemcpyAsync(U, cur, m->state_doubles * sizeof(double),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copying the ghosted state");
+  } else {
+    double* dst = on_device ? U : m->buf.ACC;
+    e = timed(m, FV_KERNEL_OTHER, 1,
+              [&] { return launch_gather_interior(cur, dst, m->P, m->stream); });
+    if (e != cudaSuccess) return cuda_fail(e, "gather kernel");
+    if (!on_device) {
+      e = cudaMemcpyAsync(U, m->buf.ACC, m->dense_doubles * sizeof(double),
+                          cudaMemcpyDeviceToHost, m->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "copying the state to the host");
+    }
+  }
+  if ((st = read_counters(m)) != FV_OK) return st;
+  return nonphysical_status(m);
+}
+
+fv_status fv_get_state(fv_mesh_t m, double* U, int on_device) {
+  return get_state_impl(m, U, on_device, false);
+}
+
+fv_status fv_get_ghosted_state(fv_mesh_t m, double* U, int on_device) {
+  return get_state_impl(m, U, on_device, true);
+}
+
+fv_status fv_reduce_dt(fv_mesh_t m, double cfl, double* dt_out) {
+  fv_status st = check_handle(m);
+  if (st != FV_OK) return st;
+  if (!dt_out || !(cfl > 0.0) || !std::isfinite(cfl)) {
+    set_error("fv_reduce_dt needs cfl > 0 (got %g) and a non-NULL dt_out", cfl);
+    return FV_ERR_INVALID_ARG;
+  }
+  if (m->stage_pending) {
+    set_error("fv_reduce_dt called between the two RK substeps");
+    return FV_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(m->device);
+  cudaError_t e = timed(m, FV_KERNEL_DT, 1,
+                        [&] { return launch_reduce_dt(m->buf.U, m->P, m->buf.ctr, m->stream); });
+  if (e != cudaSuccess) return cuda_fail(e, "time-step kernel");
+  if ((st = read_counters(m)) != FV_OK) return st;
+  double smax;
+  std::memcpy(&smax, &m->host_ctr->smax_bits, sizeof smax);
+  *dt_out = cfl / smax;
+  return nonphysical_status(m);
+}
+
+fv_status fv_substep(fv_mesh_t m, int stage, double dt) {
+  fv_status st = check_handle(m);
+  if (st != FV_OK) return st;
+  if (!(dt >= 0.0) || !std::isfinite(dt)) {
+    set_error("dt %g must be finite and >= 0", dt);
+    return FV_ERR_INVALID_ARG;
+  }
+  if (stage != 1 && stage != 2) {
+    set_error("stage %d must be 1 or 2", stage);
+    return FV_ERR_INVALID_ARG;
+  }
+  if ((stage == 1) == (m->stage_pending != 0)) {
+    set_error(stage == 1 ? "substep 1 requested while substep 2 is pending"
+                         : "substep 2 requested without substep 1");
+    return FV_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(m->device);
+  cudaError_t e = launch_substep(m, stage, dt);
+  if (e != cudaSuccess) return cuda_fail(e, "substep kernels");
+  m->stage_pending = stage == 1;
+  return FV_OK;
+}
+
+fv_status fv_step(fv_mesh_t m, double dt) {
+  fv_status st = check_handle(m);
+  if (st != FV_OK) return st;
+  if (m->stage_pending) {
+    set_error("fv_step called between the two RK substeps");
+    return FV_ERR_INVALID_ARG;
+  }
+  if ((st = fv_substep(m, 1, dt)) != FV_OK) return st;
+  return fv_substep(m, 2, dt);
+}
+
+fv_status fv_fill_ghosts(fv_mesh_t m) {
+  fv_status st = check_handle(m);
+  if (st != FV_OK) return st;
+  DeviceGuard g(m->device);
+  double* cur = m->stage_pending ? m->buf.U1 : m->buf.U;
+  cudaError_t e = timed(m, FV_KERNEL_GHOST, 1, [&] { return launch_fill_ghosts(cur, m->P, m->stream); });
+  if (e != cudaSuccess) return cuda_fail(e, "ghost-fill kernel");
+  return FV_OK;
+}
+
+fv_status fv_conserved_sums(fv_mesh_t m, double out[5]) {
+  fv_status st = check_handle(m);
+  if (st != FV_OK) return st;
+  if (!out) {
+    set_error("out is NULL");
+    return FV_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(m->device);
+  const double* cur = m->stage_pending ? m->buf.U1 : m->buf.U;
+  cudaError_t e = timed(m, FV_KERNEL_OTHER, 1, [&] {
+    return launch_pairwise_sums(cur, m->P, m->sums_work, m->sums_out, m->stream);
+  });
+  if (e != cudaSuccess) return cuda_fail(e, "sum kernels");
+  e = cudaMemcpyAsync(m->host_sums, m->sums_out, 5 * sizeof(double), cudaMemcpyDeviceToHost,
+                      m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reading sums");
+  const double dx = m->desc.lx / m->desc.nx, dy = m->desc.ly / m->desc.ny,
+               dz = m->desc.lz / m->desc.nz;
+  const double vol = (dx * dy) * dz;
+  for (int q = 0; q < 5; ++q) out[q] = m->host_sums[q] * vol;
+  return FV_OK;
+}
+
+fv_status fv_get_counters(fv_mesh_t m, long long* nonphysical_cells, long long* fallback_faces) {
+  fv_status st = check_handle(m);
+  if (st != FV_OK) return st;
+  DeviceGuard g(m->device);
+  if ((st = read_counters(m)) != FV_OK) return st;
+  if (nonphysical_cells)
+    *nonphysical_cells = (long long)(m->host_ctr->np_step + m->host_ctr->np_dt);
+  if (fallback_faces) *fallback_faces = (long long)m->host_ctr->fallback;
+  return FV_OK;
+}
+
+fv_status fv_profile_enable(fv_mesh_t m, int on) {
+  fv_status st = check_handle(m);
+  if (st != FV_OK) return st;
+  m->prof_on = on != 0;
+  return FV_OK;
+}
+
+fv_status fv_profile_read(fv_mesh_t m, double* ms, long long* launches) {
+  fv_status st = check_handle(m);
+  if (st != FV_OK) return st;
+  DeviceGuard g(m->device);
+  cudaError_t e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "fv_profile_read");
+  double acc[FV_KERNEL_NCLASS] = {0};
+  for (auto& t : m->pending) {
+    float x = 0.f;
+    if (cudaEventElapsedTime(&x, t.a, t.b) == cudaSuccess) acc[t.cls] += x;
+    m->event_pool.push_back(t.a);
+    m->event_pool.push_back(t.b);
+  }
+  m->pending.clear();
+  for (int c = 0; c < FV_KERNEL_NCLASS; ++c) {
+    if (ms) ms[c] = acc[c];
+    if (launches) launches[c] = m->launches[c];
+    m->launches[c] = 0;
+  }
+  return FV_OK;
+}
+
+fv_status fv_mesh_info(fv_mesh_t m, int dims[3], size_t* state_bytes) {
+  fv_status st = check_handle(m);
+  if (st != FV_OK) return st;
+  if (dims) {
+    dims[0] = m->desc.nx;
+    dims[1] = m->desc.ny;
+    dims[2] = m->desc.nz;
+  }
+  if (state_bytes) *state_bytes = m->state_doubles * sizeof(double);
+  return FV_OK;
+}
+
+const char* fv_status_string(fv_status s) {
+  switch (s) {
+    case FV_OK: return "FV_OK";
+    case FV_ERR_INVALID_ARG: return "FV_ERR_INVALID_ARG";
+    case FV_ERR_OOM: return "FV_ERR_OOM";
+    case FV_ERR_CUDA: return "FV_ERR_CUDA";
+    case FV_ERR_NONPHYSICAL: return "FV_ERR_NONPHYSICAL";
+    case FV_ERR_TIMEOUT: return "FV_ERR_TIMEOUT";
+    case FV_ERR_BAD_HANDLE: return "FV_ERR_BAD_HANDLE";
+  }
+  return "FV_ERR_UNKNOWN";
+}
+
+const char* fv_last_error(void) { return g_last_error; }
+
+}  // extern "C"

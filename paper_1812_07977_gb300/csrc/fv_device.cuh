@@ -1,0 +1,185 @@
+// fv_device.cuh -- device-side building blocks of the finite-volume step.
+//
+// FP64 on sm_103a retires about two double-precision operations per SM per
+// clock (a warp instruction occupies the DP units for ~16 clocks), while the
+// integer and FP32 pipes retire ~128.  Everything here that can be done
+// exactly without the DP pipe is therefore done on integers: the sign and
+// magnitude tests of the limiter and of the wave-speed maxima, the positivity
+// tests, and multiplication by 2 and by 1/2 (an exponent increment, exact
+// except at the ends of the exponent range, where the DP multiply is used).
+// Each helper returns bit for bit what the corresponding IEEE operation
+// returns, so the results stay reproducible against a plain FP64 code.
+#pragma once
+
+#include <cstdint>
+
+namespace fvd {
+
+constexpr int NF = 5;  // rho, rho*vx, rho*vy, rho*vz, E  /  rho, vx, vy, vz, p
+
+// Limiter parameter classes with an exact integer form of theta * x.
+enum ThetaKind { THETA_GENERAL = 0, THETA_ZERO = 1, THETA_ONE = 2, THETA_TWO = 3 };
+
+struct Params {
+  int nx, ny, nz;
+  long long sy, sz;       // ghosted strides of y and z (x stride is 1)
+  long long nfield;       // doubles per ghosted field
+  double gamma;           // ratio of specific heats
+  double gm1;             // gamma - 1
+  double igm1;            // 1 / (gamma - 1)
+  double theta;           // limiter parameter
+  double inv_d[3];        // 1 / dx, 1 / dy, 1 / dz
+  int bc[3];              // 0 outflow, 1 periodic
+};
+
+// ---------------------------------------------------------------- bit tools
+__device__ __forceinline__ long long bits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ double from_bits(long long b) { return __longlong_as_double(b); }
+
+constexpr long long kExpOne = 1LL << 52;
+constexpr long long kInfBits = 0x7FF0000000000000LL;
+constexpr long long kMagMask = 0x7FFFFFFFFFFFFFFFLL;
+
+// x > 0.0 (false for NaN and for -0)
+__device__ __forceinline__ bool is_pos(double x) {
+  long long b = bits(x);
+  return b > 0 && b <= kInfBits;
+}
+
+// x * 0.5, bit-identical to the IEEE product
+__device__ __forceinline__ double half(double x) {
+  long long b = bits(x);
+  unsigned e = (unsigned)(b >> 52) & 0x7FFu;
+  if (e > 1u && e < 0x7FFu) return from_bits(b - kExpOne);
+  return x * 0.5;
+}
+
+// x * 2.0, bit-identical to the IEEE product
+__device__ __forceinline__ double twice(double x) {
+  long long b = bits(x);
+  unsigned e = (unsigned)(b >> 52) & 0x7FFu;
+  if (e >= 1u && e < 0x7FEu) return from_bits(b + kExpOne);
+  return x * 2.0;
+}
+
+// minmod(a, b, c): the argument of least magnitude if all three are > 0 or
+// all three are < 0, else +0.  NaN counts as neither sign.
+__device__ __forceinline__ double minmod3(double a, double b, double c) {
+  long long ia = bits(a), ib = bits(b), ic = bits(c);
+  long long ma = ia & kMagMask, mb = ib & kMagMask, mc = ic & kMagMask;
+  bool nz = (ma != 0) & (mb != 0) & (mc != 0) & (ma <= kInfBits) & (mb <= kInfBits) &
+            (mc <= kInfBits);
+  bool same = ((ia ^ ib) >= 0) & ((ia ^ ic) >= 0);
+  long long m = ma;
+  long long r = ia;
+  if (mb < m) { m = mb; r = ib; }
+  if (mc < m) { r = ic; }
+  return (nz && same) ? from_bits(r) : 0.0;
+}
+
+// max(0, a, b) evaluated as r = 0; if (a > r) r = a; if (b > r) r = b
+__device__ __forceinline__ double max0(double a, double b) {
+  long long r = 0;
+  long long ia = bits(a), ib = bits(b);
+  if (ia > 0 && ia <= kInfBits) r = ia;
+  if (ib > r && ib <= kInfBits) r = ib;
+  return from_bits(r);
+}
+
+template <int TK>
+__device__ __forceinline__ double theta_times(double theta, double x) {
+  if (TK == THETA_TWO) return twice(x);
+  if (TK == THETA_ONE) return x;
+  return theta * x;
+}
+
+// Half of the limited slope of one cell from its two one-sided differences:
+// 0.5 * minmod(theta*dm, 0.5*(dm + dp), theta*dp).  With theta = 0 the first
+// argument is +-0 (or NaN), so the minmod is +0 whatever dm and dp are.
+template <int TK>
+__device__ __forceinline__ double half_slope(double theta, double dm, double dp) {
+  if (TK == THETA_ZERO) return 0.0;
+  return half(minmod3(theta_times<TK>(theta, dm), half(dm + dp), theta_times<TK>(theta, dp)));
+}
+
+// ---------------------------------------------------------------- physics
+struct Prim { double r, vx, vy, vz, p; };
+
+__device__ __forceinline__ double comp(const Prim& w, int q) {
+  return q == 0 ? w.r : q == 1 ? w.vx : q == 2 ? w.vy : q == 3 ? w.vz : w.p;
+}
+
+// conserved -> primitive: ir = 1/rho, v = m*ir,
+// p = (gamma-1) * (E - 0.5*((mx*vx + my*vy) + mz*vz))
+__device__ __forceinline__ Prim cons_to_prim(const double u[NF], const Params& P) {
+  Prim w;
+  double ir = 1.0 / u[0];
+  w.r = u[0];
+  w.vx = u[1] * ir;
+  w.vy = u[2] * ir;
+  w.vz = u[3] * ir;
+  double ke = half((u[1] * w.vx + u[2] * w.vy) + u[3] * w.vz);
+  w.p = P.gm1 * (u[4] - ke);
+  return w;
+}
+
+// One side of a face: conserved state, normal flux, sound speed.
+template <int AXIS>
+struct Side {
+  double u[NF];
+  double f[NF];
+  double c;
+  double vn;
+};
+
+template <int AXIS>
+__device__ __forceinline__ void euler_side(const Prim& w, const Params& P, Side<AXIS>& s) {
+  double mx = w.r * w.vx;
+  double my = w.r * w.vy;
+  double mz = w.r * w.vz;
+  double ke = half((mx * w.vx + my * w.vy) + mz * w.vz);
+  s.u[0] = w.r;
+  s.u[1] = mx;
+  s.u[2] = my;
+  s.u[3] = mz;
+  s.u[4] = w.p * P.igm1 + ke;
+  double vn = AXIS == 0 ? w.vx : AXIS == 1 ? w.vy : w.vz;
+  double mn = AXIS == 0 ? mx : AXIS == 1 ? my : mz;
+  s.vn = vn;
+  s.c = sqrt(P.gamma * w.p / w.r);
+  s.f[0] = mn;
+  s.f[1] = mn * w.vx;
+  s.f[2] = mn * w.vy;
+  s.f[3] = mn * w.vz;
+  s.f[1 + AXIS] = s.f[1 + AXIS] + w.p;
+  s.f[4] = (s.u[4] + w.p) * vn;
+}
+
+// HLL flux (Harten, Lax & van Leer 1983) with wave bounds from both sides:
+// a+ = max(0, vL + cL, vR + cR), a- = max(0, cL - vL, cR - vR),
+// F = ((a+ FL + a- FR) - a+ a- (UR - UL)) * (1 / (a+ + a-)).
+template <int AXIS>
+__device__ __forceinline__ void hll_flux(const Prim& wl, const Prim& wr, const Params& P,
+                                         double F[NF]) {
+  Side<AXIS> L, R;
+  euler_side<AXIS>(wl, P, L);
+  euler_side<AXIS>(wr, P, R);
+  double ap = max0(L.vn + L.c, R.vn + R.c);
+  double am = max0(L.c - L.vn, R.c - R.vn);
+  double r = 1.0 / (ap + am);
+  double apm = ap * am;
+#pragma unroll
+  for (int q = 0; q < NF; ++q) F[q] = ((ap * L.f[q] + am * R.f[q]) - apm * (R.u[q] - L.u[q])) * r;
+}
+
+// Source index of a ghost coordinate g along an axis of n interior cells.
+__device__ __forceinline__ int ghost_source(int g, int n, int bc) {
+  if (g >= 0 && g < n) return g;
+  if (bc == 1) {
+    int r = g % n;
+    return r < 0 ? r + n : r;
+  }
+  return g < 0 ? 0 : n - 1;
+}
+
+}  // namespace fvd

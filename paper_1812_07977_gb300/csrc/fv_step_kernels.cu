@@ -1,0 +1,197 @@
+// fv_step_kernels.cu -- one RK2 substep of the FP64 finite-volume method.
+//
+// Compiled twice: FV_NS=fv_fp64_exact with --fmad=false (every operation
+// rounded on its own, in the order of the method's definition) and
+// FV_NS=fv_fp64_fma with --fmad=true.
+//
+// Structure of one substep of Algorithm 1 (its kernel sequence):
+//   k_prim            conserved -> primitive for every ghosted cell
+//   k_sweep<x>        ComputeDifferences, ComputeReconstruction,
+//                     RiemannSolverInput and ComputeFluxes along x, and the
+//                     x part of ComputeUpdate: ACC = -(F(i+1/2)-F(i-1/2))/dx
+//   k_sweep<y>        the same along y: ACC -= (G(j+1/2)-G(j-1/2))/dy
+//   k_sweep<z>        the same along z, then dU = dt*ACC and the RK combine
+//                     (stage 1: U1 = U + dU; stage 2: U = (U + U1 + dU)/2)
+// Each thread walks one grid line along the sweep axis with a sliding
+// register window (four cells of primitives, the differences and half
+// slopes of two cells, the previous face flux), so every difference, slope
+// and face flux is computed exactly once.  On this GPU the FP64 pipe is the
+// bottleneck by a wide margin, so the design spends memory traffic (the
+// primitive and accumulator arrays) to never repeat FP64 work.
+#include "fv_device.cuh"
+#include "fv_internal.h"
+
+#ifndef FV_NS
+#error "FV_NS must name the variant namespace"
+#endif
+
+using namespace fvd;
+
+namespace FV_NS {
+namespace {
+
+constexpr int kPrimThreads = 256;
+constexpr int kSweepThreads = 128;
+
+__global__ void __launch_bounds__(kPrimThreads)
+k_prim(const double* __restrict__ U, double* __restrict__ W, Params P, DevCounters* ctr) {
+  const long long nf = P.nfield;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nf;
+       c += (long long)gridDim.x * blockDim.x) {
+    double u[NF];
+#pragma unroll
+    for (int q = 0; q < NF; ++q) u[q] = U[q * nf + c];
+    Prim w = cons_to_prim(u, P);
+    W[c] = w.r;
+    W[nf + c] = w.vx;
+    W[2 * nf + c] = w.vy;
+    W[3 * nf + c] = w.vz;
+    W[4 * nf + c] = w.p;
+    if (!(is_pos(w.r) && is_pos(w.p))) {
+      long long k = c / P.sz;
+      long long rem = c - k * P.sz;
+      long long j = rem / P.sy;
+      long long i = rem - j * P.sy;
+      if (i >= 2 && i < P.nx + 2 && j >= 2 && j < P.ny + 2 && k >= 2 && k < P.nz + 2)
+        atomicAdd(&ctr->np_step, 1ULL);
+    }
+  }
+}
+
+__device__ __forceinline__ Prim load_prim(const double* __restrict__ W, long long off,
+                                          long long nf) {
+  Prim w;
+  w.r = W[off];
+  w.vx = W[nf + off];
+  w.vy = W[2 * nf + off];
+  w.vz = W[3 * nf + off];
+  w.p = W[4 * nf + off];
+  return w;
+}
+
+__device__ __forceinline__ Prim sub(const Prim& a, const Prim& b) {
+  return Prim{a.r - b.r, a.vx - b.vx, a.vy - b.vy, a.vz - b.vz, a.p - b.p};
+}
+
+__device__ __forceinline__ Prim add(const Prim& a, const Prim& b) {
+  return Prim{a.r + b.r, a.vx + b.vx, a.vy + b.vy, a.vz + b.vz, a.p + b.p};
+}
+
+template <int TK>
+__device__ __forceinline__ Prim half_slopes(double theta, const Prim& dm, const Prim& dp) {
+  return Prim{half_slope<TK>(theta, dm.r, dp.r), half_slope<TK>(theta, dm.vx, dp.vx),
+              half_slope<TK>(theta, dm.vy, dp.vy), half_slope<TK>(theta, dm.vz, dp.vz),
+              half_slope<TK>(theta, dm.p, dp.p)};
+}
+
+// AXIS: 0, 1, 2.  STAGE: 0 for the x and y sweeps; 1 or 2 (the RK stage)
+// for the z sweep, which finishes the update.
+template <int AXIS, int STAGE, int TK>
+__global__ void __launch_bounds__(kSweepThreads)
+k_sweep(const double* __restrict__ W, double* __restrict__ ACC, double* __restrict__ U,
+        double* __restrict__ U1, Params P, double dt, DevCounters* ctr) {
+  const int n = AXIS == 0 ? P.nx : AXIS == 1 ? P.ny : P.nz;
+  const int na = AXIS == 0 ? P.ny : P.nx;
+  const int nb = AXIS == 2 ? P.ny : P.nz;
+  const long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (line >= (long long)na * nb) return;
+  const int a = (int)(line % na);
+  const int b = (int)(line / na);
+  const int i0 = AXIS == 0 ? 0 : a;
+  const int j0 = AXIS == 0 ? a : (AXIS == 1 ? 0 : b);
+  const int k0 = AXIS == 2 ? 0 : b;
+  const long long nf = P.nfield;
+  const long long gs = AXIS == 0 ? 1 : (AXIS == 1 ? P.sy : P.sz);
+  const long long g0 = (k0 + 2) * P.sz + (j0 + 2) * P.sy + (i0 + 2);
+  const long long nd = (long long)P.nx * P.ny * P.nz;
+  const long long ds = AXIS == 0 ? 1 : (AXIS == 1 ? (long long)P.nx : (long long)P.nx * P.ny);
+  const long long d0 = ((long long)k0 * P.ny + j0) * P.nx + i0;
+  const double inv = P.inv_d[AXIS];
+  const double theta = P.theta;
+
+  // window: wl_cell = W(f-1), wc = W(f); differences D(f) = W(f) - W(f-1)
+  Prim wm2 = load_prim(W, g0 - 2 * gs, nf);
+  Prim wm1 = load_prim(W, g0 - gs, nf);
+  Prim wc = load_prim(W, g0, nf);
+  Prim dcur = sub(wc, wm1);                               // D(0)
+  Prim hprev = half_slopes<TK>(theta, sub(wm1, wm2), dcur);  // cell -1
+  Prim wprev = wm1;                                       // W(f-1)
+  double Fprev[NF];
+#pragma unroll
+  for (int q = 0; q < NF; ++q) Fprev[q] = 0.0;
+
+  for (int f = 0; f <= n; ++f) {
+    Prim wn = load_prim(W, g0 + (long long)(f + 1) * gs, nf);  // W(f+1)
+    Prim dnext = sub(wn, wc);                                 // D(f+1)
+    Prim hcur = half_slopes<TK>(theta, dcur, dnext);          // cell f
+    // face f-1/2 between cells f-1 and f
+    Prim wl = add(wprev, hprev);
+    Prim wr = sub(wc, hcur);
+    if (!(is_pos(wl.r) && is_pos(wl.p) && is_pos(wr.r) && is_pos(wr.p))) {
+      wl = wprev;
+      wr = wc;
+      atomicAdd(&ctr->fallback, 1ULL);
+    }
+    double F[NF];
+    hll_flux<AXIS>(wl, wr, P, F);
+    if (f > 0) {  // cell f-1 has both of its faces
+      const long long dc = d0 + (long long)(f - 1) * ds;
+#pragma unroll
+      for (int q = 0; q < NF; ++q) {
+        const double diff = F[q] - Fprev[q];
+        if (AXIS == 0) {
+          ACC[q * nd + dc] = -diff * inv;
+        } else if (AXIS == 1) {
+          ACC[q * nd + dc] = ACC[q * nd + dc] - diff * inv;
+        } else {
+          const double acc = ACC[q * nd + dc] - diff * inv;
+          const double du = dt * acc;
+          const long long gc = q * nf + g0 + (long long)(f - 1) * gs;
+          if (STAGE == 1) U1[gc] = U[gc] + du;
+          else U[gc] = half((U[gc] + U1[gc]) + du);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NF; ++q) Fprev[q] = F[q];
+    wprev = wc;
+    wc = wn;
+    dcur = dnext;
+    hprev = hcur;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_prim(const double* src, const StepBuffers& b, const Params& P,
+                        cudaStream_t s) {
+  long long blocks = (P.nfield + kPrimThreads - 1) / kPrimThreads;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_prim<<<(unsigned)blocks, kPrimThreads, 0, s>>>(src, b.W, P, b.ctr);
+  return cudaGetLastError();
+}
+
+template <int TK>
+static cudaError_t sweep_tk(int axis, int stage, const StepBuffers& b, const Params& P,
+                            double dt, cudaStream_t s) {
+  const long long lines = axis == 0 ? (long long)P.ny * P.nz
+                        : axis == 1 ? (long long)P.nx * P.nz : (long long)P.nx * P.ny;
+  const unsigned g = (unsigned)((lines + kSweepThreads - 1) / kSweepThreads);
+  if (axis == 0)
+    k_sweep<0, 0, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, b.ctr);
+  else if (axis == 1)
+    k_sweep<1, 0, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, b.ctr);
+  else if (stage == 1)
+    k_sweep<2, 1, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, b.ctr);
+  else
+    k_sweep<2, 2, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, b.ctr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(int axis, int stage, const StepBuffers& b, const Params& P, double dt,
+                         cudaStream_t s) {
+  if (P.theta == 2.0) return sweep_tk<THETA_TWO>(axis, stage, b, P, dt, s);
+  return sweep_tk<THETA_GENERAL>(axis, stage, b, P, dt, s);
+}
+
+}  // namespace FV_NS

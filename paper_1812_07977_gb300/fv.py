@@ -1,0 +1,247 @@
+"""Python binding of the C ABI in include/fv.h (argument marshalling only).
+
+Every stage of the step runs in the CUDA kernels of ``libfvgb.so``; this
+module converts arguments, checks shapes and raises :class:`FvError` on a
+non-OK status.  It never computes anything itself and has no CPU path: if
+the library is missing it raises instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfvgb.so")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_BAD_HANDLE = range(7)
+BC = {"outflow": 0, "periodic": 1}
+PRECISION = {"fp64": 0, "fp64_fma": 1}
+
+# Every entry point declared in include/fv.h.
+ABI_SYMBOLS = (
+    "fv_create_mesh", "fv_destroy_mesh", "fv_set_state", "fv_get_state",
+    "fv_get_ghosted_state", "fv_reduce_dt", "fv_step", "fv_substep", "fv_fill_ghosts",
+    "fv_conserved_sums", "fv_get_counters", "fv_profile_enable", "fv_profile_read",
+    "fv_mesh_info", "fv_status_string", "fv_last_error",
+)
+KERNEL_CLASSES = ("prim", "sweep_x", "sweep_y", "sweep_z", "ghost", "dt", "other")
+
+
+class FvError(RuntimeError):
+    def __init__(self, status: int, call: str, detail: str):
+        self.status = status
+        super().__init__(f"{call}: {_status_name(status)}: {detail}")
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("theta", ctypes.c_double),
+                ("bc", ctypes.c_int * 3), ("precision", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libfvgb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"CUDA library {p} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(p)
+    vp, dp, i = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    d = ctypes.c_double
+    sig = {
+        "fv_create_mesh": ([ctypes.POINTER(MeshDesc), vp, ctypes.POINTER(vp)], i),
+        "fv_destroy_mesh": ([vp], i),
+        "fv_set_state": ([vp, vp, i], i),
+        "fv_get_state": ([vp, vp, i], i),
+        "fv_get_ghosted_state": ([vp, vp, i], i),
+        "fv_reduce_dt": ([vp, d, dp], i),
+        "fv_step": ([vp, d], i),
+        "fv_substep": ([vp, i, d], i),
+        "fv_fill_ghosts": ([vp], i),
+        "fv_conserved_sums": ([vp, dp], i),
+        "fv_get_counters": ([vp, ctypes.POINTER(ctypes.c_longlong),
+                             ctypes.POINTER(ctypes.c_longlong)], i),
+        "fv_profile_enable": ([vp, i], i),
+        "fv_profile_read": ([vp, dp, ctypes.POINTER(ctypes.c_longlong)], i),
+        "fv_mesh_info": ([vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)], i),
+        "fv_status_string": ([i], ctypes.c_char_p),
+        "fv_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _status_name(s: int) -> str:
+    names = ["FV_OK", "FV_ERR_INVALID_ARG", "FV_ERR_OOM", "FV_ERR_CUDA",
+             "FV_ERR_NONPHYSICAL", "FV_ERR_TIMEOUT", "FV_ERR_BAD_HANDLE"]
+    return names[s] if 0 <= s < len(names) else f"status {s}"
+
+
+def _check(status: int, call: str):
+    if status != OK:
+        raise FvError(status, call, load_library().fv_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Mesh:
+    """One mesh of the RK2 finite-volume step on the current CUDA device.
+
+    States are (5, nz, ny, nx) float64 arrays of conserved variables
+    (rho, rho*vx, rho*vy, rho*vz, E): torch CUDA tensors are passed by
+    device pointer, numpy arrays / CPU tensors through host memory.
+    """
+
+    def __init__(self, nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, gamma=1.4, theta=2.0,
+                 bc=("outflow", "outflow", "outflow"), precision="fp64", stream=None):
+        self._lib = load_library()
+        torch = _torch()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        d = MeshDesc()
+        d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
+        d.lx, d.ly, d.lz = float(lx), float(ly), float(lz)
+        d.gamma, d.theta = float(gamma), float(theta)
+        for a in range(3):
+            d.bc[a] = BC[bc[a]] if isinstance(bc[a], str) else int(bc[a])
+        d.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        self.desc = d
+        self.shape = (5, d.nz, d.ny, d.nx)
+        self.ghosted_shape = (5, d.nz + 4, d.ny + 4, d.nx + 4)
+        self.device = torch.cuda.current_device()
+        h = ctypes.c_void_p()
+        _check(self._lib.fv_create_mesh(ctypes.byref(d), ctypes.c_void_p(stream.cuda_stream),
+                                        ctypes.byref(h)), "fv_create_mesh")
+        self._h = h
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(self._lib.fv_destroy_mesh(self._h), "fv_destroy_mesh")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- state
+    def _buffer(self, U, shape, writable):
+        torch = _torch()
+        if isinstance(U, torch.Tensor):
+            if tuple(U.shape) != shape or U.dtype != torch.float64 or not U.is_contiguous():
+                raise ValueError(f"expected a contiguous float64 tensor of shape {shape}")
+            if U.is_cuda:
+                return ctypes.c_void_p(U.data_ptr()), 1
+            return ctypes.c_void_p(U.data_ptr()), 0
+        if isinstance(U, np.ndarray):
+            if U.shape != shape or U.dtype != np.float64 or not U.flags["C_CONTIGUOUS"]:
+                raise ValueError(f"expected a C-contiguous float64 array of shape {shape}")
+            if writable and not U.flags["WRITEABLE"]:
+                raise ValueError("output array is read-only")
+            return ctypes.c_void_p(U.ctypes.data), 0
+        raise TypeError("state must be a torch tensor or a numpy array")
+
+    def set_state(self, U):
+        ptr, dev = self._buffer(U, self.shape, False)
+        _check(self._lib.fv_set_state(self._h, ptr, dev), "fv_set_state")
+
+    def get_state(self, out=None):
+        """Interior state; into `out` if given, else a new CUDA tensor."""
+        if out is None:
+            out = _torch().empty(self.shape, dtype=_torch().float64, device=f"cuda:{self.device}")
+        ptr, dev = self._buffer(out, self.shape, True)
+        _check(self._lib.fv_get_state(self._h, ptr, dev), "fv_get_state")
+        return out
+
+    def get_ghosted_state(self, out=None):
+        if out is None:
+            out = _torch().empty(self.ghosted_shape, dtype=_torch().float64,
+                                 device=f"cuda:{self.device}")
+        ptr, dev = self._buffer(out, self.ghosted_shape, True)
+        _check(self._lib.fv_get_ghosted_state(self._h, ptr, dev), "fv_get_ghosted_state")
+        return out
+
+    # -- the method
+    def reduce_dt(self, cfl: float) -> float:
+        dt = ctypes.c_double()
+        _check(self._lib.fv_reduce_dt(self._h, float(cfl), ctypes.byref(dt)), "fv_reduce_dt")
+        return dt.value
+
+    def step(self, dt: float):
+        _check(self._lib.fv_step(self._h, float(dt)), "fv_step")
+
+    def substep(self, stage: int, dt: float):
+        _check(self._lib.fv_substep(self._h, int(stage), float(dt)), "fv_substep")
+
+    def fill_ghosts(self):
+        _check(self._lib.fv_fill_ghosts(self._h), "fv_fill_ghosts")
+
+    def conserved_sums(self) -> np.ndarray:
+        out = (ctypes.c_double * 5)()
+        _check(self._lib.fv_conserved_sums(self._h, out), "fv_conserved_sums")
+        return np.array(out[:])
+
+    def counters(self):
+        a, b = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(self._lib.fv_get_counters(self._h, ctypes.byref(a), ctypes.byref(b)),
+               "fv_get_counters")
+        return a.value, b.value
+
+    def profile(self, on: bool = True):
+        _check(self._lib.fv_profile_enable(self._h, int(bool(on))), "fv_profile_enable")
+
+    def read_profile(self):
+        """{class: (device ms, launches)} since the last read; resets."""
+        n = len(KERNEL_CLASSES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_longlong * n)()
+        _check(self._lib.fv_profile_read(self._h, ms, cnt), "fv_profile_read")
+        return {c: (ms[k], cnt[k]) for k, c in enumerate(KERNEL_CLASSES)}
+
+    def evolve(self, cfl: float, t_end: float | None = None, nsteps: int | None = None):
+        """Algorithm 1's time loop: dt = min(ComputeTimeStep, t_end - t), step.
+        Returns (t, steps, dts)."""
+        t, n, dts = 0.0, 0, []
+        while True:
+            if t_end is not None and not t < t_end:
+                break
+            if nsteps is not None and n >= nsteps:
+                break
+            dt = self.reduce_dt(cfl)
+            if t_end is not None and dt > t_end - t:
+                dt = t_end - t
+            self.step(dt)
+            dts.append(dt)
+            t += dt
+            n += 1
+        return t, n, dts

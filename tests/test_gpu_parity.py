@@ -1,0 +1,260 @@
+"""GPU parity: every stage of the CUDA path against the oracle on the same
+seeded inputs, through the C ABI.
+
+The FP64 path (FV_PREC_FP64) performs the method's operations in the
+oracle's order without contraction, so the comparison is bitwise (equality,
+which also satisfies the 1e-12 relative target).  The FMA-contracted
+variant is held to the 1e-12 target: |gpu - oracle| <= 1e-12 * max|oracle|
+per field (field-scale relative error; the momenta vanish in places, so an
+elementwise relative error has no meaningful denominator there).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1812_07977_gb300 import problems
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+OUT, PER = 0, 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+
+
+def _pair(nx, ny, nz, U0, bc=(OUT, OUT, OUT), theta=2.0, precision="fp64", l=(1.0, 1.0, 1.0),
+          gamma=1.4):
+    from paper_1812_07977_gb300.fv import Mesh
+    om = oracle.mesh(nx, ny, nz, lx=l[0], ly=l[1], lz=l[2], gamma=gamma, theta=theta, bc=bc)
+    Uo = oracle.ghosted_from_interior(om, U0)
+    m = Mesh(nx, ny, nz, lx=l[0], ly=l[1], lz=l[2], gamma=gamma, theta=theta,
+             bc=tuple("periodic" if b == PER else "outflow" for b in bc), precision=precision)
+    m.set_state(torch.from_numpy(np.ascontiguousarray(U0)).cuda())
+    return om, Uo, m
+
+
+def _field_rel_err(got, ref):
+    scale = np.abs(ref).reshape(5, -1).max(1)
+    return (np.abs(got - ref).reshape(5, -1).max(1) / np.maximum(scale, 1e-300))
+
+
+def _run_both(om, Uo, m, nsteps, cfl=0.4):
+    for _ in range(nsteps):
+        dt = m.reduce_dt(cfl)
+        dto, _, bad = oracle.reduce_dt(om, Uo, cfl)
+        assert bad == 0
+        assert dt == dto, (dt, dto)
+        m.step(dt)
+        oracle.step(om, Uo, dt)
+
+
+SIZES = [(4, 4, 4), (5, 7, 3), (1, 9, 1), (33, 17, 9), (48, 40, 36)]
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("bc", [(OUT, OUT, OUT), (PER, PER, PER), (PER, OUT, PER)])
+def test_ghost_fill_bitwise(n, bc):
+    nx, ny, nz = n
+    rng = np.random.default_rng(nx * 100 + ny)
+    U0 = rng.standard_normal((5, nz, ny, nx))
+    om, Uo, m = _pair(nx, ny, nz, U0, bc=bc)
+    got = m.get_ghosted_state().cpu().numpy()
+    assert np.array_equal(got, Uo)
+    m.close()
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_reduce_dt_bitwise(n):
+    nx, ny, nz = n
+    U0 = problems.random_smooth_periodic(nx, ny, nz, seed=5)
+    om, Uo, m = _pair(nx, ny, nz, U0, l=(1.0, 2.0, 0.5))
+    dt = m.reduce_dt(0.4)
+    dto, _, _ = oracle.reduce_dt(om, Uo, 0.4)
+    assert dt == dto
+    m.close()
+
+
+@pytest.mark.parametrize("n", [(5, 7, 3), (33, 17, 9), (48, 40, 36)])
+@pytest.mark.parametrize("theta", [2.0, 1.0, 0.0, 1.3])
+def test_substep1_bitwise(n, theta):
+    nx, ny, nz = n
+    U0 = problems.random_smooth_periodic(nx, ny, nz, seed=17)
+    om, Uo, m = _pair(nx, ny, nz, U0, theta=theta, bc=(PER, OUT, PER))
+    dt = 0.3 * oracle.reduce_dt(om, Uo, 0.4)[0]
+    dU, bad, fb = oracle.compute_update(om, Uo, dt)
+    m.substep(1, dt)
+    got = m.get_state().cpu().numpy()
+    ref = oracle.interior(Uo) + oracle.interior(dU)
+    assert np.array_equal(got, ref)
+    m.substep(2, dt)
+    m.close()
+
+
+def test_sod_32_to_t02_bitwise():
+    """Plain FP64 3D Sod shock tube, 32^3, outflow, CFL 0.4, to t = 0.2."""
+    n = 32
+    U0 = problems.riemann_planar(n, n, n)
+    om, Uo, m = _pair(n, n, n, U0)
+    t = 0.0
+    steps = 0
+    while t < 0.2:
+        dt = m.reduce_dt(0.4)
+        dto, _, _ = oracle.reduce_dt(om, Uo, 0.4)
+        assert dt == dto
+        dt = min(dt, 0.2 - t)
+        m.step(dt)
+        oracle.step(om, Uo, dt)
+        t += dt
+        steps += 1
+    got = m.get_state().cpu().numpy()
+    assert steps > 40
+    assert np.array_equal(got, oracle.interior(Uo))
+    assert np.array_equal(m.get_ghosted_state().cpu().numpy(), Uo)
+    m.close()
+
+
+@pytest.mark.parametrize("theta", [2.0, 1.0])
+def test_oblique_ragged_bitwise(theta):
+    nx, ny, nz = 48, 40, 36
+    om, Uo, m = _pair(nx, ny, nz, problems.riemann_oblique(nx, ny, nz), theta=theta)
+    _run_both(om, Uo, m, 25)
+    assert np.array_equal(m.get_state().cpu().numpy(), oracle.interior(Uo))
+    m.close()
+
+
+def test_periodic_random_bitwise_and_conserved_sums():
+    n = (20, 24, 16)
+    U0 = problems.random_smooth_periodic(*n, seed=3)
+    om, Uo, m = _pair(*n, U0, bc=(PER, PER, PER))
+    _run_both(om, Uo, m, 20)
+    assert np.array_equal(m.get_state().cpu().numpy(), oracle.interior(Uo))
+    assert np.array_equal(m.conserved_sums(), oracle.conserved_sums(om, Uo))
+    m.close()
+
+
+def test_fma_variant_within_1e12():
+    n = 32
+    U0 = problems.riemann_oblique(n, n, n)
+    om, Uo, m = _pair(n, n, n, U0, precision="fp64_fma")
+    for _ in range(60):
+        dt = oracle.reduce_dt(om, Uo, 0.4)[0]
+        m.step(dt)
+        oracle.step(om, Uo, dt)
+    err = _field_rel_err(m.get_state().cpu().numpy(), oracle.interior(Uo))
+    assert np.all(err <= 1e-12), err
+    m.close()
+
+
+def test_face_fallback_count_matches():
+    nx = 8
+    p = np.array([6.0, 6.0, 6.0, 1.0, 1e-20, 1e-20, 1e-20, 1e-20])
+    z = np.zeros(nx)
+    U0 = problems.conserved_from_primitive(np.ones(nx), z, z, z, p).reshape(5, 1, 1, nx)
+    om, Uo, m = _pair(nx, 1, 1, np.ascontiguousarray(U0))
+    dU, bad, fb = oracle.compute_update(om, Uo, 1e-3)
+    m.substep(1, 1e-3)
+    assert np.array_equal(m.get_state().cpu().numpy(), oracle.interior(Uo) + oracle.interior(dU))
+    assert m.counters() == (0, fb) and fb == 1
+    m.close()
+
+
+def test_host_buffers_match_device_buffers():
+    n = (16, 12, 10)
+    U0 = problems.riemann_oblique(*n)
+    from paper_1812_07977_gb300.fv import Mesh
+    a = Mesh(*n)
+    b = Mesh(*n)
+    a.set_state(torch.from_numpy(U0).cuda())
+    b.set_state(U0.copy())                      # numpy host buffer
+    for _ in range(3):
+        dt = a.reduce_dt(0.4)
+        a.step(dt)
+        b.step(b.reduce_dt(0.4))
+    host = np.empty_like(U0)
+    b.get_state(host)
+    pinned = torch.empty(U0.shape, dtype=torch.float64).pin_memory()
+    a.get_state(pinned)
+    assert np.array_equal(host, pinned.numpy())
+    a.close()
+    b.close()
+
+
+def test_nonphysical_state_is_reported():
+    from paper_1812_07977_gb300.fv import FvError, Mesh, ERR_NONPHYSICAL
+    n = (6, 5, 4)
+    U0 = problems.uniform(*n, 1.0, (0.0, 0.0, 0.0), 1.0)
+    U0[4, 1, 2, 3] = -1.0
+    with Mesh(*n) as m:
+        m.set_state(U0)
+        with pytest.raises(FvError) as e:
+            m.reduce_dt(0.4)
+        assert e.value.status == ERR_NONPHYSICAL
+        assert m.counters()[0] == 1
+        m.set_state(problems.uniform(*n, 1.0, (0.0, 0.0, 0.0), 1.0))   # clears the latch
+        assert m.reduce_dt(0.4) > 0
+
+
+def test_call_order_and_handle_errors():
+    from paper_1812_07977_gb300.fv import FvError, Mesh, ERR_INVALID_ARG, ERR_BAD_HANDLE
+    n = (6, 5, 4)
+    m = Mesh(*n)
+    m.set_state(problems.uniform(*n, 1.0, (0.1, 0.0, 0.0), 1.0))
+    m.substep(1, 1e-3)
+    for bad in (lambda: m.step(1e-3), lambda: m.reduce_dt(0.4), lambda: m.substep(1, 1e-3)):
+        with pytest.raises(FvError) as e:
+            bad()
+        assert e.value.status == ERR_INVALID_ARG
+    with pytest.raises(FvError):
+        m.step(float("nan"))
+    m.substep(2, 1e-3)
+    h = m.handle
+    m.close()
+    lib = m._lib
+    assert lib.fv_step(h, 1e-3) == ERR_BAD_HANDLE
+
+
+def test_full_size_256_sampled_windows():
+    """The timed workload (oblique Riemann problem, 256^3, outflow) in the
+    benchmark's launch configuration: after two steps, windows of the GPU
+    state match the oracle run on the sub-box around each window (the
+    result in a window depends only on inputs within 4 cells per step)."""
+    n = 256
+    U0 = problems.riemann_oblique(n, n, n)
+    om_full = oracle.mesh(n, n, n)
+    from paper_1812_07977_gb300.fv import Mesh
+    m = Mesh(n, n, n)
+    m.set_state(torch.from_numpy(U0).cuda())
+    dts = []
+    for _ in range(2):
+        dt = m.reduce_dt(0.4)
+        dts.append(dt)
+        m.step(dt)
+    got = m.get_state().cpu().numpy()
+    m.close()
+    # the first dt against the oracle over the whole mesh
+    dto, _, _ = oracle.reduce_dt(om_full, oracle.ghosted_from_interior(om_full, U0), 0.4)
+    assert dts[0] == dto
+    halo = 4 * len(dts)
+    w = 8
+    starts = [0, 60, 124, 128, 200, n - w]
+    rng = np.random.default_rng(0)
+    windows = [(a, a, a) for a in starts] + [tuple(rng.choice(starts, 3)) for _ in range(4)]
+    for (i0, j0, k0) in windows:
+        lo = [max(0, c - halo) for c in (i0, j0, k0)]
+        hi = [min(n, c + w + halo) for c in (i0, j0, k0)]
+        sub = U0[:, lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]]
+        ns = [hi[a] - lo[a] for a in range(3)]
+        om = oracle.mesh(*ns, lx=ns[0] / n, ly=ns[1] / n, lz=ns[2] / n)
+        Uo = oracle.ghosted_from_interior(om, np.ascontiguousarray(sub))
+        for dt in dts:
+            oracle.step(om, Uo, dt)
+        ref = oracle.interior(Uo)[:, k0 - lo[2]:k0 - lo[2] + w, j0 - lo[1]:j0 - lo[1] + w,
+                                  i0 - lo[0]:i0 - lo[0] + w]
+        win = got[:, k0:k0 + w, j0:j0 + w, i0:i0 + w]
+        assert np.array_equal(win, ref), (i0, j0, k0)
