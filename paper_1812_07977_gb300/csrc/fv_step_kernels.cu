@@ -31,7 +31,8 @@ namespace FV_NS {
 namespace {
 
 constexpr int kPrimThreads = 256;
-constexpr int kSweepThreads = 128;
+constexpr int kSweepThreads = 64;
+constexpr int kSweepMinBlocks = 8;   // 16 warps per SM: at most 128 registers
 
 __global__ void __launch_bounds__(kPrimThreads)
 k_prim(const double* __restrict__ U, double* __restrict__ W, Params P, DevCounters* ctr) {
@@ -87,7 +88,7 @@ __device__ __forceinline__ Prim half_slopes(double theta, const Prim& dm, const 
 // AXIS: 0, 1, 2.  STAGE: 0 for the x and y sweeps; 1 or 2 (the RK stage)
 // for the z sweep, which finishes the update.
 template <int AXIS, int STAGE, int TK>
-__global__ void __launch_bounds__(kSweepThreads)
+__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks)
 k_sweep(const double* __restrict__ W, double* __restrict__ ACC, double* __restrict__ U,
         double* __restrict__ U1, Params P, double dt, DevCounters* ctr) {
   const int n = AXIS == 0 ? P.nx : AXIS == 1 ? P.ny : P.nz;
