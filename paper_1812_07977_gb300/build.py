@@ -19,6 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfvgb.so")
+PROBE = os.path.join(BUILD, "fp64_probe")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -45,16 +46,16 @@ def _sources():
     out = []
     for d in (CSRC, INCLUDE):
         for f in os.listdir(d):
-            if f.endswith((".cu", ".cuh", ".h")):
+            if f.endswith((".cu", ".cuh", ".h")) and f != "fp64_probe.cu":
                 out.append(os.path.join(d, f))
     out.append(os.path.abspath(__file__))
     return out
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PROBE):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PROBE))
     return all(os.path.getmtime(s) <= t for s in _sources())
 
 
@@ -75,8 +76,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+    def compile_probe():
+        cmd = [cc, *ARCH, "-O3", "-std=c++17", os.path.join(CSRC, "fp64_probe.cu"), "-o", PROBE]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on fp64_probe.cu:\n{r.stderr}")
+
+    with ThreadPoolExecutor(max_workers=len(UNITS) + 1) as ex:
+        probe = ex.submit(compile_probe)
         objs = list(ex.map(compile_unit, UNITS))
+        probe.result()
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *[os.path.join(BUILD, o) for o in objs]]
     r = subprocess.run(cmd, capture_output=True, text=True)
