@@ -176,6 +176,35 @@ FV_API fv_status fv_profile_enable(fv_mesh_t m, int on);
  * FV_KERNEL_NCLASS entries; either may be NULL.  Synchronising. */
 FV_API fv_status fv_profile_read(fv_mesh_t m, double* ms, long long* launches);
 
+/* Conservation sums of a caller-held state, allocating nothing.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory -- a host code whose device memory belongs
+ * to its own allocator under a fixed budget, or a time loop that must not
+ * pay cudaMalloc's implicit device-wide synchronisation.  It computes what
+ * fv_conserved_sums computes (the same pairwise tree, identical bits) for a
+ * state the caller already holds, without a mesh.
+ *
+ * U: device pointer (current device) to the dense interior state, 5*nz*ny*nx
+ * doubles [q][k][j][i]; extents lx, ly, lz as in fv_mesh_desc; out: 5 host
+ * doubles.  Work runs on `cuda_stream` (NULL = default stream) and the call
+ * synchronises that stream before returning.
+ *
+ * Scratch: partial sums live in one file-scope device array of 41,008
+ * doubles (about 320 KiB) that every GPU loading this library holds until
+ * the process exits; nothing is allocated or freed per call.  Limit:
+ * nx*ny*nz <= 2^24 (16,777,216 cells, e.g. 256^3); larger states are
+ * rejected with FV_ERR_INVALID_ARG.  Every call fully overwrites the
+ * partials it reads, so nothing needs clearing between calls, but all calls
+ * share the one array: calls whose work overlaps on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.  The first
+ * call on each device looks up the array's device address (with that device
+ * current) and caches it; make that first call before any stream capture.
+ * Errors: INVALID_ARG (NULL pointer, size out of range), CUDA. */
+FV_API fv_status fv_conserved_sums_noalloc(const double* U, int nx, int ny, int nz,
+                                           double lx, double ly, double lz,
+                                           void* cuda_stream, double out[5]);
+
 /* Mesh facts: interior sizes and the byte size of one device state. */
 FV_API fv_status fv_mesh_info(fv_mesh_t m, int dims[3], size_t* state_bytes);
 

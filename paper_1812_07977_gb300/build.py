@@ -32,6 +32,7 @@ UNITS = [
     ("fv_step_fp64_fma.o", "fv_step_kernels.cu", ["--fmad=true", "-DFV_NS=fv_fp64_fma"]),
     ("fv_aux.o", "fv_aux.cu", ["--fmad=false"]),
     ("fv_core.o", "fv_core.cu", ["--fmad=false"]),
+    ("fv_noalloc.o", "fv_noalloc.cu", ["--fmad=false"]),
 ]
 
 

@@ -24,6 +24,12 @@ void set_error(const char* fmt, ...) {
   va_end(ap);
 }
 
+}  // namespace
+
+void fv_internal_set_error(const char* msg) { set_error("%s", msg); }
+
+namespace {
+
 std::mutex g_registry_mutex;
 std::unordered_set<const void*> g_registry;  // live mesh handles
 

@@ -50,3 +50,7 @@ cudaError_t launch_gather_interior(const double* U, double* dense, const fvd::Pa
 size_t sums_work_doubles(const fvd::Params& P);
 cudaError_t launch_pairwise_sums(const double* U, const fvd::Params& P, double* work,
                                  double* out5, cudaStream_t s);
+
+// fv_core.cu: sets the detail string that fv_last_error() returns on the
+// calling thread (for entry points defined outside fv_core.cu).
+void fv_internal_set_error(const char* msg);

@@ -24,7 +24,7 @@ ABI_SYMBOLS = (
     "fv_create_mesh", "fv_destroy_mesh", "fv_set_state", "fv_get_state",
     "fv_get_ghosted_state", "fv_reduce_dt", "fv_step", "fv_substep", "fv_fill_ghosts",
     "fv_conserved_sums", "fv_get_counters", "fv_profile_enable", "fv_profile_read",
-    "fv_mesh_info", "fv_status_string", "fv_last_error",
+    "fv_mesh_info", "fv_status_string", "fv_last_error", "fv_conserved_sums_noalloc",
 )
 KERNEL_CLASSES = ("prim", "sweep_x", "sweep_y", "sweep_z", "ghost", "dt", "other")
 
@@ -73,6 +73,7 @@ def load_library(path: str | None = None):
         "fv_profile_enable": ([vp, i], i),
         "fv_profile_read": ([vp, dp, ctypes.POINTER(ctypes.c_longlong)], i),
         "fv_mesh_info": ([vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)], i),
+        "fv_conserved_sums_noalloc": ([vp, i, i, i, d, d, d, vp, dp], i),
         "fv_status_string": ([i], ctypes.c_char_p),
         "fv_last_error": ([], ctypes.c_char_p),
     }
@@ -245,3 +246,23 @@ class Mesh:
             t += dt
             n += 1
         return t, n, dts
+
+
+def conserved_sums_noalloc(U, lx=1.0, ly=1.0, lz=1.0, stream=None):
+    """Conservation sums of a caller-held (5, nz, ny, nx) float64 CUDA tensor
+    through fv_conserved_sums_noalloc, which allocates no device memory (for
+    callers whose device memory is managed elsewhere)."""
+    torch = _torch()
+    if not (isinstance(U, torch.Tensor) and U.is_cuda and U.dtype == torch.float64
+            and U.is_contiguous() and U.dim() == 4 and U.shape[0] == 5):
+        raise ValueError("U must be a contiguous float64 CUDA tensor of shape (5, nz, ny, nx)")
+    if stream is None:
+        stream = torch.cuda.current_stream(U.device)
+    _, nz, ny, nx = U.shape
+    out = (ctypes.c_double * 5)()
+    lib = load_library()
+    _check(lib.fv_conserved_sums_noalloc(ctypes.c_void_p(U.data_ptr()), nx, ny, nz, float(lx),
+                                         float(ly), float(lz),
+                                         ctypes.c_void_p(stream.cuda_stream), out),
+           "fv_conserved_sums_noalloc")
+    return np.array(out[:])
