@@ -51,6 +51,10 @@ FLOPS_DT = 23            # per interior cell
 # stage 2: stage 1 reads U^n, writes U^1 (80 B); stage 2 reads U^1, U^n and
 # writes U^{n+1} (120 B).
 BYTES_PER_ZONE_UPDATE = 200
+# DRAM bytes (read + write) per sweep launch, mean of the x, y and z sweeps of
+# the FP64-FMA build at 256^3 from one ncu capture
+# (profiles/k_sweep_fp64_fma_oblique256.md); None for builds not captured.
+SWEEP_TRAFFIC = {"fp64_fma": 2.49e9}
 
 
 def fp64_probe():
@@ -218,6 +222,41 @@ def run_reference(args):
     return 0
 
 
+def _timed_run(m, U0_dev, steps, warmup, world, dev, rank, sample_clocks):
+    """Warm up, restart the workload from U0, time `steps` steps with CUDA
+    events on the current stream; returns (ms_max, ms_local, profile, clocks)."""
+    import torch
+
+    def step():
+        m.step(m.reduce_dt(CFL))
+
+    m.set_state(U0_dev)
+    for _ in range(warmup):
+        step()
+    m.set_state(U0_dev)
+    torch.cuda.synchronize()
+    m.profile(True)
+    m.read_profile()
+    sampler = ClockSampler(dev.index)
+    if rank == 0 and sample_clocks:
+        sampler.start()
+    _barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(steps):
+        step()
+    ev1.record()
+    torch.cuda.synchronize()
+    _barrier(world)
+    clocks = sampler.stop() if (rank == 0 and sample_clocks) else None
+    ms = ev0.elapsed_time(ev1)
+    prof = m.read_profile()
+    m.profile(False)
+    return _max_over_ranks(ms, world, dev), ms, prof, clocks
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -234,39 +273,12 @@ def run_ours(args):
     U0 = problems.riemann_oblique(n, n, n)
     U0_dev = torch.from_numpy(U0).to(dev)
     m = Mesh(n, n, n, precision=args.precision)
+    ms_max, ms, prof, clocks = _timed_run(m, U0_dev, args.steps, args.warmup, world, dev, rank,
+                                          True)
+    value = world * zones * args.steps / (ms_max / 1e3)
 
     def step():
-        dt = m.reduce_dt(CFL)
-        m.step(dt)
-
-    # warm-up, then restart the workload from its initial state
-    m.set_state(U0_dev)
-    for _ in range(args.warmup):
-        step()
-    m.set_state(U0_dev)
-    torch.cuda.synchronize()
-    m.profile(True)
-    m.read_profile()
-
-    sampler = ClockSampler(local)
-    if rank == 0:
-        sampler.start()
-    _barrier(world)
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    for _ in range(args.steps):
-        step()
-    ev1.record()
-    torch.cuda.synchronize()
-    _barrier(world)
-    clocks = sampler.stop() if rank == 0 else None
-    ms = ev0.elapsed_time(ev1)
-    prof = m.read_profile()
-    m.profile(False)
-    ms_max = _max_over_ranks(ms, world, dev)
-    value = world * zones * args.steps / (ms_max / 1e3)
+        m.step(m.reduce_dt(CFL))
 
     # end to end through the public API with host buffers: each step copies
     # the state in from pinned host memory and the result back out
@@ -290,6 +302,21 @@ def run_ours(args):
            "steps": args.e2e_steps}
     m.close()
 
+    # the other arithmetic variants of the same step, fewer steps each
+    variants = {}
+    for prec in args.variants:
+        if prec == args.precision:
+            continue
+        mv = Mesh(n, n, n, precision=prec)
+        vms_max, _, vprof, _ = _timed_run(mv, U0_dev, args.variant_steps, args.warmup, world,
+                                          dev, rank, False)
+        mv.close()
+        variants[prec] = {"value": world * zones * args.variant_steps / (vms_max / 1e3),
+                          "ms_per_step": vms_max / args.variant_steps,
+                          "steps": args.variant_steps,
+                          "kernel_ms_per_step": {c: v[0] / args.variant_steps
+                                                 for c, v in vprof.items()}}
+
     if rank != 0:
         return 0
 
@@ -311,7 +338,8 @@ def run_ours(args):
     achieved = sweep_flops / (sweep_ms / 1e3) / 1e12 if sweep_ms > 0 else None
     roofline = {"bound": "alu", "kernel": "k_sweep (x, y, z)", "achieved": achieved,
                 "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak if achieved else None, "traffic": args.traffic,
+                "frac": achieved / fp64_peak if achieved else None,
+                "traffic": args.traffic if args.traffic else SWEEP_TRAFFIC.get(args.precision),
                 "peak_source": peak_source, "derived_peak": derived_peak,
                 "flops_per_launch": sweep_flops / max(sweep_launches, 1),
                 "avg_launch_ms": sweep_ms / max(sweep_launches, 1)}
@@ -337,6 +365,7 @@ def run_ours(args):
                          "note": "whole step vs the algorithmic minimum traffic, of measured"},
         "fp64_flop_rate_whole_step_tflops": total_flops_step * args.steps / (ms / 1e3) / 1e12,
         "kernel_ms_per_step": {c: v[0] / args.steps for c, v in prof.items()},
+        "variants": variants,
         "gpu_launches": launches,
         "fp64_probe": probe,
         "e2e": e2e,
@@ -354,7 +383,10 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp64_fma"])
+    ap.add_argument("--precision", default="fp64_fma", choices=["fp64", "fp64_fma"])
+    ap.add_argument("--variants", nargs="*", default=["fp64"],
+                    help="other precisions timed beside the headline one")
+    ap.add_argument("--variant-steps", type=int, default=50)
     ap.add_argument("--n", type=int, default=N)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--traffic", type=float, default=None,
