@@ -70,7 +70,16 @@ typedef enum { FV_BC_OUTFLOW = 0, FV_BC_PERIODIC = 1 } fv_bc;
  *  FV_PREC_FP64_FMA  FP64 with fused multiply-add contraction: the same
  *                    method, a few ulp per operation away from FV_PREC_FP64.
  */
-typedef enum { FV_PREC_FP64 = 0, FV_PREC_FP64_FMA = 1 } fv_precision;
+/*  FV_PREC_FP32_BULK FP64 state, FP32 bulk arithmetic: reconstruction, wave
+ *                    speeds, HLL fluxes and the flux divergence in FP32 (one
+ *                    fused kernel per substep); the RK combine adds the FP32
+ *                    update to the FP64 state in FP64; the pressure of cells
+ *                    whose kinetic energy exceeds 99% of E is recovered in
+ *                    FP64; the CFL maximum is exact and dt = cfl / max is
+ *                    formed in FP64 (per-cell signal speeds in FP32);
+ *                    conservation sums as FV_PREC_FP64.
+ */
+typedef enum { FV_PREC_FP64 = 0, FV_PREC_FP64_FMA = 1, FV_PREC_FP32_BULK = 2 } fv_precision;
 
 typedef struct {
   int nx, ny, nz;       /* interior cells per axis, each >= 1 */
@@ -154,14 +163,15 @@ FV_API fv_status fv_get_counters(fv_mesh_t m, long long* nonphysical_cells,
 
 /* Kernel classes of the profiling hooks below. */
 typedef enum {
-  FV_KERNEL_PRIM = 0,     /* conserved -> primitive */
+  FV_KERNEL_PRIM = 0,     /* conserved -> primitive (FP64 paths) */
   FV_KERNEL_SWEEP_X = 1,  /* differences, reconstruction, HLL fluxes, update: x */
   FV_KERNEL_SWEEP_Y = 2,  /* the same along y */
   FV_KERNEL_SWEEP_Z = 3,  /* the same along z, with the RK combine */
-  FV_KERNEL_GHOST = 4,    /* ghost fill */
-  FV_KERNEL_DT = 5,       /* CFL time-step reduction */
-  FV_KERNEL_OTHER = 6,    /* state copies and conservation sums */
-  FV_KERNEL_NCLASS = 7
+  FV_KERNEL_FUSED = 4,    /* the whole substep in one kernel (FP32-bulk path) */
+  FV_KERNEL_GHOST = 5,    /* ghost fill */
+  FV_KERNEL_DT = 6,       /* CFL time-step reduction */
+  FV_KERNEL_OTHER = 7,    /* state copies and conservation sums */
+  FV_KERNEL_NCLASS = 8
 } fv_kernel_class;
 
 /* Per-kernel timing on (on != 0) or off.  While on, every kernel launch of
@@ -204,6 +214,16 @@ FV_API fv_status fv_profile_read(fv_mesh_t m, double* ms, long long* launches);
 FV_API fv_status fv_conserved_sums_noalloc(const double* U, int nx, int ny, int nz,
                                            double lx, double ly, double lz,
                                            void* cuda_stream, double out[5]);
+
+/* Tuning knobs (not part of the paper).
+ *  FV_TUNE_KCHUNK        z planes per CTA of the fused FP32-bulk kernel
+ *                        (integer >= 1; default 64, or nz when nz < 128)
+ *  FV_TUNE_VACUUM_RATIO  FP32-bulk: recover the pressure in FP64 where the
+ *                        kinetic energy exceeds this fraction of E (default
+ *                        0.99; a value > 1 turns the recovery off)
+ * Errors: INVALID_ARG for an unknown key or a value out of range. */
+typedef enum { FV_TUNE_KCHUNK = 0, FV_TUNE_VACUUM_RATIO = 1 } fv_tuning_key;
+FV_API fv_status fv_set_tuning(fv_mesh_t m, int key, double value);
 
 /* Mesh facts: interior sizes and the byte size of one device state. */
 FV_API fv_status fv_mesh_info(fv_mesh_t m, int dims[3], size_t* state_bytes);

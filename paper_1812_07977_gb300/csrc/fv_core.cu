@@ -48,6 +48,8 @@ struct fv_mesh_s {
   DevCounters* host_ctr;    // pinned mirror of the device counters
   double* host_sums;        // pinned, 5 doubles
   int stage_pending;        // 1 after fv_substep(1) until fv_substep(2)
+  int kchunk;               // z planes per CTA of the fused FP32-bulk kernel
+  double vacuum_ratio;      // FP32-bulk FP64 pressure-recovery threshold
   // profiling
   bool prof_on;
   std::vector<cudaEvent_t> event_pool;
@@ -124,7 +126,8 @@ fv_status validate_desc(const fv_mesh_desc* d) {
     set_error("theta %g outside [0, 2]", d->theta);
     return FV_ERR_INVALID_ARG;
   }
-  if (d->precision != FV_PREC_FP64 && d->precision != FV_PREC_FP64_FMA) {
+  if (d->precision != FV_PREC_FP64 && d->precision != FV_PREC_FP64_FMA &&
+      d->precision != FV_PREC_FP32_BULK) {
     set_error("precision %d unknown", d->precision);
     return FV_ERR_INVALID_ARG;
   }
@@ -222,6 +225,15 @@ cudaError_t timed(fv_mesh_t m, int cls, int nlaunch, F&& launch) {
 }
 
 cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
+  if (m->desc.precision == FV_PREC_FP32_BULK) {
+    cudaError_t e = timed(m, FV_KERNEL_FUSED, 1, [&] {
+      return fv_fp32::launch_stage(stage, m->buf, m->P, dt, m->kchunk, m->vacuum_ratio,
+                                   m->stream);
+    });
+    if (e != cudaSuccess) return e;
+    double* dst = stage == 1 ? m->buf.U1 : m->buf.U;
+    return timed(m, FV_KERNEL_GHOST, 1, [&] { return launch_fill_ghosts(dst, m->P, m->stream); });
+  }
   const bool fma = m->desc.precision == FV_PREC_FP64_FMA;
   const double* src = stage == 1 ? m->buf.U : m->buf.U1;
   cudaError_t e = timed(m, FV_KERNEL_PRIM, 1, [&] {
@@ -259,6 +271,8 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   m->stream = (cudaStream_t)cuda_stream;
   m->stage_pending = 0;
   m->prof_on = false;
+  m->kchunk = desc->nz >= 128 ? 64 : desc->nz;
+  m->vacuum_ratio = 0.99;
   for (int c = 0; c < FV_KERNEL_NCLASS; ++c) m->launches[c] = 0;
   cudaError_t e = cudaGetDevice(&m->device);
   if (e != cudaSuccess) {
@@ -272,7 +286,7 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   const size_t wb = sums_work_doubles(m->P) * sizeof(double);
   if ((e = cudaMalloc(&m->buf.U, sb)) != cudaSuccess ||
       (e = cudaMalloc(&m->buf.U1, sb)) != cudaSuccess ||
-      (e = cudaMalloc(&m->buf.W, sb)) != cudaSuccess ||
+      (desc->precision != FV_PREC_FP32_BULK && (e = cudaMalloc(&m->buf.W, sb)) != cudaSuccess) ||
       (e = cudaMalloc(&m->buf.ACC, db)) != cudaSuccess ||
       (e = cudaMalloc(&m->buf.ctr, sizeof(DevCounters))) != cudaSuccess ||
       (e = cudaMalloc(&m->sums_work, wb)) != cudaSuccess ||
@@ -393,8 +407,12 @@ fv_status fv_reduce_dt(fv_mesh_t m, double cfl, double* dt_out) {
     return FV_ERR_INVALID_ARG;
   }
   DeviceGuard g(m->device);
-  cudaError_t e = timed(m, FV_KERNEL_DT, 1,
-                        [&] { return launch_reduce_dt(m->buf.U, m->P, m->buf.ctr, m->stream); });
+  cudaError_t e = timed(m, FV_KERNEL_DT, 1, [&] {
+    return m->desc.precision == FV_PREC_FP32_BULK
+               ? fv_fp32::launch_reduce_dt(m->buf.U, m->P, m->vacuum_ratio, m->buf.ctr,
+                                           m->stream)
+               : launch_reduce_dt(m->buf.U, m->P, m->buf.ctr, m->stream);
+  });
   if (e != cudaSuccess) return cuda_fail(e, "time-step kernel");
   if ((st = read_counters(m)) != FV_OK) return st;
   double smax;
@@ -480,6 +498,29 @@ fv_status fv_get_counters(fv_mesh_t m, long long* nonphysical_cells, long long* 
     *nonphysical_cells = (long long)(m->host_ctr->np_step + m->host_ctr->np_dt);
   if (fallback_faces) *fallback_faces = (long long)m->host_ctr->fallback;
   return FV_OK;
+}
+
+fv_status fv_set_tuning(fv_mesh_t m, int key, double value) {
+  fv_status st = check_handle(m);
+  if (st != FV_OK) return st;
+  if (key == FV_TUNE_KCHUNK) {
+    if (!(value >= 1.0 && value <= 1 << 20) || value != (double)(int)value) {
+      set_error("FV_TUNE_KCHUNK must be an integer >= 1 (got %g)", value);
+      return FV_ERR_INVALID_ARG;
+    }
+    m->kchunk = (int)value;
+    return FV_OK;
+  }
+  if (key == FV_TUNE_VACUUM_RATIO) {
+    if (!(value > 0.0) || !std::isfinite(value)) {
+      set_error("FV_TUNE_VACUUM_RATIO must be finite and > 0 (got %g)", value);
+      return FV_ERR_INVALID_ARG;
+    }
+    m->vacuum_ratio = value;
+    return FV_OK;
+  }
+  set_error("unknown tuning key %d", key);
+  return FV_ERR_INVALID_ARG;
 }
 
 fv_status fv_profile_enable(fv_mesh_t m, int on) {

@@ -1,0 +1,147 @@
+// fv_device32.cuh -- FP32 building blocks of the FP32-bulk step.
+//
+// The FP32-bulk arithmetic keeps the state in FP64 (the RK combine adds the
+// FP32 update to the FP64 state; the pressure of near-vacuum cells is
+// recovered in FP64) and does reconstruction and fluxes in FP32.  On sm_103a
+// the double<->float conversions issue on the FP64 pipe, at the FP64 rate
+// (2 per SM per clock), so they are done here on the integer pipe instead:
+// d2f / f2d return exactly what the IEEE conversions return (round to
+// nearest even), taking the hardware conversion only outside the float
+// normal range.
+#pragma once
+
+#include <cstdint>
+
+#include "fv_device.cuh"
+
+namespace fvd32 {
+
+using fvd::NF;
+
+// double -> float, round to nearest even
+__device__ __forceinline__ float d2f(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  if (e - 897u < 254u) {  // result exponent 1..254 (a carry may round to inf)
+    unsigned field = ((e - 896u) << 23) | ((hi & 0x000FFFFFu) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1FFFFFFFu;
+    field += (unsigned)(rem > 0x10000000u) | ((unsigned)(rem == 0x10000000u) & (field & 1u));
+    return __uint_as_float(field | (hi & 0x80000000u));
+  }
+  if ((b << 1) == 0ULL) return __uint_as_float(hi & 0x80000000u);  // +-0
+  return __double2float_rn(x);  // tiny, huge, inf or NaN
+}
+
+// float -> double (exact)
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned x = __float_as_uint(f);
+  const unsigned ex = (x >> 23) & 0xFFu;
+  if (ex - 1u < 254u) {  // normal
+    const unsigned hi = (((x & 0x7FFFFFFFu) >> 3) + (896u << 20)) | (x & 0x80000000u);
+    return __hiloint2double((int)hi, (int)(x << 29));
+  }
+  if ((x << 1) == 0u) return __hiloint2double((int)(x & 0x80000000u), 0);  // +-0
+  return (double)f;  // subnormal, inf or NaN
+}
+
+// Approximate reciprocal (one MUFU.RCP, within 2 ulp): the FP32-bulk
+// arithmetic is judged by its error against FP64, not bit for bit.
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+
+struct Prim32 { float r, vx, vy, vz, p; };
+
+struct Params32 {
+  float gamma, gm1, igm1, theta;
+  float inv_d[3];
+  double gm1_d;             // gamma - 1 in FP64 (near-vacuum pressure recovery)
+  float vacuum_ratio;       // recover p in FP64 when kinetic / total energy > this
+};
+
+// Primitive state of one cell from its FP64 conserved state.  The pressure
+// p = (gamma-1)(E - ke) cancels when the kinetic energy is nearly all of E;
+// there it is recomputed in FP64 from the FP64 state.
+__device__ __forceinline__ Prim32 prim_from_state(const double u[NF], const Params32& Q) {
+  Prim32 w;
+  const float r = d2f(u[0]), mx = d2f(u[1]), my = d2f(u[2]), mz = d2f(u[3]), E = d2f(u[4]);
+  const float ir = rcp(r);
+  w.r = r;
+  w.vx = mx * ir;
+  w.vy = my * ir;
+  w.vz = mz * ir;
+  const float ke = 0.5f * (mx * w.vx + my * w.vy + mz * w.vz);
+  w.p = Q.gm1 * (E - ke);
+  if (ke > Q.vacuum_ratio * E) {
+    const double ked = 0.5 * ((u[1] * u[1] + u[2] * u[2]) + u[3] * u[3]) / u[0];
+    w.p = d2f(Q.gm1_d * (u[4] - ked));
+  }
+  return w;
+}
+
+// minmod(a, b, c): the argument of least magnitude when all three share a
+// strict sign, else 0:  s * max(0, min(s*a, s*b, s*c)) with s = sign(a).
+__device__ __forceinline__ float minmod3(float a, float b, float c) {
+  const float s = copysignf(1.0f, a);
+  return s * fmaxf(0.0f, fminf(fminf(s * a, s * b), s * c));
+}
+
+__device__ __forceinline__ float half_slope(float theta, float dm, float dp) {
+  return 0.5f * minmod3(theta * dm, 0.5f * (dm + dp), theta * dp);
+}
+
+__device__ __forceinline__ bool physical(const Prim32& w) { return w.r > 0.0f && w.p > 0.0f; }
+
+__device__ __forceinline__ Prim32 operator+(const Prim32& a, const Prim32& b) {
+  return Prim32{a.r + b.r, a.vx + b.vx, a.vy + b.vy, a.vz + b.vz, a.p + b.p};
+}
+__device__ __forceinline__ Prim32 operator-(const Prim32& a, const Prim32& b) {
+  return Prim32{a.r - b.r, a.vx - b.vx, a.vy - b.vy, a.vz - b.vz, a.p - b.p};
+}
+
+__device__ __forceinline__ Prim32 half_slopes(float theta, const Prim32& dm, const Prim32& dp) {
+  return Prim32{half_slope(theta, dm.r, dp.r), half_slope(theta, dm.vx, dp.vx),
+                half_slope(theta, dm.vy, dp.vy), half_slope(theta, dm.vz, dp.vz),
+                half_slope(theta, dm.p, dp.p)};
+}
+
+// HLL flux normal to AXIS from face states wl, wr (the FP64 method's
+// formulas in FP32, with approximate reciprocal and square root):
+// F = wL FL + wR FR - wD (UR - UL), wL = a+ r, wR = a- r, wD = a+ a- r,
+// r = 1 / (a+ + a-).
+template <int AXIS>
+__device__ __forceinline__ void hll_flux(const Prim32& wl, const Prim32& wr, const Params32& Q,
+                                         float F[NF]) {
+  float UL[NF], UR[NF], FL[NF], FR[NF], c[2], vn[2];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const Prim32& w = s == 0 ? wl : wr;
+    float* U = s == 0 ? UL : UR;
+    float* Fs = s == 0 ? FL : FR;
+    const float mx = w.r * w.vx, my = w.r * w.vy, mz = w.r * w.vz;
+    const float ke = 0.5f * (mx * w.vx + my * w.vy + mz * w.vz);
+    U[0] = w.r;
+    U[1] = mx;
+    U[2] = my;
+    U[3] = mz;
+    U[4] = w.p * Q.igm1 + ke;
+    const float v = AXIS == 0 ? w.vx : AXIS == 1 ? w.vy : w.vz;
+    const float mn = AXIS == 0 ? mx : AXIS == 1 ? my : mz;
+    vn[s] = v;
+    const float c2 = Q.gamma * w.p * rcp(w.r);
+    c[s] = c2 * rsqrtf(c2);
+    Fs[0] = mn;
+    Fs[1] = mn * w.vx;
+    Fs[2] = mn * w.vy;
+    Fs[3] = mn * w.vz;
+    Fs[1 + AXIS] += w.p;
+    Fs[4] = (U[4] + w.p) * v;
+  }
+  const float ap = fmaxf(0.0f, fmaxf(vn[0] + c[0], vn[1] + c[1]));
+  const float am = fmaxf(0.0f, fmaxf(c[0] - vn[0], c[1] - vn[1]));
+  const float r = rcp(ap + am);
+  const float wL = ap * r, wR = am * r, wD = ap * am * r;
+#pragma unroll
+  for (int q = 0; q < NF; ++q) F[q] = wL * FL[q] + wR * FR[q] - wD * (UR[q] - UL[q]);
+}
+
+}  // namespace fvd32

@@ -37,6 +37,15 @@ struct StepBuffers {
 FV_DECLARE_STEP_VARIANT(fv_fp64_exact)
 FV_DECLARE_STEP_VARIANT(fv_fp64_fma)
 
+// fv_step32_kernels.cu: the FP32-bulk substep (one fused kernel; z chunks
+// of `kchunk` planes per CTA) and its CFL reduction.
+namespace fv_fp32 {
+cudaError_t launch_stage(int stage, const StepBuffers& b, const fvd::Params& P, double dt,
+                         int kchunk, double vacuum_ratio, cudaStream_t s);
+cudaError_t launch_reduce_dt(const double* U, const fvd::Params& P, double vacuum_ratio,
+                             DevCounters* ctr, cudaStream_t s);
+}
+
 // fv_aux.cu (always built without contraction)
 cudaError_t launch_fill_ghosts(double* U, const fvd::Params& P, cudaStream_t s);
 cudaError_t launch_reduce_dt(const double* U, const fvd::Params& P, DevCounters* ctr,

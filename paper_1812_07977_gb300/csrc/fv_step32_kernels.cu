@@ -1,0 +1,305 @@
+// fv_step32_kernels.cu -- one RK2 substep of the FP32-bulk method, fused.
+//
+// One kernel per substep does all of Algorithm 1's substep kernels
+// (ComputeDifferences, ComputeReconstruction, RiemannSolverInput,
+// ComputeFluxes, ComputeUpdate and the RK combine) for a tile of 32 x 8
+// columns marching along z over a chunk of planes, so each substep reads
+// its input state once (plus the tile's two-cell halo) and writes its output
+// once: 120-200 B of FP64 state traffic per zone-update instead of the
+// ~1 KB of the FP64 path's separate sweeps.
+//
+// Per plane k, each thread owns one column (i, j) of the tile:
+//   z  : a register window along its column (primitives of planes k..k+2,
+//        the z differences and half slopes of planes k, k+1, and the z
+//        flux of face k-1/2 carried from the previous plane) gives the z
+//        flux of face k+1/2 -- every z flux computed once;
+//   x,y: the plane's primitives (tile plus two-cell halo) go to shared
+//        memory; the 33 x 8 x-faces and 32 x 9 y-faces are computed once
+//        each (slopes of both neighbours recomputed per face) into shared
+//        memory;
+//   update: dU = dt * (-(Fx(i+1/2)-Fx(i-1/2))/dx - (..)/dy - (..)/dz) in FP32,
+//        then the RK combine in FP64 on the FP64 state.
+#include "fv_device32.cuh"
+#include "fv_internal.h"
+
+using namespace fvd32;
+
+namespace fv_fp32 {
+namespace {
+
+constexpr int TX = 32;
+constexpr int TY = 8;
+constexpr int kThreads = TX * TY;
+constexpr int PX = TX + 4;                  // plane buffer with a two-cell halo
+constexpr int PY = TY + 4;
+constexpr int kHalo = PX * PY - TX * TY;    // 176 halo cells per plane
+constexpr int kXFaces = (TX + 1) * TY;      // 264
+constexpr int kYFaces = TX * (TY + 1);      // 288
+
+struct Smem {
+  float w[NF][PY][PX];
+  float fx[NF][TY][TX + 1];
+  float fy[NF][TY + 1][TX];
+};
+
+__device__ __forceinline__ void load_state(const double* __restrict__ U, long long nf,
+                                           long long off, double u[NF]) {
+#pragma unroll
+  for (int q = 0; q < NF; ++q) u[q] = U[q * nf + off];
+}
+
+__device__ __forceinline__ Prim32 load_prim(const double* __restrict__ U, long long nf,
+                                            long long off, const Params32& Q) {
+  double u[NF];
+  load_state(U, nf, off, u);
+  return prim_from_state(u, Q);
+}
+
+__device__ __forceinline__ Prim32 smem_prim(const Smem& s, int row, int col) {
+  return Prim32{s.w[0][row][col], s.w[1][row][col], s.w[2][row][col], s.w[3][row][col],
+                s.w[4][row][col]};
+}
+
+__device__ __forceinline__ void smem_store(Smem& s, int row, int col, const Prim32& w) {
+  s.w[0][row][col] = w.r;
+  s.w[1][row][col] = w.vx;
+  s.w[2][row][col] = w.vy;
+  s.w[3][row][col] = w.vz;
+  s.w[4][row][col] = w.p;
+}
+
+// Face flux between cells a1 and a2 given the four cells a0..a3 along the
+// face normal; falls back to first order if a face state is non-physical.
+template <int AXIS>
+__device__ __forceinline__ void face_flux(const Prim32& a0, const Prim32& a1, const Prim32& a2,
+                                          const Prim32& a3, const Params32& Q, float F[NF],
+                                          unsigned& fallbacks) {
+  const Prim32 d0 = a1 - a0, d1 = a2 - a1, d2 = a3 - a2;
+  Prim32 wl = a1 + half_slopes(Q.theta, d0, d1);
+  Prim32 wr = a2 - half_slopes(Q.theta, d1, d2);
+  if (!(physical(wl) && physical(wr))) {
+    wl = a1;
+    wr = a2;
+    ++fallbacks;
+  }
+  hll_flux<AXIS>(wl, wr, Q, F);
+}
+
+// STAGE 1: U1 = U + dU.  STAGE 2: U = ((U + U1) + dU) / 2.  The input of the
+// substep (U for stage 1, U1 for stage 2) has its ghosts filled.
+template <int STAGE>
+__global__ void __launch_bounds__(kThreads, 2)
+k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params32 Q, float dt,
+          int kchunk, DevCounters* ctr) {
+  __shared__ Smem s;
+  const double* __restrict__ src = STAGE == 1 ? U : U1;
+  const int tid = threadIdx.x;
+  const int ti = tid % TX, tj = tid / TX;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int k0 = blockIdx.z * kchunk;
+  const int k1 = min(k0 + kchunk, P.nz);
+  const long long nf = P.nfield;
+  // this thread's column, clamped into the ghosted array (columns past a
+  // ragged edge compute unused values and store nothing)
+  const int gi = min(i0 + ti, P.nx + 1), gj = min(j0 + tj, P.ny + 1);
+  const bool owner = (i0 + ti < P.nx) && (j0 + tj < P.ny);
+  const long long col = (long long)(gj + 2) * P.sy + (gi + 2);
+  // the halo cell this thread loads each plane (threads 0..175)
+  int hrow = 0, hcol = 0;
+  if (tid < kHalo) {
+    if (tid < 2 * PX) {
+      hrow = tid / PX - 2;
+      hcol = tid % PX - 2;
+    } else if (tid < 4 * PX) {
+      hrow = TY + (tid - 2 * PX) / PX;
+      hcol = (tid - 2 * PX) % PX - 2;
+    } else {
+      const int u = tid - 4 * PX;
+      hrow = u / 4;
+      const int c = u % 4;
+      hcol = c < 2 ? c - 2 : TX + c - 2;
+    }
+  }
+  const int hgi = min(i0 + hcol, P.nx + 1), hgj = min(j0 + hrow, P.ny + 1);
+  const long long hcolo = (long long)(hgj + 2) * P.sy + (hgi + 2);
+
+  unsigned fallbacks = 0;
+  const float idx = Q.inv_d[0], idy = Q.inv_d[1], idz = Q.inv_d[2];
+
+  // z window prologue: planes k0-2 .. k0+1
+  Prim32 wm2 = load_prim(src, nf, col + (long long)(k0 + 0) * P.sz, Q);   // plane k0-2
+  Prim32 wm1 = load_prim(src, nf, col + (long long)(k0 + 1) * P.sz, Q);   // plane k0-1
+  Prim32 w0 = load_prim(src, nf, col + (long long)(k0 + 2) * P.sz, Q);    // plane k0
+  Prim32 w1 = load_prim(src, nf, col + (long long)(k0 + 3) * P.sz, Q);    // plane k0+1
+  Prim32 d1 = w1 - w0;                                                    // D(k0+1)
+  Prim32 h0 = half_slopes(Q.theta, w0 - wm1, d1);                         // cell k0
+  float fz_lo[NF];
+  {
+    Prim32 hm1 = half_slopes(Q.theta, wm1 - wm2, w0 - wm1);               // cell k0-1
+    Prim32 wl = wm1 + hm1, wr = w0 - h0;
+    if (!(physical(wl) && physical(wr))) {
+      wl = wm1;
+      wr = w0;
+      ++fallbacks;
+    }
+    hll_flux<2>(wl, wr, Q, fz_lo);
+  }
+  // the first chunk's lower face is the domain boundary face; later chunks
+  // recompute a face the previous chunk counted
+  if (k0 != 0 || !owner) fallbacks = 0;
+  unsigned long long bad = 0;
+
+  for (int k = k0; k < k1; ++k) {
+    if (owner && !physical(w0)) ++bad;   // each interior cell once per substep
+    // (a) z: plane k+2 enters the window; flux of face k+1/2
+    const Prim32 w2 = load_prim(src, nf, col + (long long)(k + 4) * P.sz, Q);
+    const Prim32 d2 = w2 - w1;
+    const Prim32 h1 = half_slopes(Q.theta, d1, d2);
+    float fz_hi[NF];
+    {
+      Prim32 wl = w0 + h0, wr = w1 - h1;
+      if (!(physical(wl) && physical(wr))) {
+        wl = w0;
+        wr = w1;
+        if (owner) ++fallbacks;
+      }
+      hll_flux<2>(wl, wr, Q, fz_hi);
+    }
+    // (b) the plane's primitives into shared memory
+    smem_store(s, tj + 2, ti + 2, w0);
+    if (tid < kHalo)
+      smem_store(s, hrow + 2, hcol + 2, load_prim(src, nf, hcolo + (long long)(k + 2) * P.sz, Q));
+    __syncthreads();
+    // (c) x faces: face fi (between columns fi-1 and fi) of row r
+    for (int f = tid; f < kXFaces; f += kThreads) {
+      const int r = f / (TX + 1), fi = f % (TX + 1);
+      float F[NF];
+      unsigned fb = 0;
+      face_flux<0>(smem_prim(s, r + 2, fi), smem_prim(s, r + 2, fi + 1),
+                   smem_prim(s, r + 2, fi + 2), smem_prim(s, r + 2, fi + 3), Q, F, fb);
+      if (i0 + fi <= P.nx && j0 + r < P.ny) fallbacks += fb;
+#pragma unroll
+      for (int q = 0; q < NF; ++q) s.fx[q][r][fi] = F[q];
+    }
+    // (d) y faces: face fj (between rows fj-1 and fj) of column c
+    for (int f = tid; f < kYFaces; f += kThreads) {
+      const int fj = f / TX, c = f % TX;
+      float F[NF];
+      unsigned fb = 0;
+      face_flux<1>(smem_prim(s, fj, c + 2), smem_prim(s, fj + 1, c + 2),
+                   smem_prim(s, fj + 2, c + 2), smem_prim(s, fj + 3, c + 2), Q, F, fb);
+      if (i0 + c < P.nx && j0 + fj <= P.ny) fallbacks += fb;
+#pragma unroll
+      for (int q = 0; q < NF; ++q) s.fy[q][fj][c] = F[q];
+    }
+    __syncthreads();
+    // (e) update of cell (i, j, k): FP32 divergence, FP64 RK combine
+    if (owner) {
+      const long long g = col + (long long)(k + 2) * P.sz;
+#pragma unroll
+      for (int q = 0; q < NF; ++q) {
+        const float acc = -(s.fx[q][tj][ti + 1] - s.fx[q][tj][ti]) * idx -
+                          (s.fy[q][tj + 1][ti] - s.fy[q][tj][ti]) * idy -
+                          (fz_hi[q] - fz_lo[q]) * idz;
+        const double du = f2d(dt * acc);
+        if (STAGE == 1) {
+          U1[q * nf + g] = U[q * nf + g] + du;
+        } else {
+          U[q * nf + g] = fvd::half((U[q * nf + g] + U1[q * nf + g]) + du);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NF; ++q) fz_lo[q] = fz_hi[q];
+    w0 = w1;
+    w1 = w2;
+    d1 = d2;
+    h0 = h1;
+  }
+  if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
+  if (bad) atomicAdd(&ctr->np_step, bad);
+}
+
+// CFL signal speed per interior cell in FP32 from the FP64 state; the
+// maximum is taken exactly (non-negative floats order like their bits) and
+// handed over as the bits of the equal double; dt = cfl / max is formed in
+// FP64 on the host.
+__global__ void __launch_bounds__(256)
+k_reduce_dt32(const double* __restrict__ U, fvd::Params P, Params32 Q, DevCounters* ctr) {
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  unsigned smax = 0;
+  unsigned long long bad = 0;
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < n;
+       m += (long long)gridDim.x * blockDim.x) {
+    const long long k = m / ((long long)P.nx * P.ny);
+    const long long r = m - k * ((long long)P.nx * P.ny);
+    const long long j = r / P.nx, i = r - j * P.nx;
+    double u[NF];
+    load_state(U, P.nfield, (k + 2) * P.sz + (j + 2) * P.sy + (i + 2), u);
+    const Prim32 w = prim_from_state(u, Q);
+    if (!physical(w)) {
+      ++bad;
+      continue;
+    }
+    const float c2 = Q.gamma * w.p * rcp(w.r);
+    const float c = c2 * rsqrtf(c2);
+    const float sp = (fabsf(w.vx) + c) * Q.inv_d[0] + (fabsf(w.vy) + c) * Q.inv_d[1] +
+                     (fabsf(w.vz) + c) * Q.inv_d[2];
+    const unsigned b = __float_as_uint(sp);
+    if (sp > 0.0f && b < 0x7F800000u && b > smax) smax = b;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+  __shared__ unsigned wmax[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) wmax[wid] = smax;
+  if (bad) atomicAdd(&ctr->np_dt, bad);
+  __syncthreads();
+  if (wid == 0) {
+    smax = lane < 8 ? wmax[lane] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+    if (lane == 0 && smax)
+      atomicMax(&ctr->smax_bits,
+                (unsigned long long)__double_as_longlong(f2d(__uint_as_float(smax))));
+  }
+}
+
+}  // namespace
+
+Params32 make_params32(const fvd::Params& P, double vacuum_ratio) {
+  Params32 Q;
+  Q.gamma = (float)P.gamma;
+  Q.gm1 = (float)P.gm1;
+  Q.igm1 = (float)P.igm1;
+  Q.theta = (float)P.theta;
+  for (int a = 0; a < 3; ++a) Q.inv_d[a] = (float)P.inv_d[a];
+  Q.gm1_d = P.gm1;
+  Q.vacuum_ratio = (float)vacuum_ratio;
+  return Q;
+}
+
+cudaError_t launch_stage(int stage, const StepBuffers& b, const fvd::Params& P, double dt,
+                         int kchunk, double vacuum_ratio, cudaStream_t s) {
+  const Params32 Q = make_params32(P, vacuum_ratio);
+  if (kchunk < 1) kchunk = 1;
+  const dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + kchunk - 1) / kchunk);
+  if (stage == 1)
+    k_stage32<1><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, (float)dt, kchunk, b.ctr);
+  else
+    k_stage32<2><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, (float)dt, kchunk, b.ctr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_dt(const double* U, const fvd::Params& P, double vacuum_ratio,
+                             DevCounters* ctr, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(&ctr->smax_bits, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_reduce_dt32<<<(unsigned)blocks, 256, 0, s>>>(U, P, make_params32(P, vacuum_ratio), ctr);
+  return cudaGetLastError();
+}
+
+}  // namespace fv_fp32

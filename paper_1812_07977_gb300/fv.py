@@ -17,16 +17,17 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfvgb.so")
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_BAD_HANDLE = range(7)
 BC = {"outflow": 0, "periodic": 1}
-PRECISION = {"fp64": 0, "fp64_fma": 1}
+PRECISION = {"fp64": 0, "fp64_fma": 1, "fp32_bulk": 2}
 
 # Every entry point declared in include/fv.h.
 ABI_SYMBOLS = (
     "fv_create_mesh", "fv_destroy_mesh", "fv_set_state", "fv_get_state",
     "fv_get_ghosted_state", "fv_reduce_dt", "fv_step", "fv_substep", "fv_fill_ghosts",
-    "fv_conserved_sums", "fv_get_counters", "fv_profile_enable", "fv_profile_read",
+    "fv_conserved_sums", "fv_get_counters", "fv_set_tuning", "fv_profile_enable",
+    "fv_profile_read",
     "fv_mesh_info", "fv_status_string", "fv_last_error", "fv_conserved_sums_noalloc",
 )
-KERNEL_CLASSES = ("prim", "sweep_x", "sweep_y", "sweep_z", "ghost", "dt", "other")
+KERNEL_CLASSES = ("prim", "sweep_x", "sweep_y", "sweep_z", "fused", "ghost", "dt", "other")
 
 
 class FvError(RuntimeError):
@@ -70,6 +71,7 @@ def load_library(path: str | None = None):
         "fv_conserved_sums": ([vp, dp], i),
         "fv_get_counters": ([vp, ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(ctypes.c_longlong)], i),
+        "fv_set_tuning": ([vp, i, d], i),
         "fv_profile_enable": ([vp, i], i),
         "fv_profile_read": ([vp, dp, ctypes.POINTER(ctypes.c_longlong)], i),
         "fv_mesh_info": ([vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)], i),
@@ -217,6 +219,10 @@ class Mesh:
         _check(self._lib.fv_get_counters(self._h, ctypes.byref(a), ctypes.byref(b)),
                "fv_get_counters")
         return a.value, b.value
+
+    def set_tuning(self, key: str, value):
+        keys = {"kchunk": 0, "vacuum_ratio": 1}
+        _check(self._lib.fv_set_tuning(self._h, keys[key], float(value)), "fv_set_tuning")
 
     def profile(self, on: bool = True):
         _check(self._lib.fv_profile_enable(self._h, int(bool(on))), "fv_profile_enable")
