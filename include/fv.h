@@ -217,12 +217,14 @@ FV_API fv_status fv_conserved_sums_noalloc(const double* U, int nx, int ny, int 
 
 /* Tuning knobs (not part of the paper).
  *  FV_TUNE_KCHUNK        z planes per CTA of the fused FP32-bulk kernel
- *                        (integer >= 1; default 64, or nz when nz < 128)
+ *                        (integer >= 1; default 32, or nz when nz < 64)
  *  FV_TUNE_VACUUM_RATIO  FP32-bulk: recover the pressure in FP64 where the
  *                        kinetic energy exceeds this fraction of E (default
  *                        0.99; a value > 1 turns the recovery off)
+ *  FV_TUNE_OCCUPANCY     CTAs per SM the fused FP32-bulk kernel is built for:
+ *                        2 (up to 128 registers, default) or 3 (80 registers)
  * Errors: INVALID_ARG for an unknown key or a value out of range. */
-typedef enum { FV_TUNE_KCHUNK = 0, FV_TUNE_VACUUM_RATIO = 1 } fv_tuning_key;
+typedef enum { FV_TUNE_KCHUNK = 0, FV_TUNE_VACUUM_RATIO = 1, FV_TUNE_OCCUPANCY = 2 } fv_tuning_key;
 FV_API fv_status fv_set_tuning(fv_mesh_t m, int key, double value);
 
 /* Mesh facts: interior sizes and the byte size of one device state. */

@@ -50,6 +50,7 @@ struct fv_mesh_s {
   int stage_pending;        // 1 after fv_substep(1) until fv_substep(2)
   int kchunk;               // z planes per CTA of the fused FP32-bulk kernel
   double vacuum_ratio;      // FP32-bulk FP64 pressure-recovery threshold
+  int occupancy;            // CTAs per SM the fused kernel is compiled for (2 or 3)
   // profiling
   bool prof_on;
   std::vector<cudaEvent_t> event_pool;
@@ -228,7 +229,7 @@ cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
   if (m->desc.precision == FV_PREC_FP32_BULK) {
     cudaError_t e = timed(m, FV_KERNEL_FUSED, 1, [&] {
       return fv_fp32::launch_stage(stage, m->buf, m->P, dt, m->kchunk, m->vacuum_ratio,
-                                   m->stream);
+                                   m->occupancy, m->stream);
     });
     if (e != cudaSuccess) return e;
     double* dst = stage == 1 ? m->buf.U1 : m->buf.U;
@@ -271,8 +272,9 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   m->stream = (cudaStream_t)cuda_stream;
   m->stage_pending = 0;
   m->prof_on = false;
-  m->kchunk = desc->nz >= 128 ? 64 : desc->nz;
+  m->kchunk = desc->nz >= 64 ? 32 : desc->nz;
   m->vacuum_ratio = 0.99;
+  m->occupancy = 2;
   for (int c = 0; c < FV_KERNEL_NCLASS; ++c) m->launches[c] = 0;
   cudaError_t e = cudaGetDevice(&m->device);
   if (e != cudaSuccess) {
@@ -517,6 +519,14 @@ fv_status fv_set_tuning(fv_mesh_t m, int key, double value) {
       return FV_ERR_INVALID_ARG;
     }
     m->vacuum_ratio = value;
+    return FV_OK;
+  }
+  if (key == FV_TUNE_OCCUPANCY) {
+    if (value != 2.0 && value != 3.0) {
+      set_error("FV_TUNE_OCCUPANCY must be 2 or 3 (got %g)", value);
+      return FV_ERR_INVALID_ARG;
+    }
+    m->occupancy = (int)value;
     return FV_OK;
   }
   set_error("unknown tuning key %d", key);

@@ -41,7 +41,7 @@ FV_DECLARE_STEP_VARIANT(fv_fp64_fma)
 // of `kchunk` planes per CTA) and its CFL reduction.
 namespace fv_fp32 {
 cudaError_t launch_stage(int stage, const StepBuffers& b, const fvd::Params& P, double dt,
-                         int kchunk, double vacuum_ratio, cudaStream_t s);
+                         int kchunk, double vacuum_ratio, int occupancy, cudaStream_t s);
 cudaError_t launch_reduce_dt(const double* U, const fvd::Params& P, double vacuum_ratio,
                              DevCounters* ctr, cudaStream_t s);
 }

@@ -87,8 +87,8 @@ __device__ __forceinline__ void face_flux(const Prim32& a0, const Prim32& a1, co
 
 // STAGE 1: U1 = U + dU.  STAGE 2: U = ((U + U1) + dU) / 2.  The input of the
 // substep (U for stage 1, U1 for stage 2) has its ghosts filled.
-template <int STAGE>
-__global__ void __launch_bounds__(kThreads, 2)
+template <int STAGE, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
 k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params32 Q, float dt,
           int kchunk, DevCounters* ctr) {
   __shared__ Smem s;
@@ -149,10 +149,36 @@ k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params
   if (k0 != 0 || !owner) fallbacks = 0;
   unsigned long long bad = 0;
 
+  // raw FP64 state of the next column plane (k+2) and halo cell (plane k),
+  // loaded one iteration ahead so their latency overlaps the face work
+  double next_col[NF], next_halo[NF];
+  load_state(src, nf, col + (long long)(k0 + 4) * P.sz, next_col);
+  if (tid < kHalo) load_state(src, nf, hcolo + (long long)(k0 + 2) * P.sz, next_halo);
+
   for (int k = k0; k < k1; ++k) {
     if (owner && !physical(w0)) ++bad;   // each interior cell once per substep
+    double cur_col[NF], cur_halo[NF];
+#pragma unroll
+    for (int q = 0; q < NF; ++q) {
+      cur_col[q] = next_col[q];
+      cur_halo[q] = next_halo[q];
+    }
+    if (k + 1 < k1) {
+      load_state(src, nf, col + (long long)(k + 5) * P.sz, next_col);
+      if (tid < kHalo) load_state(src, nf, hcolo + (long long)(k + 3) * P.sz, next_halo);
+    }
+    // operands of this plane's RK combine, loaded before the face work
+    double rk0[NF], rk1[NF];
+    const long long g = col + (long long)(k + 2) * P.sz;
+    if (owner) {
+#pragma unroll
+      for (int q = 0; q < NF; ++q) {
+        rk0[q] = U[q * nf + g];
+        rk1[q] = STAGE == 2 ? U1[q * nf + g] : 0.0;
+      }
+    }
     // (a) z: plane k+2 enters the window; flux of face k+1/2
-    const Prim32 w2 = load_prim(src, nf, col + (long long)(k + 4) * P.sz, Q);
+    const Prim32 w2 = prim_from_state(cur_col, Q);
     const Prim32 d2 = w2 - w1;
     const Prim32 h1 = half_slopes(Q.theta, d1, d2);
     float fz_hi[NF];
@@ -167,8 +193,7 @@ k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params
     }
     // (b) the plane's primitives into shared memory
     smem_store(s, tj + 2, ti + 2, w0);
-    if (tid < kHalo)
-      smem_store(s, hrow + 2, hcol + 2, load_prim(src, nf, hcolo + (long long)(k + 2) * P.sz, Q));
+    if (tid < kHalo) smem_store(s, hrow + 2, hcol + 2, prim_from_state(cur_halo, Q));
     __syncthreads();
     // (c) x faces: face fi (between columns fi-1 and fi) of row r
     for (int f = tid; f < kXFaces; f += kThreads) {
@@ -195,7 +220,6 @@ k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params
     __syncthreads();
     // (e) update of cell (i, j, k): FP32 divergence, FP64 RK combine
     if (owner) {
-      const long long g = col + (long long)(k + 2) * P.sz;
 #pragma unroll
       for (int q = 0; q < NF; ++q) {
         const float acc = -(s.fx[q][tj][ti + 1] - s.fx[q][tj][ti]) * idx -
@@ -203,9 +227,9 @@ k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params
                           (fz_hi[q] - fz_lo[q]) * idz;
         const double du = f2d(dt * acc);
         if (STAGE == 1) {
-          U1[q * nf + g] = U[q * nf + g] + du;
+          U1[q * nf + g] = rk0[q] + du;
         } else {
-          U[q * nf + g] = fvd::half((U[q * nf + g] + U1[q * nf + g]) + du);
+          U[q * nf + g] = fvd::half((rk0[q] + rk1[q]) + du);
         }
       }
     }
@@ -280,14 +304,18 @@ Params32 make_params32(const fvd::Params& P, double vacuum_ratio) {
 }
 
 cudaError_t launch_stage(int stage, const StepBuffers& b, const fvd::Params& P, double dt,
-                         int kchunk, double vacuum_ratio, cudaStream_t s) {
+                         int kchunk, double vacuum_ratio, int occupancy, cudaStream_t s) {
   const Params32 Q = make_params32(P, vacuum_ratio);
   if (kchunk < 1) kchunk = 1;
   const dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + kchunk - 1) / kchunk);
-  if (stage == 1)
-    k_stage32<1><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, (float)dt, kchunk, b.ctr);
-  else
-    k_stage32<2><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, (float)dt, kchunk, b.ctr);
+  const float fdt = (float)dt;
+  if (occupancy == 3) {  // 3 CTAs per SM: 80 registers, a few spills
+    if (stage == 1) k_stage32<1, 3><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+    else k_stage32<2, 3><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+  } else {               // 2 CTAs per SM: up to 128 registers
+    if (stage == 1) k_stage32<1, 2><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+    else k_stage32<2, 2><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+  }
   return cudaGetLastError();
 }
 
