@@ -18,6 +18,20 @@ namespace fvd32 {
 
 using fvd::NF;
 
+// Hardware conversions for the rare operands.  As volatile asm they stay
+// behind their branch; a plain conversion would be if-converted by the
+// compiler and issued on the FP64 pipe for every value.
+__device__ __forceinline__ float d2f_rare(double x) {
+  float r;
+  asm volatile("cvt.rn.f32.f64 %0, %1;" : "=f"(r) : "d"(x));
+  return r;
+}
+__device__ __forceinline__ double f2d_rare(float x) {
+  double r;
+  asm volatile("cvt.f64.f32 %0, %1;" : "=d"(r) : "f"(x));
+  return r;
+}
+
 // double -> float, round to nearest even
 __device__ __forceinline__ float d2f(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -30,7 +44,7 @@ __device__ __forceinline__ float d2f(double x) {
     return __uint_as_float(field | (hi & 0x80000000u));
   }
   if ((b << 1) == 0ULL) return __uint_as_float(hi & 0x80000000u);  // +-0
-  return __double2float_rn(x);  // tiny, huge, inf or NaN
+  return d2f_rare(x);  // tiny, huge, inf or NaN
 }
 
 // float -> double (exact)
@@ -42,7 +56,7 @@ __device__ __forceinline__ double f2d(float f) {
     return __hiloint2double((int)hi, (int)(x << 29));
   }
   if ((x << 1) == 0u) return __hiloint2double((int)(x & 0x80000000u), 0);  // +-0
-  return (double)f;  // subnormal, inf or NaN
+  return f2d_rare(f);  // subnormal, inf or NaN
 }
 
 // Approximate reciprocal (one MUFU.RCP, within 2 ulp): the FP32-bulk
@@ -58,6 +72,12 @@ struct Params32 {
   float vacuum_ratio;       // recover p in FP64 when kinetic / total energy > this
 };
 
+// p = (gamma-1)(E - |m|^2 / (2 rho)) in FP64, rounded to float.
+__device__ __forceinline__ float pressure_fp64(const double u[NF], double gm1) {
+  const double ked = 0.5 * ((u[1] * u[1] + u[2] * u[2]) + u[3] * u[3]) / u[0];
+  return d2f(gm1 * (u[4] - ked));
+}
+
 // Primitive state of one cell from its FP64 conserved state.  The pressure
 // p = (gamma-1)(E - ke) cancels when the kinetic energy is nearly all of E;
 // there it is recomputed in FP64 from the FP64 state.
@@ -71,10 +91,7 @@ __device__ __forceinline__ Prim32 prim_from_state(const double u[NF], const Para
   w.vz = mz * ir;
   const float ke = 0.5f * (mx * w.vx + my * w.vy + mz * w.vz);
   w.p = Q.gm1 * (E - ke);
-  if (ke > Q.vacuum_ratio * E) {
-    const double ked = 0.5 * ((u[1] * u[1] + u[2] * u[2]) + u[3] * u[3]) / u[0];
-    w.p = d2f(Q.gm1_d * (u[4] - ked));
-  }
+  if (ke > Q.vacuum_ratio * E) w.p = pressure_fp64(u, Q.gm1_d);
   return w;
 }
 
