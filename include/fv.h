@@ -186,6 +186,54 @@ FV_API fv_status fv_profile_enable(fv_mesh_t m, int on);
  * FV_KERNEL_NCLASS entries; either may be NULL.  Synchronising. */
 FV_API fv_status fv_profile_read(fv_mesh_t m, double* ms, long long* launches);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent meshes of uneven sizes advanced together.
+ * Not in the paper (whose ranks each own one subdomain): the on-device
+ * analogue of many independent RiemannProblem runs.  Every mesh of a batch
+ * uses the FP32-bulk arithmetic (FV_PREC_FP32_BULK; the precision field of
+ * the descriptions is ignored) and its own CFL time step.  One step is:
+ * per-mesh dt = cfl / max signal speed (on the device, FP64 division), then
+ * the two RK substeps, each ONE persistent launch over the work items
+ * (mesh, 32x8 tile, z chunk) of all meshes, each followed by the ghost fill.
+ * ------------------------------------------------------------------------ */
+typedef struct fv_batch_s* fv_batch_t;
+
+/* Allocate a batch of `nmesh` meshes (each description validated as for
+ * fv_create_mesh).  `cuda_stream` NULL: the batch creates its own
+ * non-blocking stream (needed for graph capture).  Synchronous.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+FV_API fv_status fv_batch_create(const fv_mesh_desc* descs, int nmesh, void* cuda_stream,
+                                 fv_batch_t* out);
+FV_API fv_status fv_batch_destroy(fv_batch_t b);
+
+/* Interior state of mesh `mesh` in or out, layout as fv_set_state. */
+FV_API fv_status fv_batch_set_state(fv_batch_t b, int mesh, const double* U, int on_device);
+FV_API fv_status fv_batch_get_state(fv_batch_t b, int mesh, double* U, int on_device);
+
+/* One step of every mesh with its own dt = cfl / (its maximum signal
+ * speed).  use_graph != 0: the whole step (CFL reductions, both substeps and
+ * ghost fills) is captured once into a CUDA graph and replayed (re-captured
+ * when cfl or the tuning changes).  Asynchronous. */
+FV_API fv_status fv_batch_step(fv_batch_t b, double cfl, int use_graph);
+
+/* The dt each mesh used in the last step (nmesh doubles).  Synchronising. */
+FV_API fv_status fv_batch_get_dt(fv_batch_t b, double* dt);
+
+/* Launch configuration: z planes per work item and CTAs per SM (2 or 3). */
+FV_API fv_status fv_batch_set_tuning(fv_batch_t b, int kchunk, int occupancy);
+
+/* Autotuner: times one step for each z chunk in {8, 16, 32, 64} and each
+ * occupancy in {2, 3} on the batch's current state, keeps the fastest and
+ * reports it.  The state and counters are restored afterwards (a snapshot
+ * buffer of one state is allocated on first use).  Synchronising. */
+FV_API fv_status fv_batch_autotune(fv_batch_t b, double cfl, int* kchunk, int* occupancy,
+                                   double* ms_per_step);
+
+FV_API fv_status fv_batch_get_counters(fv_batch_t b, long long* nonphysical_cells,
+                                       long long* fallback_faces);
+FV_API fv_status fv_batch_info(fv_batch_t b, int* nmesh, long long* total_cells,
+                               long long* work_items);
+
 /* Conservation sums of a caller-held state, allocating nothing.
  *
  * The paper has no counterpart: this entry point exists for callers that

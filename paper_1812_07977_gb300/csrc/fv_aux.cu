@@ -19,50 +19,12 @@ inline unsigned grid_for(long long n) {
 }
 
 // ---------------------------------------------------------------- ghosts
-// The axis-by-axis fill (x, then y, then z, each over the full ghosted
-// extent of the other axes) leaves every ghost cell equal to the interior
-// cell (src_x(i), src_y(j), src_z(k)), so each ring cell is written once,
-// straight from its source.  Ring cells are enumerated as the z slabs
-// (4 full planes), the y slabs of the interior planes, and the x slabs of
-// the interior rows.
 __global__ void __launch_bounds__(kThreads)
 k_fill_ghosts(double* __restrict__ U, Params P) {
-  const long long X = P.nx + 4, Y = P.ny + 4;
-  const long long nz_slab = 4 * Y * X;
-  const long long ny_slab = 4 * (long long)P.nz * X;
-  const long long nx_slab = 4 * (long long)P.nz * P.ny;
-  const long long total = nz_slab + ny_slab + nx_slab;
+  const long long total = ring_cells(P);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    int i, j, k;
-    if (t < nz_slab) {
-      const long long s = t / (Y * X), r = t - s * (Y * X);
-      k = s < 2 ? (int)s - 2 : P.nz + (int)s - 2;
-      j = (int)(r / X) - 2;
-      i = (int)(r % X) - 2;
-    } else if (t < nz_slab + ny_slab) {
-      const long long u = t - nz_slab;
-      const long long kk = u / (4 * X), r = u - kk * (4 * X);
-      const int s = (int)(r / X);
-      k = (int)kk;
-      j = s < 2 ? s - 2 : P.ny + s - 2;
-      i = (int)(r % X) - 2;
-    } else {
-      const long long u = t - nz_slab - ny_slab;
-      const long long row = u / 4;
-      const int s = (int)(u - row * 4);
-      k = (int)(row / P.ny);
-      j = (int)(row % P.ny);
-      i = s < 2 ? s - 2 : P.nx + s - 2;
-    }
-    const int si = ghost_source(i, P.nx, P.bc[0]);
-    const int sj = ghost_source(j, P.ny, P.bc[1]);
-    const int sk = ghost_source(k, P.nz, P.bc[2]);
-    const long long dst = (k + 2) * P.sz + (j + 2) * P.sy + (i + 2);
-    const long long src = (sk + 2) * P.sz + (sj + 2) * P.sy + (si + 2);
-#pragma unroll
-    for (int q = 0; q < NF; ++q) U[q * P.nfield + dst] = U[q * P.nfield + src];
-  }
+       t += (long long)gridDim.x * blockDim.x)
+    fill_ghost_cell(U, P, t);
 }
 
 // ---------------------------------------------------------------- time step
@@ -211,9 +173,7 @@ long long next_pow2(long long n) {
 }  // namespace
 
 cudaError_t launch_fill_ghosts(double* U, const Params& P, cudaStream_t s) {
-  const long long X = P.nx + 4, Y = P.ny + 4;
-  const long long total = 4 * Y * X + 4 * (long long)P.nz * X + 4 * (long long)P.nz * P.ny;
-  k_fill_ghosts<<<grid_for(total), kThreads, 0, s>>>(U, P);
+  k_fill_ghosts<<<grid_for(ring_cells(P)), kThreads, 0, s>>>(U, P);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,455 @@
+// fv_batch.cu -- the C ABI of mesh batches (include/fv.h, "Batches"):
+// many independent meshes of uneven sizes advanced together by the
+// FP32-bulk step, one persistent launch per RK substep, the whole step
+// optionally replayed from a CUDA graph, and an autotuner for the launch
+// configuration.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <unordered_set>
+#include <vector>
+
+#include "fv.h"
+#include "fv_internal.h"
+
+namespace {
+
+std::mutex g_batch_mutex;
+std::unordered_set<const void*> g_batches;
+
+fv_status fail(fv_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  fv_internal_set_error(buf);
+  return st;
+}
+
+fv_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(FV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+}  // namespace
+
+struct fv_batch_s {
+  int nmesh = 0;
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<fv_mesh_desc> desc;
+  std::vector<BatchMesh> host_meshes;
+  long long total_cells = 0;
+  size_t state_doubles = 0;          // all meshes, ghosted
+  size_t max_dense = 0;              // largest mesh, dense interior doubles
+  BatchDevice dev{};
+  double* staging = nullptr;         // dense interior staging for host copies
+  double* backup = nullptr;          // state snapshot used by the autotuner
+  DevCounters* host_ctr = nullptr;
+  int kchunk = 32;
+  int occupancy = 2;
+  // CUDA graph of one whole step
+  cudaGraphExec_t graph = nullptr;
+  double graph_cfl = -1.0;
+  int graph_kchunk = -1, graph_occupancy = -1;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+fv_status check(fv_batch_t b) {
+  if (!b) return fail(FV_ERR_BAD_HANDLE, "NULL batch handle");
+  std::lock_guard<std::mutex> lk(g_batch_mutex);
+  if (!g_batches.count(b)) return fail(FV_ERR_BAD_HANDLE, "batch handle %p is not live", (void*)b);
+  return FV_OK;
+}
+
+void free_batch(fv_batch_s* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  cudaFree(b->dev.U);
+  cudaFree(b->dev.U1);
+  cudaFree(b->dev.meshes);
+  cudaFree(b->dev.items);
+  cudaFree(b->dev.dt_blocks);
+  cudaFree(b->dev.ghost_blocks);
+  cudaFree(b->dev.next_item);
+  cudaFree(b->dev.ctr);
+  cudaFree(b->staging);
+  cudaFree(b->backup);
+  cudaFreeHost(b->host_ctr);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+// Fused-kernel work items for a z chunk: every (mesh, tile x, tile y, chunk),
+// largest meshes first so the tail of the persistent launch is short.
+fv_status build_items(fv_batch_t b, int kchunk) {
+  if (b->graph) {  // the captured step refers to the item table being replaced
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  std::vector<int> order(b->nmesh);
+  for (int m = 0; m < b->nmesh; ++m) order[m] = m;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    const fvd::Params &A = b->host_meshes[a].P, &C = b->host_meshes[c].P;
+    return (long long)A.nx * A.ny * A.nz > (long long)C.nx * C.ny * C.nz;
+  });
+  std::vector<int4> items;
+  for (int m : order) {
+    const fvd::Params& P = b->host_meshes[m].P;
+    const int tx = (P.nx + fv_fp32::kTileX - 1) / fv_fp32::kTileX;
+    const int ty = (P.ny + fv_fp32::kTileY - 1) / fv_fp32::kTileY;
+    const int tz = (P.nz + kchunk - 1) / kchunk;
+    for (int z = 0; z < tz; ++z)
+      for (int y = 0; y < ty; ++y)
+        for (int x = 0; x < tx; ++x) items.push_back(make_int4(m, x, y, z));
+  }
+  cudaFree(b->dev.items);
+  b->dev.items = nullptr;
+  cudaError_t e = cudaMalloc(&b->dev.items, items.size() * sizeof(int4));
+  if (e != cudaSuccess) return cuda_fail(e, "allocating work items");
+  e = cudaMemcpy(b->dev.items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "uploading work items");
+  b->dev.nitems = (int)items.size();
+  b->kchunk = kchunk;
+  return FV_OK;
+}
+
+cudaError_t launch_step(fv_batch_t b, double cfl) {
+  cudaError_t e = fv_fp32::launch_batch_dt(b->dev, cfl, b->stream);
+  for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage) {
+    e = fv_fp32::launch_batch_stage(stage, b->dev, b->kchunk, b->occupancy, b->num_sms,
+                                    b->stream);
+    if (e == cudaSuccess) e = fv_fp32::launch_batch_ghosts(stage, b->dev, b->stream);
+  }
+  return e;
+}
+
+fv_status check_mesh_index(fv_batch_t b, int mesh) {
+  if (mesh < 0 || mesh >= b->nmesh)
+    return fail(FV_ERR_INVALID_ARG, "mesh index %d outside [0, %d)", mesh, b->nmesh);
+  return FV_OK;
+}
+
+double* mesh_base(fv_batch_t b, double* base, int mesh) {
+  return base + b->host_meshes[mesh].offset;
+}
+
+}  // namespace
+
+extern "C" {
+
+fv_status fv_batch_create(const fv_mesh_desc* descs, int nmesh, void* cuda_stream,
+                          fv_batch_t* out) {
+  if (!out) return fail(FV_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!descs || nmesh < 1 || nmesh > (1 << 16))
+    return fail(FV_ERR_INVALID_ARG, "need 1 .. 65536 mesh descriptions (got %d)", nmesh);
+  for (int m = 0; m < nmesh; ++m) {
+    fv_status st = fv_internal_validate_desc(&descs[m]);
+    if (st != FV_OK) return st;
+  }
+  fv_batch_s* b = new fv_batch_s();
+  b->nmesh = nmesh;
+  b->desc.assign(descs, descs + nmesh);
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "querying the device");
+  }
+  if (cuda_stream) {
+    b->stream = (cudaStream_t)cuda_stream;
+  } else {  // a stream of our own: the legacy default stream cannot be captured
+    e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete b;
+      return cuda_fail(e, "creating the batch stream");
+    }
+    b->own_stream = true;
+  }
+  // per-mesh parameters and 256-byte aligned offsets into one state block
+  size_t off = 0;
+  std::vector<int2> dt_blocks, ghost_blocks;
+  for (int m = 0; m < nmesh; ++m) {
+    BatchMesh bm{};
+    bm.P = fv_internal_params(&descs[m]);
+    bm.Q = fv_fp32::make_params32(bm.P, 0.99);
+    bm.offset = (long long)off;
+    const size_t doubles = (size_t)fvd::NF * bm.P.nfield;
+    off += (doubles + 31) / 32 * 32;
+    const long long n = (long long)bm.P.nx * bm.P.ny * bm.P.nz;
+    b->total_cells += n;
+    b->max_dense = std::max(b->max_dense, (size_t)(fvd::NF * n));
+    for (long long c = 0; c * fv_fp32::kBatchDtChunk < n; ++c) dt_blocks.push_back(make_int2(m, (int)c));
+    const long long ring = fvd::ring_cells(bm.P);
+    for (long long c = 0; c * fv_fp32::kBatchGhostChunk < ring; ++c)
+      ghost_blocks.push_back(make_int2(m, (int)c));
+    b->host_meshes.push_back(bm);
+  }
+  b->state_doubles = off;
+  const size_t sb = off * sizeof(double);
+  if ((e = cudaMalloc(&b->dev.U, sb)) != cudaSuccess ||
+      (e = cudaMalloc(&b->dev.U1, sb)) != cudaSuccess ||
+      (e = cudaMalloc(&b->dev.meshes, nmesh * sizeof(BatchMesh))) != cudaSuccess ||
+      (e = cudaMalloc(&b->dev.dt_blocks, dt_blocks.size() * sizeof(int2))) != cudaSuccess ||
+      (e = cudaMalloc(&b->dev.ghost_blocks, ghost_blocks.size() * sizeof(int2))) != cudaSuccess ||
+      (e = cudaMalloc(&b->dev.next_item, 2 * sizeof(unsigned))) != cudaSuccess ||
+      (e = cudaMalloc(&b->dev.ctr, sizeof(DevCounters))) != cudaSuccess ||
+      (e = cudaMalloc(&b->staging, b->max_dense * sizeof(double))) != cudaSuccess ||
+      (e = cudaMallocHost(&b->host_ctr, sizeof(DevCounters))) != cudaSuccess) {
+    cudaGetLastError();
+    free_batch(b);
+    return fail(e == cudaErrorMemoryAllocation ? FV_ERR_OOM : FV_ERR_CUDA,
+                "allocating %.3f GB of batch storage: %s", 2.0 * sb / 1e9, cudaGetErrorString(e));
+  }
+  b->dev.nmesh = nmesh;
+  b->dev.ndt_blocks = (int)dt_blocks.size();
+  b->dev.nghost_blocks = (int)ghost_blocks.size();
+  if ((e = cudaMemcpy(b->dev.meshes, b->host_meshes.data(), nmesh * sizeof(BatchMesh),
+                      cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->dev.dt_blocks, dt_blocks.data(), dt_blocks.size() * sizeof(int2),
+                      cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->dev.ghost_blocks, ghost_blocks.data(), ghost_blocks.size() * sizeof(int2),
+                      cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(b->dev.U, 0, sb)) != cudaSuccess ||
+      (e = cudaMemset(b->dev.U1, 0, sb)) != cudaSuccess ||
+      (e = cudaMemset(b->dev.ctr, 0, sizeof(DevCounters))) != cudaSuccess) {
+    free_batch(b);
+    return cuda_fail(e, "initialising batch storage");
+  }
+  fv_status st = build_items(b, 32);
+  if (st != FV_OK) {
+    free_batch(b);
+    return st;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mutex);
+    g_batches.insert(b);
+  }
+  *out = b;
+  return FV_OK;
+}
+
+fv_status fv_batch_destroy(fv_batch_t b) {
+  if (!b) return FV_OK;
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mutex);
+    if (!g_batches.erase(b)) return fail(FV_ERR_BAD_HANDLE, "batch handle %p is not live", (void*)b);
+  }
+  DeviceGuard g(b->device);
+  cudaStreamSynchronize(b->stream);
+  free_batch(b);
+  return FV_OK;
+}
+
+fv_status fv_batch_set_state(fv_batch_t b, int mesh, const double* U, int on_device) {
+  fv_status st = check(b);
+  if (st == FV_OK) st = check_mesh_index(b, mesh);
+  if (st != FV_OK) return st;
+  if (!U) return fail(FV_ERR_INVALID_ARG, "U is NULL");
+  DeviceGuard g(b->device);
+  const fvd::Params& P = b->host_meshes[mesh].P;
+  const size_t dense = (size_t)fvd::NF * P.nx * P.ny * P.nz;
+  cudaError_t e = cudaSuccess;
+  const double* src = U;
+  if (!on_device) {
+    e = cudaMemcpyAsync(b->staging, U, dense * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+    src = b->staging;
+  }
+  double* dst = mesh_base(b, b->dev.U, mesh);
+  if (e == cudaSuccess) e = launch_scatter_interior(src, dst, P, b->stream);
+  if (e == cudaSuccess) e = launch_fill_ghosts(dst, P, b->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "fv_batch_set_state");
+  return FV_OK;
+}
+
+fv_status fv_batch_get_state(fv_batch_t b, int mesh, double* U, int on_device) {
+  fv_status st = check(b);
+  if (st == FV_OK) st = check_mesh_index(b, mesh);
+  if (st != FV_OK) return st;
+  if (!U) return fail(FV_ERR_INVALID_ARG, "U is NULL");
+  DeviceGuard g(b->device);
+  const fvd::Params& P = b->host_meshes[mesh].P;
+  const size_t dense = (size_t)fvd::NF * P.nx * P.ny * P.nz;
+  double* dst = on_device ? U : b->staging;
+  cudaError_t e = launch_gather_interior(mesh_base(b, b->dev.U, mesh), dst, P, b->stream);
+  if (e == cudaSuccess && !on_device)
+    e = cudaMemcpyAsync(U, b->staging, dense * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "fv_batch_get_state");
+  return FV_OK;
+}
+
+fv_status fv_batch_step(fv_batch_t b, double cfl, int use_graph) {
+  fv_status st = check(b);
+  if (st != FV_OK) return st;
+  if (!(cfl > 0.0) || !std::isfinite(cfl)) return fail(FV_ERR_INVALID_ARG, "cfl %g must be > 0", cfl);
+  DeviceGuard g(b->device);
+  cudaError_t e;
+  if (!use_graph) {
+    e = launch_step(b, cfl);
+    if (e != cudaSuccess) return cuda_fail(e, "batch step kernels");
+    return FV_OK;
+  }
+  if (!b->graph || b->graph_cfl != cfl || b->graph_kchunk != b->kchunk ||
+      b->graph_occupancy != b->occupancy) {
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "beginning the step capture");
+    cudaError_t le = launch_step(b, cfl);
+    e = cudaStreamEndCapture(b->stream, &graph);
+    if (le != cudaSuccess || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(le != cudaSuccess ? le : e, "capturing the step");
+    }
+    e = cudaGraphInstantiate(&b->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      b->graph = nullptr;
+      return cuda_fail(e, "instantiating the step graph");
+    }
+    b->graph_cfl = cfl;
+    b->graph_kchunk = b->kchunk;
+    b->graph_occupancy = b->occupancy;
+  }
+  e = cudaGraphLaunch(b->graph, b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the step graph");
+  return FV_OK;
+}
+
+fv_status fv_batch_get_dt(fv_batch_t b, double* dt) {
+  fv_status st = check(b);
+  if (st != FV_OK) return st;
+  if (!dt) return fail(FV_ERR_INVALID_ARG, "dt is NULL");
+  DeviceGuard g(b->device);
+  std::vector<BatchMesh> tmp(b->nmesh);
+  cudaError_t e = cudaMemcpyAsync(tmp.data(), b->dev.meshes, b->nmesh * sizeof(BatchMesh),
+                                  cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reading dt");
+  for (int m = 0; m < b->nmesh; ++m) dt[m] = tmp[m].dt;
+  return FV_OK;
+}
+
+fv_status fv_batch_set_tuning(fv_batch_t b, int kchunk, int occupancy) {
+  fv_status st = check(b);
+  if (st != FV_OK) return st;
+  if (kchunk < 1 || kchunk > 4096 || (occupancy != 2 && occupancy != 3))
+    return fail(FV_ERR_INVALID_ARG, "kchunk %d must be in [1, 4096] and occupancy 2 or 3",
+                kchunk, occupancy);
+  DeviceGuard g(b->device);
+  cudaStreamSynchronize(b->stream);
+  if (kchunk != b->kchunk && (st = build_items(b, kchunk)) != FV_OK) return st;
+  b->occupancy = occupancy;
+  return FV_OK;
+}
+
+fv_status fv_batch_autotune(fv_batch_t b, double cfl, int* kchunk_out, int* occupancy_out,
+                            double* ms_per_step_out) {
+  fv_status st = check(b);
+  if (st != FV_OK) return st;
+  if (!(cfl > 0.0)) return fail(FV_ERR_INVALID_ARG, "cfl must be > 0");
+  DeviceGuard g(b->device);
+  const size_t sb = b->state_doubles * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  if (!b->backup && (e = cudaMalloc(&b->backup, sb)) != cudaSuccess)
+    return cuda_fail(e, "allocating the autotuner's state snapshot");
+  DevCounters saved{};
+  if ((e = cudaMemcpyAsync(b->backup, b->dev.U, sb, cudaMemcpyDeviceToDevice, b->stream)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(&saved, b->dev.ctr, sizeof saved, cudaMemcpyDeviceToHost, b->stream)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
+    return cuda_fail(e, "snapshotting the state");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int kcs[] = {8, 16, 32, 64};
+  const int occs[] = {2, 3};
+  double best = 1e300;
+  int best_kc = b->kchunk, best_occ = b->occupancy;
+  for (int kc : kcs) {
+    if ((st = build_items(b, kc)) != FV_OK) break;
+    for (int occ : occs) {
+      b->occupancy = occ;
+      e = launch_step(b, cfl);  // warm-up
+      cudaEventRecord(e0, b->stream);
+      for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_step(b, cfl);
+      cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms / 3.0 < best) {
+        best = ms / 3.0;
+        best_kc = kc;
+        best_occ = occ;
+      }
+    }
+    if (e != cudaSuccess) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == FV_OK && e == cudaSuccess) st = build_items(b, best_kc);
+  b->occupancy = best_occ;
+  // restore the state (ghosts included) and the counters
+  cudaError_t r = cudaMemcpyAsync(b->dev.U, b->backup, sb, cudaMemcpyDeviceToDevice, b->stream);
+  if (r == cudaSuccess)
+    r = cudaMemcpyAsync(b->dev.ctr, &saved, sizeof saved, cudaMemcpyHostToDevice, b->stream);
+  if (r == cudaSuccess) r = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "autotuning");
+  if (r != cudaSuccess) return cuda_fail(r, "restoring the state after autotuning");
+  if (st != FV_OK) return st;
+  if (kchunk_out) *kchunk_out = best_kc;
+  if (occupancy_out) *occupancy_out = best_occ;
+  if (ms_per_step_out) *ms_per_step_out = best;
+  return FV_OK;
+}
+
+fv_status fv_batch_get_counters(fv_batch_t b, long long* nonphysical_cells,
+                                long long* fallback_faces) {
+  fv_status st = check(b);
+  if (st != FV_OK) return st;
+  DeviceGuard g(b->device);
+  cudaError_t e = cudaMemcpyAsync(b->host_ctr, b->dev.ctr, sizeof(DevCounters),
+                                  cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reading batch counters");
+  if (nonphysical_cells)
+    *nonphysical_cells = (long long)(b->host_ctr->np_step + b->host_ctr->np_dt);
+  if (fallback_faces) *fallback_faces = (long long)b->host_ctr->fallback;
+  return FV_OK;
+}
+
+fv_status fv_batch_info(fv_batch_t b, int* nmesh, long long* total_cells, long long* work_items) {
+  fv_status st = check(b);
+  if (st != FV_OK) return st;
+  if (nmesh) *nmesh = b->nmesh;
+  if (total_cells) *total_cells = b->total_cells;
+  if (work_items) *work_items = b->dev.nitems;
+  return FV_OK;
+}
+
+}  // extern "C"

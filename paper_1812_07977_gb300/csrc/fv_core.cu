@@ -29,6 +29,14 @@ void set_error(const char* fmt, ...) {
 void fv_internal_set_error(const char* msg) { set_error("%s", msg); }
 
 namespace {
+fv_status validate_desc(const fv_mesh_desc* d);
+fvd::Params make_params(const fv_mesh_desc* d);
+}  // namespace
+
+fv_status fv_internal_validate_desc(const fv_mesh_desc* d) { return validate_desc(d); }
+fvd::Params fv_internal_params(const fv_mesh_desc* d) { return make_params(d); }
+
+namespace {
 
 std::mutex g_registry_mutex;
 std::unordered_set<const void*> g_registry;  // live mesh handles

@@ -193,4 +193,52 @@ __device__ __forceinline__ int ghost_source(int g, int n, int bc) {
   return g < 0 ? 0 : n - 1;
 }
 
+// Number of ghost (ring) cells of one field.
+__host__ __device__ __forceinline__ long long ring_cells(const Params& P) {
+  const long long X = P.nx + 4, Y = P.ny + 4;
+  return 4 * Y * X + 4 * (long long)P.nz * X + 4 * (long long)P.nz * P.ny;
+}
+
+// Ghost fill of ring cell t (0 <= t < ring_cells) of all five fields.  The
+// axis-by-axis fill (x, then y, then z, each over the full ghosted extent of
+// the other axes) leaves every ghost cell equal to the interior cell
+// (src_x(i), src_y(j), src_z(k)), so each ring cell is written once, straight
+// from its source.  Ring cells are enumerated as the z slabs (4 full
+// planes), the y slabs of the interior planes and the x slabs of the
+// interior rows.
+__device__ __forceinline__ void fill_ghost_cell(double* __restrict__ U, const Params& P,
+                                                long long t) {
+  const long long X = P.nx + 4, Y = P.ny + 4;
+  const long long nz_slab = 4 * Y * X;
+  const long long ny_slab = 4 * (long long)P.nz * X;
+  int i, j, k;
+  if (t < nz_slab) {
+    const long long s = t / (Y * X), r = t - s * (Y * X);
+    k = s < 2 ? (int)s - 2 : P.nz + (int)s - 2;
+    j = (int)(r / X) - 2;
+    i = (int)(r % X) - 2;
+  } else if (t < nz_slab + ny_slab) {
+    const long long u = t - nz_slab;
+    const long long kk = u / (4 * X), r = u - kk * (4 * X);
+    const int s = (int)(r / X);
+    k = (int)kk;
+    j = s < 2 ? s - 2 : P.ny + s - 2;
+    i = (int)(r % X) - 2;
+  } else {
+    const long long u = t - nz_slab - ny_slab;
+    const long long row = u / 4;
+    const int s = (int)(u - row * 4);
+    k = (int)(row / P.ny);
+    j = (int)(row % P.ny);
+    i = s < 2 ? s - 2 : P.nx + s - 2;
+  }
+  const int si = ghost_source(i, P.nx, P.bc[0]);
+  const int sj = ghost_source(j, P.ny, P.bc[1]);
+  const int sk = ghost_source(k, P.nz, P.bc[2]);
+  const long long dst = (k + 2) * P.sz + (j + 2) * P.sy + (i + 2);
+  const long long src = (sk + 2) * P.sz + (sj + 2) * P.sy + (si + 2);
+#pragma unroll
+  for (int q = 0; q < NF; ++q) U[q * P.nfield + dst] = U[q * P.nfield + src];
+}
+
 }  // namespace fvd

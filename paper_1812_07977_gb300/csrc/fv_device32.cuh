@@ -1,5 +1,9 @@
 // fv_device32.cuh -- FP32 building blocks of the FP32-bulk step.
 //
+// The FP32 code is built without implicit contraction (--fmad=false) and
+// writes its fused multiply-adds out (fmaf), so every kernel that inlines
+// these helpers computes the same bits.
+//
 // The FP32-bulk arithmetic keeps the state in FP64 (the RK combine adds the
 // FP32 update to the FP64 state; the pressure of near-vacuum cells is
 // recovered in FP64) and does reconstruction and fluxes in FP32.  On sm_103a
@@ -89,7 +93,7 @@ __device__ __forceinline__ Prim32 prim_from_state(const double u[NF], const Para
   w.vx = mx * ir;
   w.vy = my * ir;
   w.vz = mz * ir;
-  const float ke = 0.5f * (mx * w.vx + my * w.vy + mz * w.vz);
+  const float ke = 0.5f * fmaf(mz, w.vz, fmaf(my, w.vy, mx * w.vx));
   w.p = Q.gm1 * (E - ke);
   if (ke > Q.vacuum_ratio * E) w.p = pressure_fp64(u, Q.gm1_d);
   return w;
@@ -135,12 +139,12 @@ __device__ __forceinline__ void hll_flux(const Prim32& wl, const Prim32& wr, con
     float* U = s == 0 ? UL : UR;
     float* Fs = s == 0 ? FL : FR;
     const float mx = w.r * w.vx, my = w.r * w.vy, mz = w.r * w.vz;
-    const float ke = 0.5f * (mx * w.vx + my * w.vy + mz * w.vz);
+    const float ke = 0.5f * fmaf(mz, w.vz, fmaf(my, w.vy, mx * w.vx));
     U[0] = w.r;
     U[1] = mx;
     U[2] = my;
     U[3] = mz;
-    U[4] = w.p * Q.igm1 + ke;
+    U[4] = fmaf(w.p, Q.igm1, ke);
     const float v = AXIS == 0 ? w.vx : AXIS == 1 ? w.vy : w.vz;
     const float mn = AXIS == 0 ? mx : AXIS == 1 ? my : mz;
     vn[s] = v;
@@ -158,7 +162,7 @@ __device__ __forceinline__ void hll_flux(const Prim32& wl, const Prim32& wr, con
   const float r = rcp(ap + am);
   const float wL = ap * r, wR = am * r, wD = ap * am * r;
 #pragma unroll
-  for (int q = 0; q < NF; ++q) F[q] = wL * FL[q] + wR * FR[q] - wD * (UR[q] - UL[q]);
+  for (int q = 0; q < NF; ++q) F[q] = fmaf(wL, FL[q], fmaf(wR, FR[q], -(wD * (UR[q] - UL[q]))));
 }
 
 }  // namespace fvd32

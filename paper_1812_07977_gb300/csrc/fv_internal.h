@@ -4,7 +4,10 @@
 
 #include <cuda_runtime.h>
 
+#include "fv.h"
+
 #include "fv_device.cuh"
+#include "fv_device32.cuh"
 
 // Device-resident flags and results of one mesh, read back in one copy.
 struct DevCounters {
@@ -37,6 +40,31 @@ struct StepBuffers {
 FV_DECLARE_STEP_VARIANT(fv_fp64_exact)
 FV_DECLARE_STEP_VARIANT(fv_fp64_fma)
 
+// One mesh of a batch, as the batched kernels see it.
+struct BatchMesh {
+  fvd::Params P;
+  fvd32::Params32 Q;
+  long long offset;              // doubles from the batch's U (and U1) base to this mesh
+  double dt;                     // this step's dt, written by the batched CFL kernels
+  unsigned long long smax_bits;  // CFL maximum of this step (bits of a double >= 0)
+};
+
+// Device-side tables of a batch.
+struct BatchDevice {
+  double* U;
+  double* U1;
+  BatchMesh* meshes;
+  int nmesh;
+  int4* items;          // fused-kernel work items: mesh, tile x, tile y, z chunk
+  int nitems;
+  int2* dt_blocks;      // CFL kernel blocks: mesh, chunk of 2048 interior cells
+  int ndt_blocks;
+  int2* ghost_blocks;   // ghost kernel blocks: mesh, chunk of 256 ring cells
+  int nghost_blocks;
+  unsigned* next_item;  // two work counters (stage 1, stage 2)
+  DevCounters* ctr;
+};
+
 // fv_step32_kernels.cu: the FP32-bulk substep (one fused kernel; z chunks
 // of `kchunk` planes per CTA) and its CFL reduction.
 namespace fv_fp32 {
@@ -44,6 +72,16 @@ cudaError_t launch_stage(int stage, const StepBuffers& b, const fvd::Params& P, 
                          int kchunk, double vacuum_ratio, int occupancy, cudaStream_t s);
 cudaError_t launch_reduce_dt(const double* U, const fvd::Params& P, double vacuum_ratio,
                              DevCounters* ctr, cudaStream_t s);
+// Batches: per-mesh CFL dt on the device (dt = cfl / max), the fused substep
+// over all meshes' work items (one persistent launch), and the ghost fill.
+constexpr int kBatchDtChunk = 2048;
+constexpr int kBatchGhostChunk = 256;
+constexpr int kTileX = 32, kTileY = 8;
+cudaError_t launch_batch_dt(const BatchDevice& b, double cfl, cudaStream_t s);
+cudaError_t launch_batch_stage(int stage, const BatchDevice& b, int kchunk, int occupancy,
+                               int num_sms, cudaStream_t s);
+cudaError_t launch_batch_ghosts(int stage, const BatchDevice& b, cudaStream_t s);
+fvd32::Params32 make_params32(const fvd::Params& P, double vacuum_ratio);
 }
 
 // fv_aux.cu (always built without contraction)
@@ -63,3 +101,8 @@ cudaError_t launch_pairwise_sums(const double* U, const fvd::Params& P, double* 
 // fv_core.cu: sets the detail string that fv_last_error() returns on the
 // calling thread (for entry points defined outside fv_core.cu).
 void fv_internal_set_error(const char* msg);
+
+// fv_core.cu: mesh description checks and derived parameters, shared with
+// the batch entry points.
+fv_status fv_internal_validate_desc(const fv_mesh_desc* d);
+fvd::Params fv_internal_params(const fv_mesh_desc* d);

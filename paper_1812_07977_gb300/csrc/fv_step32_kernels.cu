@@ -85,19 +85,19 @@ __device__ __forceinline__ void face_flux(const Prim32& a0, const Prim32& a1, co
   hll_flux<AXIS>(wl, wr, Q, F);
 }
 
+// One tile (32 x 8 columns, planes k0 .. k1-1) of a substep.
 // STAGE 1: U1 = U + dU.  STAGE 2: U = ((U + U1) + dU) / 2.  The input of the
-// substep (U for stage 1, U1 for stage 2) has its ghosts filled.
-template <int STAGE, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB)
-k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params32 Q, float dt,
-          int kchunk, DevCounters* ctr) {
-  __shared__ Smem s;
+// substep (U for stage 1, U1 for stage 2) has its ghosts filled.  Counts of
+// face fallbacks and non-physical cells accumulate in the caller's counters.
+template <int STAGE>
+__device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
+                                             double* __restrict__ U1, const fvd::Params& P,
+                                             const Params32& Q, float dt, int i0, int j0,
+                                             int k0, int k1, unsigned& fallbacks_out,
+                                             unsigned long long& bad_out) {
   const double* __restrict__ src = STAGE == 1 ? U : U1;
   const int tid = threadIdx.x;
   const int ti = tid % TX, tj = tid / TX;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  const int k0 = blockIdx.z * kchunk;
-  const int k1 = min(k0 + kchunk, P.nz);
   const long long nf = P.nfield;
   // this thread's column, clamped into the ghosted array (columns past a
   // ragged edge compute unused values and store nothing)
@@ -222,9 +222,9 @@ k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params
     if (owner) {
 #pragma unroll
       for (int q = 0; q < NF; ++q) {
-        const float acc = -(s.fx[q][tj][ti + 1] - s.fx[q][tj][ti]) * idx -
-                          (s.fy[q][tj + 1][ti] - s.fy[q][tj][ti]) * idy -
-                          (fz_hi[q] - fz_lo[q]) * idz;
+        const float acc = fmaf(fz_lo[q] - fz_hi[q], idz,
+                               fmaf(s.fy[q][tj][ti] - s.fy[q][tj + 1][ti], idy,
+                                    (s.fx[q][tj][ti] - s.fx[q][tj][ti + 1]) * idx));
         const double du = f2d(dt * acc);
         if (STAGE == 1) {
           U1[q * nf + g] = rk0[q] + du;
@@ -240,8 +240,76 @@ k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params
     d1 = d2;
     h0 = h1;
   }
+  fallbacks_out += fallbacks;
+  bad_out += bad;
+}
+
+template <int STAGE, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
+k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params32 Q, float dt,
+          int kchunk, DevCounters* ctr) {
+  __shared__ Smem s;
+  unsigned fallbacks = 0;
+  unsigned long long bad = 0;
+  const int k0 = blockIdx.z * kchunk;
+  stage32_tile<STAGE>(s, U, U1, P, Q, dt, blockIdx.x * TX, blockIdx.y * TY, k0,
+                      min(k0 + kchunk, P.nz), fallbacks, bad);
   if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
   if (bad) atomicAdd(&ctr->np_step, bad);
+}
+
+// ---------------------------------------------------------------- batches
+// Persistent kernel over the tiles of many meshes: each CTA takes work items
+// (mesh, tile x, tile y, z chunk) from an atomic counter until none is left.
+template <int STAGE, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
+k_stage32_batch(double* __restrict__ U, double* __restrict__ U1,
+                const BatchMesh* __restrict__ meshes, const int4* __restrict__ items, int nitems,
+                int kchunk, unsigned* __restrict__ next_item, DevCounters* ctr) {
+  __shared__ Smem s;
+  __shared__ int s_item;
+  unsigned fallbacks = 0;
+  unsigned long long bad = 0;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(next_item, 1u);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= nitems) break;
+    const int4 w = items[it];       // mesh, tile x, tile y, chunk
+    const BatchMesh& m = meshes[w.x];
+    const int k0 = w.w * kchunk;
+    stage32_tile<STAGE>(s, U + m.offset, U1 + m.offset, m.P, m.Q, (float)m.dt, w.y * TX,
+                        w.z * TY, k0, min(k0 + kchunk, m.P.nz), fallbacks, bad);
+  }
+  if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
+  if (bad) atomicAdd(&ctr->np_step, bad);
+}
+
+// CFL signal speed of interior cell m of a mesh in FP32 (bits of a
+// non-negative float; 0 for a non-physical cell, which is counted).
+__device__ __forceinline__ unsigned cell_speed_bits(const double* __restrict__ U,
+                                                    const fvd::Params& P, const Params32& Q,
+                                                    long long m, unsigned long long& bad) {
+  const long long k = m / ((long long)P.nx * P.ny);
+  const long long r = m - k * ((long long)P.nx * P.ny);
+  const long long j = r / P.nx, i = r - j * P.nx;
+  double u[NF];
+  load_state(U, P.nfield, (k + 2) * P.sz + (j + 2) * P.sy + (i + 2), u);
+  const Prim32 w = prim_from_state(u, Q);
+  if (!physical(w)) {
+    ++bad;
+    return 0u;
+  }
+  // explicit roundings (no contraction): every kernel that computes the
+  // speed gets the same bits, so single-mesh and batched runs share a dt
+  const float c2 = __fmul_rn(__fmul_rn(Q.gamma, w.p), rcp(w.r));
+  const float c = __fmul_rn(c2, rsqrtf(c2));
+  const float sp = __fadd_rn(__fadd_rn(__fmul_rn(__fadd_rn(fabsf(w.vx), c), Q.inv_d[0]),
+                                       __fmul_rn(__fadd_rn(fabsf(w.vy), c), Q.inv_d[1])),
+                             __fmul_rn(__fadd_rn(fabsf(w.vz), c), Q.inv_d[2]));
+  const unsigned b = __float_as_uint(sp);
+  return (sp > 0.0f && b < 0x7F800000u) ? b : 0u;
 }
 
 // CFL signal speed per interior cell in FP32 from the FP64 state; the
@@ -254,24 +322,8 @@ k_reduce_dt32(const double* __restrict__ U, fvd::Params P, Params32 Q, DevCounte
   unsigned smax = 0;
   unsigned long long bad = 0;
   for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < n;
-       m += (long long)gridDim.x * blockDim.x) {
-    const long long k = m / ((long long)P.nx * P.ny);
-    const long long r = m - k * ((long long)P.nx * P.ny);
-    const long long j = r / P.nx, i = r - j * P.nx;
-    double u[NF];
-    load_state(U, P.nfield, (k + 2) * P.sz + (j + 2) * P.sy + (i + 2), u);
-    const Prim32 w = prim_from_state(u, Q);
-    if (!physical(w)) {
-      ++bad;
-      continue;
-    }
-    const float c2 = Q.gamma * w.p * rcp(w.r);
-    const float c = c2 * rsqrtf(c2);
-    const float sp = (fabsf(w.vx) + c) * Q.inv_d[0] + (fabsf(w.vy) + c) * Q.inv_d[1] +
-                     (fabsf(w.vz) + c) * Q.inv_d[2];
-    const unsigned b = __float_as_uint(sp);
-    if (sp > 0.0f && b < 0x7F800000u && b > smax) smax = b;
-  }
+       m += (long long)gridDim.x * blockDim.x)
+    smax = max(smax, cell_speed_bits(U, P, Q, m, bad));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, o));
   __shared__ unsigned wmax[8];
@@ -287,6 +339,62 @@ k_reduce_dt32(const double* __restrict__ U, fvd::Params P, Params32 Q, DevCounte
       atomicMax(&ctr->smax_bits,
                 (unsigned long long)__double_as_longlong(f2d(__uint_as_float(smax))));
   }
+}
+
+// Batched CFL maximum: block b reduces chunk c of mesh m (dt_blocks[b]) and
+// folds it into that mesh's maximum.
+__global__ void __launch_bounds__(256)
+k_batch_dt(const double* __restrict__ U, BatchMesh* __restrict__ meshes,
+           const int2* __restrict__ blocks, DevCounters* ctr) {
+  const int2 bm = blocks[blockIdx.x];
+  BatchMesh& mesh = meshes[bm.x];
+  const long long n = (long long)mesh.P.nx * mesh.P.ny * mesh.P.nz;
+  const long long lo = (long long)bm.y * kBatchDtChunk;
+  const long long hi = min(n, lo + kBatchDtChunk);
+  unsigned smax = 0;
+  unsigned long long bad = 0;
+  for (long long m = lo + threadIdx.x; m < hi; m += blockDim.x)
+    smax = max(smax, cell_speed_bits(U + mesh.offset, mesh.P, mesh.Q, m, bad));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+  __shared__ unsigned wmax[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) wmax[wid] = smax;
+  if (bad) atomicAdd(&ctr->np_dt, bad);
+  __syncthreads();
+  if (wid == 0) {
+    smax = lane < 8 ? wmax[lane] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+    if (lane == 0 && smax)
+      atomicMax(&mesh.smax_bits,
+                (unsigned long long)__double_as_longlong(f2d(__uint_as_float(smax))));
+  }
+}
+
+// Clears the per-mesh maxima and the work counters before a step.
+__global__ void k_batch_reset(BatchMesh* __restrict__ meshes, int nmesh, unsigned* next_item) {
+  for (int m = threadIdx.x; m < nmesh; m += blockDim.x) meshes[m].smax_bits = 0ULL;
+  if (threadIdx.x < 2) next_item[threadIdx.x] = 0u;
+}
+
+// dt = cfl / max, formed in FP64 per mesh (0 if the mesh had no physical cell).
+__global__ void k_batch_dt_finalize(BatchMesh* __restrict__ meshes, int nmesh, double cfl) {
+  for (int m = threadIdx.x; m < nmesh; m += blockDim.x) {
+    const double smax = __longlong_as_double((long long)meshes[m].smax_bits);
+    meshes[m].dt = smax > 0.0 ? cfl / smax : 0.0;
+  }
+}
+
+// Batched ghost fill of the state of `stage` (U after stage 2, U1 after 1).
+__global__ void __launch_bounds__(256)
+k_batch_ghosts(double* __restrict__ base, const BatchMesh* __restrict__ meshes,
+               const int2* __restrict__ blocks) {
+  const int2 bm = blocks[blockIdx.x];
+  const BatchMesh& mesh = meshes[bm.x];
+  const long long t = (long long)bm.y * kBatchGhostChunk + threadIdx.x;
+  if (threadIdx.x < kBatchGhostChunk && t < fvd::ring_cells(mesh.P))
+    fvd::fill_ghost_cell(base + mesh.offset, mesh.P, t);
 }
 
 }  // namespace
@@ -327,6 +435,46 @@ cudaError_t launch_reduce_dt(const double* U, const fvd::Params& P, double vacuu
   long long blocks = (n + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   k_reduce_dt32<<<(unsigned)blocks, 256, 0, s>>>(U, P, make_params32(P, vacuum_ratio), ctr);
+  return cudaGetLastError();
+}
+
+}  // namespace fv_fp32
+
+namespace fv_fp32 {
+
+cudaError_t launch_batch_dt(const BatchDevice& b, double cfl, cudaStream_t s) {
+  k_batch_reset<<<1, 128, 0, s>>>(b.meshes, b.nmesh, b.next_item);
+  if (b.ndt_blocks > 0) k_batch_dt<<<b.ndt_blocks, 256, 0, s>>>(b.U, b.meshes, b.dt_blocks, b.ctr);
+  k_batch_dt_finalize<<<1, 128, 0, s>>>(b.meshes, b.nmesh, cfl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_stage(int stage, const BatchDevice& b, int kchunk, int occupancy,
+                               int num_sms, cudaStream_t s) {
+  const int grid = num_sms * (occupancy == 3 ? 3 : 2);
+  unsigned* counter = b.next_item + (stage == 1 ? 0 : 1);
+  if (occupancy == 3) {
+    if (stage == 1)
+      k_stage32_batch<1, 3><<<grid, kThreads, 0, s>>>(b.U, b.U1, b.meshes, b.items, b.nitems,
+                                                       kchunk, counter, b.ctr);
+    else
+      k_stage32_batch<2, 3><<<grid, kThreads, 0, s>>>(b.U, b.U1, b.meshes, b.items, b.nitems,
+                                                       kchunk, counter, b.ctr);
+  } else {
+    if (stage == 1)
+      k_stage32_batch<1, 2><<<grid, kThreads, 0, s>>>(b.U, b.U1, b.meshes, b.items, b.nitems,
+                                                       kchunk, counter, b.ctr);
+    else
+      k_stage32_batch<2, 2><<<grid, kThreads, 0, s>>>(b.U, b.U1, b.meshes, b.items, b.nitems,
+                                                       kchunk, counter, b.ctr);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_ghosts(int stage, const BatchDevice& b, cudaStream_t s) {
+  if (b.nghost_blocks > 0)
+    k_batch_ghosts<<<b.nghost_blocks, kBatchGhostChunk, 0, s>>>(stage == 1 ? b.U1 : b.U,
+                                                                b.meshes, b.ghost_blocks);
   return cudaGetLastError();
 }
 

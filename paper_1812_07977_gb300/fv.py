@@ -26,6 +26,9 @@ ABI_SYMBOLS = (
     "fv_conserved_sums", "fv_get_counters", "fv_set_tuning", "fv_profile_enable",
     "fv_profile_read",
     "fv_mesh_info", "fv_status_string", "fv_last_error", "fv_conserved_sums_noalloc",
+    "fv_batch_create", "fv_batch_destroy", "fv_batch_set_state", "fv_batch_get_state",
+    "fv_batch_step", "fv_batch_get_dt", "fv_batch_set_tuning", "fv_batch_autotune",
+    "fv_batch_get_counters", "fv_batch_info",
 )
 KERNEL_CLASSES = ("prim", "sweep_x", "sweep_y", "sweep_z", "fused", "ghost", "dt", "other")
 
@@ -76,6 +79,18 @@ def load_library(path: str | None = None):
         "fv_profile_read": ([vp, dp, ctypes.POINTER(ctypes.c_longlong)], i),
         "fv_mesh_info": ([vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)], i),
         "fv_conserved_sums_noalloc": ([vp, i, i, i, d, d, d, vp, dp], i),
+        "fv_batch_create": ([ctypes.POINTER(MeshDesc), i, vp, ctypes.POINTER(vp)], i),
+        "fv_batch_destroy": ([vp], i),
+        "fv_batch_set_state": ([vp, i, vp, i], i),
+        "fv_batch_get_state": ([vp, i, vp, i], i),
+        "fv_batch_step": ([vp, d, i], i),
+        "fv_batch_get_dt": ([vp, dp], i),
+        "fv_batch_set_tuning": ([vp, i, i], i),
+        "fv_batch_autotune": ([vp, d, ctypes.POINTER(i), ctypes.POINTER(i), dp], i),
+        "fv_batch_get_counters": ([vp, ctypes.POINTER(ctypes.c_longlong),
+                                   ctypes.POINTER(ctypes.c_longlong)], i),
+        "fv_batch_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong),
+                           ctypes.POINTER(ctypes.c_longlong)], i),
         "fv_status_string": ([i], ctypes.c_char_p),
         "fv_last_error": ([], ctypes.c_char_p),
     }
@@ -272,3 +287,98 @@ def conserved_sums_noalloc(U, lx=1.0, ly=1.0, lz=1.0, stream=None):
                                          ctypes.c_void_p(stream.cuda_stream), out),
            "fv_conserved_sums_noalloc")
     return np.array(out[:])
+
+
+class Batch:
+    """Many independent meshes advanced together by the FP32-bulk step
+    (fv_batch_* in include/fv.h).  `shapes` is a list of (nx, ny, nz) on the
+    unit cube (or pass `descs` kwargs per mesh)."""
+
+    def __init__(self, shapes, gamma=1.4, theta=2.0, bc=("outflow",) * 3, stream=None,
+                 extents=None):
+        self._lib = load_library()
+        self.shapes = [tuple(int(v) for v in s) for s in shapes]
+        arr = (MeshDesc * len(self.shapes))()
+        for m, (nx, ny, nz) in enumerate(self.shapes):
+            d = arr[m]
+            d.nx, d.ny, d.nz = nx, ny, nz
+            l = extents[m] if extents else (1.0, 1.0, 1.0)
+            d.lx, d.ly, d.lz = (float(v) for v in l)
+            d.gamma, d.theta = float(gamma), float(theta)
+            for a in range(3):
+                d.bc[a] = BC[bc[a]] if isinstance(bc[a], str) else int(bc[a])
+            d.precision = PRECISION["fp32_bulk"]
+        self.device = _torch().cuda.current_device()
+        h = ctypes.c_void_p()
+        s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        _check(self._lib.fv_batch_create(arr, len(self.shapes), s, ctypes.byref(h)),
+               "fv_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(self._lib.fv_batch_destroy(self._h), "fv_batch_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _buf(self, m, U, writable):
+        if not 0 <= m < len(self.shapes):   # let the library report the bad index
+            return None, 0
+        nx, ny, nz = self.shapes[m]
+        return Mesh._buffer(self, U, (5, nz, ny, nx), writable)
+
+    def set_state(self, m, U):
+        ptr, dev = self._buf(m, U, False)
+        _check(self._lib.fv_batch_set_state(self._h, int(m), ptr, dev), "fv_batch_set_state")
+
+    def get_state(self, m, out=None):
+        nx, ny, nz = self.shapes[m] if 0 <= m < len(self.shapes) else (1, 1, 1)
+        if out is None:
+            out = _torch().empty((5, nz, ny, nx), dtype=_torch().float64,
+                                 device=f"cuda:{self.device}")
+        ptr, dev = self._buf(m, out, True)
+        _check(self._lib.fv_batch_get_state(self._h, int(m), ptr, dev), "fv_batch_get_state")
+        return out
+
+    def step(self, cfl=0.4, use_graph=True):
+        _check(self._lib.fv_batch_step(self._h, float(cfl), int(bool(use_graph))),
+               "fv_batch_step")
+
+    def dts(self):
+        out = (ctypes.c_double * len(self.shapes))()
+        _check(self._lib.fv_batch_get_dt(self._h, out), "fv_batch_get_dt")
+        return np.array(out[:])
+
+    def set_tuning(self, kchunk, occupancy):
+        _check(self._lib.fv_batch_set_tuning(self._h, int(kchunk), int(occupancy)),
+               "fv_batch_set_tuning")
+
+    def autotune(self, cfl=0.4):
+        kc, occ, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(self._lib.fv_batch_autotune(self._h, float(cfl), ctypes.byref(kc),
+                                           ctypes.byref(occ), ctypes.byref(ms)),
+               "fv_batch_autotune")
+        return kc.value, occ.value, ms.value
+
+    def counters(self):
+        a, b = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(self._lib.fv_batch_get_counters(self._h, ctypes.byref(a), ctypes.byref(b)),
+               "fv_batch_get_counters")
+        return a.value, b.value
+
+    def info(self):
+        n, c, w = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(self._lib.fv_batch_info(self._h, ctypes.byref(n), ctypes.byref(c),
+                                       ctypes.byref(w)), "fv_batch_info")
+        return n.value, c.value, w.value

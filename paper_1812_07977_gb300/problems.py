@@ -178,3 +178,47 @@ def entropy_wave_3d(n: int, amp=0.2, p=1.0, gamma=GAMMA) -> np.ndarray:
     U[3] = rho
     U[4] = p / (gamma - 1.0) + 1.5 * rho
     return U
+
+
+def riemann_random_plane(nx, ny, nz, left, right, normal, gamma=GAMMA) -> np.ndarray:
+    """Riemann problem split by the plane through the cube centre with unit
+    `normal`: primitive states left = (rho, v(3), p) where
+    (x - 1/2, y - 1/2, z - 1/2) . normal < 0, right elsewhere.  The unit cube
+    is covered by nx x ny x nz cells (dx differs per axis when they differ)."""
+    x, y, z = _grid(nx, ny, nz)
+    s = (x - 0.5) * normal[0] + (y - 0.5) * normal[1] + (z - 0.5) * normal[2]
+    is_left = s < 0.0
+    f = [np.where(is_left, left[q], right[q]) for q in range(5)]
+    return conserved_from_primitive(f[0], f[1], f[2], f[3], f[4], gamma)
+
+
+def batched_riemann(seed: int = 12345, count: int = 96,
+                    lengths=tuple(range(16, 129, 8))):
+    """The batched workload: `count` meshes, each axis length drawn uniformly
+    from {16, 24, ..., 128}; each mesh a Riemann problem with rho and p
+    log-uniform in [0.1, 10] on either side, velocities uniform in the unit
+    ball, and a plane normal uniform on the sphere.  Returns a list of dicts
+    with the shape (nx, ny, nz), the states, the normal and U0."""
+    g = SplitMix64(seed)
+    out = []
+    L = np.array(lengths)
+    for _ in range(count):
+        n = [int(L[min(int(u * len(L)), len(L) - 1)]) for u in g.uniform(3)]
+        rho = 10.0 ** (-1.0 + 2.0 * g.uniform(2))
+        p = 10.0 ** (-1.0 + 2.0 * g.uniform(2))
+        vel = []
+        while len(vel) < 2:
+            c = 2.0 * g.uniform(3) - 1.0
+            if float(c @ c) <= 1.0:
+                vel.append(c)
+        while True:
+            c = 2.0 * g.uniform(3) - 1.0
+            r2 = float(c @ c)
+            if 1e-6 < r2 <= 1.0:
+                normal = c / math.sqrt(r2)
+                break
+        left = (rho[0], *vel[0], p[0])
+        right = (rho[1], *vel[1], p[1])
+        out.append({"shape": tuple(n), "left": left, "right": right, "normal": normal,
+                    "U0": riemann_random_plane(*n, left, right, normal)})
+    return out
