@@ -179,6 +179,13 @@ class Mesh:
             if tuple(U.shape) != shape or U.dtype != torch.float64 or not U.is_contiguous():
                 raise ValueError(f"expected a contiguous float64 tensor of shape {shape}")
             if U.is_cuda:
+                # the library reads/writes U on its own stream, asynchronously:
+                # order it after the work queued on the caller's stream and keep
+                # the tensor's memory from being reused before that work is done
+                cur = torch.cuda.current_stream(U.device)
+                if self.stream.cuda_stream != cur.cuda_stream:
+                    self.stream.wait_stream(cur)
+                    U.record_stream(self.stream)
                 return ctypes.c_void_p(U.data_ptr()), 1
             return ctypes.c_void_p(U.data_ptr()), 0
         if isinstance(U, np.ndarray):
@@ -309,10 +316,12 @@ class Batch:
                 d.bc[a] = BC[bc[a]] if isinstance(bc[a], str) else int(bc[a])
             d.precision = PRECISION["fp32_bulk"]
         self.device = _torch().cuda.current_device()
+        if stream is None:  # a stream of its own: capturable, unlike the default one
+            stream = _torch().cuda.Stream()
+        self.stream = stream
         h = ctypes.c_void_p()
-        s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
-        _check(self._lib.fv_batch_create(arr, len(self.shapes), s, ctypes.byref(h)),
-               "fv_batch_create")
+        _check(self._lib.fv_batch_create(arr, len(self.shapes), ctypes.c_void_p(stream.cuda_stream),
+                                         ctypes.byref(h)), "fv_batch_create")
         self._h = h
 
     def close(self):
