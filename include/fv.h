@@ -234,6 +234,49 @@ FV_API fv_status fv_batch_get_counters(fv_batch_t b, long long* nonphysical_cell
 FV_API fv_status fv_batch_info(fv_batch_t b, int* nmesh, long long* total_cells,
                                long long* work_items);
 
+/* ------------------------------------------------------------------------
+ * Learned flux correction (not in the paper: an extension that lets a
+ * coarse mesh approach fine-mesh solutions).  A network of three 3x3x3
+ * convolutions (5 -> 32 -> 32 -> 5 channels, tanh after the first two)
+ * maps the normalised primitives of each cell, x = (W - in_mean)/in_scale,
+ * to o; phi = out_scale * o.  The flux through every face is corrected by
+ * phi(right cell) - phi(left cell), so a cell's state changes by
+ *   dU = -sum_d dt/dx_d (phi(i+e_d) - 2 phi(i) + phi(i-e_d)),
+ * which is conservative and zero for uniform states.  Weights and
+ * activations are BF16, accumulation FP32.  Periodic meshes only.
+ * Parameters (FP32, fv_net_param_count() of them) in the order
+ *   w1 [32][5][27], b1 [32], w2 [32][32][27], b2 [32], w3 [5][32][27], b3 [5]
+ * with kernel index o = 9 dz + 3 dy + dx for offsets (dz, dy, dx) - 1.
+ * ------------------------------------------------------------------------ */
+typedef struct fv_net_s* fv_net_t;
+
+FV_API size_t fv_net_param_count(void);
+/* A network on the current device, parameters zero, scales 1. */
+FV_API fv_status fv_net_create(fv_net_t* out);
+FV_API fv_status fv_net_destroy(fv_net_t n);
+/* Host arrays of fv_net_param_count() floats; set resets the Adam state.
+ * get: either pointer may be NULL; grads are those of the last train step. */
+FV_API fv_status fv_net_set_params(fv_net_t n, const float* params);
+FV_API fv_status fv_net_get_params(fv_net_t n, float* params, float* grads);
+/* Input normalisation, output scale and the residual scale of the loss. */
+FV_API fv_status fv_net_set_scales(fv_net_t n, const double in_mean[5], const double in_scale[5],
+                                   const double out_scale[5], const double res_scale[5]);
+/* o (device pointer, 5*nz*ny*nx floats [q][k][j][i]) for the mesh's
+ * current state; o_out may be NULL.  Synchronising when o_out is given. */
+FV_API fv_status fv_net_forward(fv_net_t n, fv_mesh_t m, float* o_out);
+/* One training step on the mesh's current state: loss
+ *   L = mean over cells and fields of ((dU - r) / res_scale)^2
+ * for the residual r (device pointer, 5*nz*ny*nx FP64 values: the fine
+ * solution averaged to the mesh minus the mesh's own RK2 step over dt),
+ * gradients by the backward kernels, then Adam (beta 0.9, 0.999, eps 1e-8)
+ * with learning rate lr (lr = 0: gradients only).  *loss_out = L before the
+ * update.  Synchronising. */
+FV_API fv_status fv_net_train_step(fv_net_t n, fv_mesh_t m, const double* residual, double dt,
+                                   double lr, double* loss_out);
+/* One corrected step: phi from the current state, fv_step(m, dt), then
+ * U += dU(phi) on the interior and a ghost fill.  Asynchronous. */
+FV_API fv_status fv_step_learned(fv_mesh_t m, fv_net_t n, double dt);
+
 /* Conservation sums of a caller-held state, allocating nothing.
  *
  * The paper has no counterpart: this entry point exists for callers that

@@ -35,6 +35,7 @@ UNITS = [
     ("fv_core.o", "fv_core.cu", ["--fmad=false"]),
     ("fv_noalloc.o", "fv_noalloc.cu", ["--fmad=false"]),
     ("fv_batch.o", "fv_batch.cu", ["--fmad=false"]),
+    ("fv_learned.o", "fv_learned.cu", ["--fmad=true"]),
 ]
 
 

@@ -570,6 +570,27 @@ fv_status fv_profile_read(fv_mesh_t m, double* ms, long long* launches) {
   return FV_OK;
 }
 
+}  // extern "C"
+
+fv_status fv_internal_mesh(fv_mesh_t m, MeshView* out) {
+  fv_status st = check_handle(m);
+  if (st != FV_OK) return st;
+  if (m->stage_pending) {
+    set_error("the mesh is between the two RK substeps");
+    return FV_ERR_INVALID_ARG;
+  }
+  out->P = m->P;
+  out->U = m->buf.U;
+  out->stream = m->stream;
+  out->device = m->device;
+  out->precision = m->desc.precision;
+  return FV_OK;
+}
+
+fv_status fv_internal_step(fv_mesh_t m, double dt) { return fv_step(m, dt); }
+
+extern "C" {
+
 fv_status fv_mesh_info(fv_mesh_t m, int dims[3], size_t* state_bytes) {
   fv_status st = check_handle(m);
   if (st != FV_OK) return st;

@@ -106,3 +106,17 @@ void fv_internal_set_error(const char* msg);
 // the batch entry points.
 fv_status fv_internal_validate_desc(const fv_mesh_desc* d);
 fvd::Params fv_internal_params(const fv_mesh_desc* d);
+
+// fv_core.cu: a mesh's internals for the learned correction (fv_learned.cu).
+// fv_internal_mesh returns FV_OK and fills the fields for a live mesh at a
+// step boundary; U points to its current (ghosted, FP64) state.
+struct MeshView {
+  fvd::Params P;
+  double* U;
+  cudaStream_t stream;
+  int device;
+  int precision;
+};
+fv_status fv_internal_mesh(fv_mesh_t m, MeshView* out);
+// Run one full step of the mesh (as fv_step) / refill its ghosts.
+fv_status fv_internal_step(fv_mesh_t m, double dt);

@@ -29,6 +29,9 @@ ABI_SYMBOLS = (
     "fv_batch_create", "fv_batch_destroy", "fv_batch_set_state", "fv_batch_get_state",
     "fv_batch_step", "fv_batch_get_dt", "fv_batch_set_tuning", "fv_batch_autotune",
     "fv_batch_get_counters", "fv_batch_info",
+    "fv_net_param_count", "fv_net_create", "fv_net_destroy", "fv_net_set_params",
+    "fv_net_get_params", "fv_net_set_scales", "fv_net_forward", "fv_net_train_step",
+    "fv_step_learned",
 )
 KERNEL_CLASSES = ("prim", "sweep_x", "sweep_y", "sweep_z", "fused", "ghost", "dt", "other")
 
@@ -91,6 +94,15 @@ def load_library(path: str | None = None):
                                    ctypes.POINTER(ctypes.c_longlong)], i),
         "fv_batch_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong),
                            ctypes.POINTER(ctypes.c_longlong)], i),
+        "fv_net_param_count": ([], ctypes.c_size_t),
+        "fv_net_create": ([ctypes.POINTER(vp)], i),
+        "fv_net_destroy": ([vp], i),
+        "fv_net_set_params": ([vp, vp], i),
+        "fv_net_get_params": ([vp, vp, vp], i),
+        "fv_net_set_scales": ([vp, dp, dp, dp, dp], i),
+        "fv_net_forward": ([vp, vp, vp], i),
+        "fv_net_train_step": ([vp, vp, vp, d, d, dp], i),
+        "fv_step_learned": ([vp, vp, d], i),
         "fv_status_string": ([i], ctypes.c_char_p),
         "fv_last_error": ([], ctypes.c_char_p),
     }
@@ -391,3 +403,76 @@ class Batch:
         _check(self._lib.fv_batch_info(self._h, ctypes.byref(n), ctypes.byref(c),
                                        ctypes.byref(w)), "fv_batch_info")
         return n.value, c.value, w.value
+
+
+class Net:
+    """The learned flux correction (fv_net_* in include/fv.h): three 3x3x3
+    convolutions 5 -> 32 -> 32 -> 5, BF16 weights, FP32 accumulation."""
+
+    def __init__(self):
+        self._lib = load_library()
+        self.nparam = int(self._lib.fv_net_param_count())
+        h = ctypes.c_void_p()
+        _check(self._lib.fv_net_create(ctypes.byref(h)), "fv_net_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(self._lib.fv_net_destroy(self._h), "fv_net_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == self.nparam
+        _check(self._lib.fv_net_set_params(self._h, ctypes.c_void_p(a.ctypes.data)),
+               "fv_net_set_params")
+
+    def params(self):
+        p = np.empty(self.nparam, dtype=np.float32)
+        _check(self._lib.fv_net_get_params(self._h, ctypes.c_void_p(p.ctypes.data), None),
+               "fv_net_get_params")
+        return p
+
+    def grads(self):
+        g = np.empty(self.nparam, dtype=np.float32)
+        _check(self._lib.fv_net_get_params(self._h, None, ctypes.c_void_p(g.ctypes.data)),
+               "fv_net_get_params")
+        return g
+
+    def set_scales(self, in_mean, in_scale, out_scale, res_scale):
+        arrs = [(ctypes.c_double * 5)(*[float(v) for v in a])
+                for a in (in_mean, in_scale, out_scale, res_scale)]
+        _check(self._lib.fv_net_set_scales(self._h, *arrs), "fv_net_set_scales")
+
+    def forward(self, mesh):
+        torch = _torch()
+        out = torch.empty((5,) + mesh.shape[1:], dtype=torch.float32,
+                          device=f"cuda:{mesh.device}")
+        _check(self._lib.fv_net_forward(self._h, mesh.handle, ctypes.c_void_p(out.data_ptr())),
+               "fv_net_forward")
+        return out
+
+    def train_step(self, mesh, residual, dt, lr):
+        torch = _torch()
+        assert isinstance(residual, torch.Tensor) and residual.is_cuda
+        assert residual.dtype == torch.float64 and tuple(residual.shape) == mesh.shape
+        loss = ctypes.c_double()
+        _check(self._lib.fv_net_train_step(self._h, mesh.handle,
+                                           ctypes.c_void_p(residual.data_ptr()), float(dt),
+                                           float(lr), ctypes.byref(loss)), "fv_net_train_step")
+        return loss.value
+
+    def step(self, mesh, dt):
+        _check(self._lib.fv_step_learned(mesh.handle, self._h, float(dt)), "fv_step_learned")

@@ -1,0 +1,160 @@
+"""Learned flux correction on the GPU (fv_net_*, fv_step_learned) against the
+FP64 numpy oracle (oracle/learned.py) on the same parameters and states.
+
+The GPU network runs in BF16 (weights and activations; 8-bit mantissa)
+with FP32 accumulation, so it is compared with relative tolerances derived
+from BF16 rounding (2^-9 per value, compounded over three layers): the
+network output within 2% of its scale, the loss within 2%, each parameter
+tensor's gradient within 5% (relative L2) and aligned (cosine > 0.995)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import learned as L
+from paper_1812_07977_gb300 import problems
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PER = (True, True, True)
+NORM = {"in_mean": np.array([1.0, 0.0, 0.0, 0.0, 1.0]),
+        "in_scale": np.array([0.2, 0.3, 0.3, 0.3, 0.2]),
+        "out_scale": np.array([1e-3, 2e-3, 2e-3, 1e-3, 3e-3]),
+        "res_scale": np.array([1e-4, 1e-4, 1e-4, 1e-4, 2e-4])}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+
+
+def _prims(U):
+    rho = U[0]
+    v = U[1:4] / rho
+    p = 0.4 * (U[4] - 0.5 * rho * (v * v).sum(0))
+    return np.stack([rho, v[0], v[1], v[2], p])
+
+
+def _setup(shape=(12, 10, 9), seed=4):
+    U0 = problems.random_smooth_periodic(*shape, seed=seed)
+    p = L.init_params(seed)
+    rng = np.random.default_rng(seed)
+    for k in ("b1", "b2", "b3"):
+        p[k] = 0.1 * rng.standard_normal(p[k].shape)
+    from paper_1812_07977_gb300.fv import Mesh, Net
+    mesh = Mesh(*shape, bc=("periodic",) * 3)
+    mesh.set_state(U0)
+    net = Net()
+    net.set_params(L.flatten(p))
+    net.set_scales(NORM["in_mean"], NORM["in_scale"], NORM["out_scale"], NORM["res_scale"])
+    return U0, p, mesh, net
+
+
+def _inv_d(shape):
+    return np.array([shape[0], shape[1], shape[2]], dtype=np.float64)  # unit cube
+
+
+def test_forward_matches_oracle():
+    U0, p, mesh, net = _setup()
+    o = net.forward(mesh).cpu().numpy().astype(np.float64)
+    phi, _ = L.forward(p, _prims(U0), NORM, PER)
+    ref = phi / NORM["out_scale"][:, None, None, None]
+    err = np.abs(o - ref).max() / np.abs(ref).max()
+    rel2 = np.linalg.norm(o - ref) / np.linalg.norm(ref)
+    print("forward: max err", err, "rel L2", rel2)
+    assert err < 2e-2 and rel2 < 1e-2
+    mesh.close()
+    net.close()
+
+
+def test_loss_and_gradients_match_oracle():
+    shape = (12, 10, 9)
+    U0, p, mesh, net = _setup(shape)
+    rng = np.random.default_rng(8)
+    r = 1e-4 * rng.standard_normal((5,) + shape[::-1])
+    dt = 0.01
+    loss = net.train_step(mesh, torch.from_numpy(r).cuda(), dt, 0.0)
+    g = net.grads().astype(np.float64)
+    Lref, gref = L.loss_and_grads(p, _prims(U0), r, dt, _inv_d(shape), NORM, PER)
+    print("loss", loss, Lref)
+    assert abs(loss - Lref) <= 2e-2 * Lref
+    gr = L.unflatten(g)
+    # a constant shift of the last layer's output gives a constant phi and no
+    # correction, so the exact gradient of b3 is zero: both sides must be at
+    # round-off compared with the other gradients
+    gscale = np.abs(gref["w3"]).max()
+    assert np.abs(gr["b3"]).max() < 1e-4 * gscale and np.abs(gref["b3"]).max() < 1e-9 * gscale
+    for k in L.ORDER[:-1]:
+        a, b = gr[k].ravel(), gref[k].ravel()
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+        print(k, "rel L2", rel, "cos", cos)
+        assert rel < 5e-2 and cos > 0.995, k
+    mesh.close()
+    net.close()
+
+
+def test_training_reduces_the_loss():
+    shape = (16, 16, 8)
+    U0, p, mesh, net = _setup(shape, seed=6)
+    # a reachable target: the correction of a perturbed copy of the network
+    q = {k: v * (1.0 + 0.3 * np.random.default_rng(1).standard_normal(v.shape))
+         for k, v in p.items()}
+    phi, _ = L.forward(q, _prims(U0), NORM, PER)
+    r = L.laplacian_update(phi, 0.01, _inv_d(shape), PER)
+    rt = torch.from_numpy(r).cuda()
+    losses = [net.train_step(mesh, rt, 0.01, 2e-3) for _ in range(60)]
+    print("loss", losses[0], "->", losses[-1])
+    assert losses[-1] < 0.5 * losses[0]
+    mesh.close()
+    net.close()
+
+
+def test_zero_network_gives_the_plain_step_bitwise():
+    shape = (12, 10, 9)
+    U0 = problems.random_smooth_periodic(*shape, seed=2)
+    from paper_1812_07977_gb300.fv import Mesh, Net
+    a = Mesh(*shape, bc=("periodic",) * 3)
+    b = Mesh(*shape, bc=("periodic",) * 3)
+    a.set_state(U0)
+    b.set_state(U0)
+    with Net() as net:
+        net.set_params(np.zeros(net.nparam, dtype=np.float32))
+        for _ in range(3):
+            dt = a.reduce_dt(0.4)
+            net.step(a, dt)
+            b.step(dt)
+    assert np.array_equal(a.get_state().cpu().numpy(), b.get_state().cpu().numpy())
+    a.close()
+    b.close()
+
+
+def test_corrected_step_is_conservative():
+    shape = (12, 10, 9)
+    U0, p, mesh, net = _setup(shape)
+    from paper_1812_07977_gb300.fv import Mesh
+    plain = Mesh(*shape, bc=("periodic",) * 3)
+    plain.set_state(U0)
+    for _ in range(3):
+        dt = mesh.reduce_dt(0.4)
+        net.step(mesh, dt)
+        plain.step(dt)
+    a, b = mesh.conserved_sums(), plain.conserved_sums()
+    got = mesh.get_state().cpu().numpy()
+    assert np.abs(got - plain.get_state().cpu().numpy()).max() > 0   # it did correct
+    scale = np.abs(U0).reshape(5, -1).sum(1) / U0[0].size
+    assert np.all(np.abs(a - b) <= 1e-9 * scale), (a - b) / scale
+    mesh.close()
+    plain.close()
+    net.close()
+
+
+def test_rejects_non_periodic_mesh():
+    from paper_1812_07977_gb300.fv import FvError, Mesh, Net
+    with Mesh(8, 8, 8) as m, Net() as net:
+        m.set_state(problems.uniform(8, 8, 8, 1.0, (0, 0, 0), 1.0))
+        with pytest.raises(FvError):
+            net.forward(m)
