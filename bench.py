@@ -16,6 +16,8 @@ from __future__ import annotations
 
 import argparse
 import json
+
+import numpy as np
 import math
 import os
 import statistics
@@ -298,6 +300,26 @@ def run_batched(args, world, dev, rank):
             "nonphysical": bad}
 
 
+def run_learned(args):
+    """The learned-correction workload: periodic shear layers (rho 1 and 2,
+    vx +-0.5, vy = A sin(4 pi x), p = 2.5, gamma 1.4), fine 256^3 FP64 runs
+    block-averaged 4x onto a 64^3 coarse mesh; training by the library's
+    kernels; evaluation on a held-out amplitude against the averaged fine
+    run, with and without the correction."""
+    from paper_1812_07977_gb300 import learned
+    r = learned.run(fine_n=args.learned_fine, factor=4, train_amps=(0.01, 0.04, 0.07, 0.1),
+                    val_amp=0.085, test_amp=0.055, samples=args.learned_samples, every=2,
+                    epochs=args.learned_epochs, lr=1e-3, eval_steps=args.learned_eval_steps,
+                    val_steps=args.learned_eval_steps)
+    out = {k: v for k, v in r.items() if not isinstance(v, list)}
+    out["l1_rho_plain_mean"] = float(np.mean(r["l1_rho_plain"]))
+    out["l1_rho_learned_mean"] = float(np.mean(r["l1_rho_learned"]))
+    out["l1_rho_plain_final"] = r["l1_rho_plain"][-1]
+    out["l1_rho_learned_final"] = r["l1_rho_learned"][-1]
+    out["gain"] = out["l1_rho_plain_mean"] / max(out["l1_rho_learned_mean"], 1e-300)
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -376,6 +398,8 @@ def run_ours(args):
 
     if args.batch_steps > 0:
         variants["batched_fp32"] = run_batched(args, world, dev, rank)
+    if args.learned_epochs > 0 and rank == 0:
+        variants["learned_correction"] = run_learned(args)
 
     if rank != 0:
         return 0
@@ -451,6 +475,11 @@ def main():
     ap.add_argument("--variant-steps", type=int, default=50)
     ap.add_argument("--batch-steps", type=int, default=50,
                     help="steps of the 96-mesh batched workload (0: skip)")
+    ap.add_argument("--learned-epochs", type=int, default=16,
+                    help="training epochs of the learned correction (0: skip)")
+    ap.add_argument("--learned-fine", type=int, default=256)
+    ap.add_argument("--learned-samples", type=int, default=16)
+    ap.add_argument("--learned-eval-steps", type=int, default=32)
     ap.add_argument("--n", type=int, default=N)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--traffic", type=float, default=None,

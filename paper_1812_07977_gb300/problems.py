@@ -222,3 +222,34 @@ def batched_riemann(seed: int = 12345, count: int = 96,
         out.append({"shape": tuple(n), "left": left, "right": right, "normal": normal,
                     "U0": riemann_random_plane(*n, left, right, normal)})
     return out
+
+
+def shear_layer(n: int, amp: float, gamma: float = GAMMA, p0: float = 2.5,
+                modes=None, seed: int = 0) -> np.ndarray:
+    """Periodic shear layer on an n^3 unit cube: rho = 2, vx = +0.5 for
+    |y - 1/2| < 1/4, rho = 1, vx = -0.5 elsewhere, p = p0, and the
+    perturbation vy = amp sin(4 pi x) (the same in every z plane).  With
+    `modes` > 0 the perturbation is instead a seeded sum of that many modes
+    with integer wave vectors in {1..4}^3 and random phases, of total
+    amplitude amp, on vy and vz."""
+    x, y, z = _grid(n, n, n)
+    inside = np.abs(y - 0.5) < 0.25
+    rho = np.where(inside, 2.0, 1.0) + 0.0 * (x + z)
+    vx = np.where(inside, 0.5, -0.5) + 0.0 * (x + z)
+    if not modes:
+        vy = amp * np.sin(4.0 * math.pi * x) + 0.0 * (y + z)
+        vz = np.zeros_like(rho)
+    else:
+        g = SplitMix64(seed)
+        vy = np.zeros_like(rho)
+        vz = np.zeros_like(rho)
+        for _ in range(modes):
+            k = np.floor(g.uniform(3) * 4.0) + 1.0
+            ph = 2.0 * math.pi * g.uniform(2)
+            arg = 2.0 * math.pi * (k[0] * x + k[1] * y + k[2] * z)
+            vy = vy + np.sin(arg + ph[0])
+            vz = vz + np.sin(arg + ph[1])
+        vy *= amp / modes
+        vz *= amp / modes
+    return conserved_from_primitive(rho, vx, vy, vz, np.full_like(rho, p0), gamma)
+
