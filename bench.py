@@ -320,6 +320,61 @@ def run_learned(args):
     return out
 
 
+def run_shear(args, dev):
+    """512^3 periodic shear layer (rho 2/1, vx +-0.5, p 2.5, gamma 5/3, an
+    8-mode seeded perturbation of amplitude 0.01 on vy and vz): the FP32-bulk
+    fused step replayed from a CUDA graph (a batch of one mesh) versus the
+    FP64 step, `shear_steps` steps each on the same dt sequence (the FP64
+    run's CFL steps), with the mass and energy drift of each."""
+    import torch
+
+    from paper_1812_07977_gb300 import problems
+    from paper_1812_07977_gb300.fv import Batch, Mesh
+    n, K, g53 = args.shear_n, args.shear_steps, 5.0 / 3.0
+    U0 = problems.shear_layer_device(n, 0.01, gamma=g53, modes=8, seed=2024, device=dev)
+    m64 = Mesh(n, n, n, gamma=g53, bc=("periodic",) * 3, precision=args.precision)
+    m64.set_state(U0)
+    s0 = m64.conserved_sums()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    dts = []
+    ev[0].record()
+    for _ in range(K):
+        dt = m64.reduce_dt(CFL)
+        dts.append(dt)
+        m64.step(dt)
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms64 = ev[0].elapsed_time(ev[1]) / K
+    s64 = m64.conserved_sums()
+    rho64 = m64.get_state()[0].clone()
+    stream = torch.cuda.Stream()
+    b = Batch([(n, n, n)], gamma=g53, bc=("periodic",) * 3, stream=stream)
+    b.set_state(0, U0)
+    ev[2].record(stream)
+    for _ in range(K):                 # its own CFL dt each step, from a graph
+        b.step(CFL, use_graph=True)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    ms32 = ev[2].elapsed_time(ev[3]) / K
+    U32 = b.get_state(0)
+    b.close()
+    m64.set_state(U32)                 # the library's pairwise sums of the FP32 run
+    s32 = m64.conserved_sums()
+    drho = float((U32[0] - rho64).abs().mean() / rho64.abs().mean())
+    m64.close()
+    scale = [float(v) for v in U0.abs().reshape(5, -1).sum(1) / U0[0].numel()]
+    return {"cells": n ** 3, "steps": K,
+            "fp64": {"ms_per_step": ms64, "value": n ** 3 / (ms64 / 1e3),
+                     "mass_drift": abs(s64[0] - s0[0]) / scale[0],
+                     "energy_drift": abs(s64[4] - s0[4]) / scale[4]},
+            "fp32_graph": {"ms_per_step": ms32, "value": n ** 3 / (ms32 / 1e3),
+                           "mass_drift": abs(s32[0] - s0[0]) / scale[0],
+                           "energy_drift": abs(s32[4] - s0[4]) / scale[4]},
+            "rho_l1_rel_fp32_vs_fp64": drho,
+            "note": "drifts relative to the mean |U| per cell; the FP32 run takes its own "
+                    "CFL steps, so the two end times agree to the dt difference"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -400,6 +455,8 @@ def run_ours(args):
         variants["batched_fp32"] = run_batched(args, world, dev, rank)
     if args.learned_epochs > 0 and rank == 0:
         variants["learned_correction"] = run_learned(args)
+    if args.shear_steps > 0 and rank == 0:
+        variants["shear_layer_512"] = run_shear(args, dev)
 
     if rank != 0:
         return 0
@@ -480,6 +537,9 @@ def main():
     ap.add_argument("--learned-fine", type=int, default=256)
     ap.add_argument("--learned-samples", type=int, default=16)
     ap.add_argument("--learned-eval-steps", type=int, default=32)
+    ap.add_argument("--shear-n", type=int, default=512)
+    ap.add_argument("--shear-steps", type=int, default=100,
+                    help="steps of the 512^3 shear-layer FP32-graph vs FP64 comparison (0: skip)")
     ap.add_argument("--n", type=int, default=N)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--traffic", type=float, default=None,

@@ -253,3 +253,35 @@ def shear_layer(n: int, amp: float, gamma: float = GAMMA, p0: float = 2.5,
         vz *= amp / modes
     return conserved_from_primitive(rho, vx, vy, vz, np.full_like(rho, p0), gamma)
 
+
+
+def shear_layer_device(n: int, amp: float, gamma: float = GAMMA, p0: float = 2.5,
+                       modes: int = 8, seed: int = 0, device="cuda"):
+    """shear_layer(n, amp, gamma, p0, modes, seed) built on a torch device
+    (the same seeded draws and formulas; for meshes too large to build on
+    the host).  Returns a contiguous float64 tensor (5, n, n, n)."""
+    import torch
+    c = (torch.arange(n, dtype=torch.float64, device=device) + 0.5) / n
+    z, y, x = c[:, None, None], c[None, :, None], c[None, None, :]
+    inside = (y - 0.5).abs() < 0.25
+    shape = (n, n, n)
+    rho = torch.where(inside, 2.0, 1.0).expand(shape)
+    vx = torch.where(inside, 0.5, -0.5).expand(shape)
+    g = SplitMix64(seed)
+    vy = torch.zeros(shape, dtype=torch.float64, device=device)
+    vz = torch.zeros(shape, dtype=torch.float64, device=device)
+    for _ in range(modes):
+        k = np.floor(g.uniform(3) * 4.0) + 1.0
+        ph = 2.0 * math.pi * g.uniform(2)
+        arg = 2.0 * math.pi * (float(k[0]) * x + float(k[1]) * y + float(k[2]) * z)
+        vy += torch.sin(arg + float(ph[0]))
+        vz += torch.sin(arg + float(ph[1]))
+    vy *= amp / modes
+    vz *= amp / modes
+    U = torch.empty((5,) + shape, dtype=torch.float64, device=device)
+    U[0] = rho
+    U[1] = rho * vx
+    U[2] = rho * vy
+    U[3] = rho * vz
+    U[4] = p0 / (gamma - 1.0) + 0.5 * rho * (vx * vx + vy * vy + vz * vz)
+    return U
