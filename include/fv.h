@@ -161,6 +161,19 @@ FV_API fv_status fv_conserved_sums(fv_mesh_t m, double out[5]);
 FV_API fv_status fv_get_counters(fv_mesh_t m, long long* nonphysical_cells,
                           long long* fallback_faces);
 
+/* Face fluxes since the last fv_set_state: `evaluated` = fluxes the
+ * kernels computed, `defined` = fluxes the method defines (every face of the
+ * mesh, once per substep).  Along a grid line, a face whose five-cell
+ * neighbourhood is a run of cells equal bit for bit has the inputs, and so
+ * the flux, of the face before it; the FP64 sweeps then reuse that flux
+ * (same bits as evaluating it), so evaluated <= defined there.  The fused
+ * FP32-bulk kernel reuses z fluxes the same way and x / y fluxes whose four
+ * cells equal those one plane below; it evaluates the faces on tile and
+ * z-chunk edges in both neighbouring tiles, so for states without equal
+ * neighbours evaluated exceeds defined.  Either pointer may be NULL.
+ * Synchronising. */
+FV_API fv_status fv_get_face_counts(fv_mesh_t m, long long* evaluated, long long* defined);
+
 /* Kernel classes of the profiling hooks below. */
 typedef enum {
   FV_KERNEL_PRIM = 0,     /* conserved -> primitive (FP64 paths) */

@@ -29,7 +29,8 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
 # (object name, source, extra flags)
 UNITS = [
     ("fv_step_fp64_exact.o", "fv_step_kernels.cu", ["--fmad=false", "-DFV_NS=fv_fp64_exact"]),
-    ("fv_step_fp64_fma.o", "fv_step_kernels.cu", ["--fmad=true", "-DFV_NS=fv_fp64_fma"]),
+    ("fv_step_fp64_fma.o", "fv_step_kernels.cu", ["--fmad=true", "-DFV_NS=fv_fp64_fma",
+                                                         "-DFV_NEWTON_DIVSQRT"]),
     ("fv_step_fp32.o", "fv_step32_kernels.cu", ["--fmad=false"]),
     ("fv_aux.o", "fv_aux.cu", ["--fmad=false"]),
     ("fv_core.o", "fv_core.cu", ["--fmad=false"]),

@@ -32,11 +32,16 @@ k_fill_ghosts(double* __restrict__ U, Params P) {
 // maximum over cells is exact in any order.  Non-negative doubles order
 // like their bit patterns, so the grid-wide maximum is an integer atomicMax.
 // A NaN s never wins, as in a plain `if (s > smax)` loop.
+// A cell equal bit for bit to the thread's previous cell has the same speed
+// (already in smax) and the same validity; when the whole warp has such
+// cells (uniform regions), it skips the arithmetic.
 __global__ void __launch_bounds__(kThreads)
 k_reduce_dt(const double* __restrict__ U, Params P, DevCounters* ctr) {
   const long long n = (long long)P.nx * P.ny * P.nz;
   double smax = 0.0;
   unsigned long long bad = 0;
+  double up[NF] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  bool have = false, bad_prev = false;
   for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < n;
        m += (long long)gridDim.x * blockDim.x) {
     const long long k = m / ((long long)P.nx * P.ny);
@@ -44,10 +49,21 @@ k_reduce_dt(const double* __restrict__ U, Params P, DevCounters* ctr) {
     const long long j = r / P.nx, i = r - j * P.nx;
     const long long g = (k + 2) * P.sz + (j + 2) * P.sy + (i + 2);
     double u[NF];
+    bool eq = have;
 #pragma unroll
-    for (int q = 0; q < NF; ++q) u[q] = U[q * P.nfield + g];
+    for (int q = 0; q < NF; ++q) {
+      u[q] = U[q * P.nfield + g];
+      eq = eq && bits(u[q]) == bits(up[q]);
+      up[q] = u[q];
+    }
+    have = true;
+    if (__all_sync(__activemask(), eq)) {
+      bad += bad_prev;
+      continue;
+    }
     const Prim w = cons_to_prim(u, P);
-    if (!(is_pos(w.r) && is_pos(w.p))) ++bad;
+    bad_prev = !(is_pos(w.r) && is_pos(w.p));
+    bad += bad_prev;
     const double c = sqrt(P.gamma * w.p / w.r);
     const double s = ((fabs(w.vx) + c) * P.inv_d[0] + (fabs(w.vy) + c) * P.inv_d[1]) +
                      (fabs(w.vz) + c) * P.inv_d[2];

@@ -220,6 +220,8 @@ fv_status fv_batch_create(const fv_mesh_desc* descs, int nmesh, void* cuda_strea
                 "allocating %.3f GB of batch storage: %s", 2.0 * sb / 1e9, cudaGetErrorString(e));
   }
   b->dev.nmesh = nmesh;
+  b->dev.all_mc = true;
+  for (int m = 0; m < nmesh; ++m) b->dev.all_mc &= (b->host_meshes[m].Q.theta == 2.0f);
   b->dev.ndt_blocks = (int)dt_blocks.size();
   b->dev.nghost_blocks = (int)ghost_blocks.size();
   if ((e = cudaMemcpy(b->dev.meshes, b->host_meshes.data(), nmesh * sizeof(BatchMesh),

@@ -65,6 +65,7 @@ struct fv_mesh_s {
   struct Timed { int cls; cudaEvent_t a, b; };
   std::vector<Timed> pending;
   long long launches[FV_KERNEL_NCLASS];
+  long long faces_defined;  // face fluxes the method defines, since the last set_state
 };
 
 namespace {
@@ -233,7 +234,14 @@ cudaError_t timed(fv_mesh_t m, int cls, int nlaunch, F&& launch) {
   return e;
 }
 
+// Faces normal to `axis` (each evaluated once per substep by the method).
+long long faces_normal_to(const fvd::Params& P, int axis) {
+  const long long nx = P.nx, ny = P.ny, nz = P.nz;
+  return axis == 0 ? (nx + 1) * ny * nz : axis == 1 ? nx * (ny + 1) * nz : nx * ny * (nz + 1);
+}
+
 cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
+  for (int axis = 0; axis < 3; ++axis) m->faces_defined += faces_normal_to(m->P, axis);
   if (m->desc.precision == FV_PREC_FP32_BULK) {
     cudaError_t e = timed(m, FV_KERNEL_FUSED, 1, [&] {
       return fv_fp32::launch_stage(stage, m->buf, m->P, dt, m->kchunk, m->vacuum_ratio,
@@ -284,6 +292,7 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   m->vacuum_ratio = 0.99;
   m->occupancy = 2;
   for (int c = 0; c < FV_KERNEL_NCLASS; ++c) m->launches[c] = 0;
+  m->faces_defined = 0;
   cudaError_t e = cudaGetDevice(&m->device);
   if (e != cudaSuccess) {
     delete m;
@@ -362,6 +371,7 @@ fv_status fv_set_state(fv_mesh_t m, const double* U, int on_device) {
   if (e != cudaSuccess) return cuda_fail(e, "ghost-fill kernel");
   if ((e = cudaMemsetAsync(m->buf.ctr, 0, sizeof(DevCounters), m->stream)) != cudaSuccess)
     return cuda_fail(e, "clearing counters");
+  m->faces_defined = 0;
   m->stage_pending = 0;
   if (!on_device && (e = cudaStreamSynchronize(m->stream)) != cudaSuccess)
     return cuda_fail(e, "fv_set_state");
@@ -507,6 +517,16 @@ fv_status fv_get_counters(fv_mesh_t m, long long* nonphysical_cells, long long* 
   if (nonphysical_cells)
     *nonphysical_cells = (long long)(m->host_ctr->np_step + m->host_ctr->np_dt);
   if (fallback_faces) *fallback_faces = (long long)m->host_ctr->fallback;
+  return FV_OK;
+}
+
+fv_status fv_get_face_counts(fv_mesh_t m, long long* evaluated, long long* defined) {
+  fv_status st = check_handle(m);
+  if (st != FV_OK) return st;
+  DeviceGuard g(m->device);
+  if ((st = read_counters(m)) != FV_OK) return st;
+  if (evaluated) *evaluated = (long long)m->host_ctr->faces;
+  if (defined) *defined = m->faces_defined;
   return FV_OK;
 }
 

@@ -113,6 +113,83 @@ __device__ __forceinline__ double half_slope(double theta, double dm, double dp)
   return half(minmod3(theta_times<TK>(theta, dm), half(dm + dp), theta_times<TK>(theta, dp)));
 }
 
+// ---------------------------------------------------------------- Newton forms
+// The FMA build (held to a relative tolerance, not to the bits of IEEE
+// division and square root) replaces each correctly rounded divide and
+// square root -- about ten FP64 issue slots each on this GPU -- by an FP32
+// seed from the SFU, refined by two Newton-Raphson steps in FP64:
+//   reciprocal          y <- y + y (1 - d y)               (2 DFMA a step)
+//   inverse square root y <- y + (y/2) (1 - u y^2)         (DMUL + 2 DFMA)
+// Each step squares the relative error, so a seed within 2^-21 ends within
+// about one ulp.  Operands outside [2^-120, 2^120) in magnitude (where the
+// seed or its reciprocal would leave the normal FP32 range), zeros, infinities
+// and NaNs take the IEEE operation instead.
+
+// IEEE operations for the rare operands, kept behind their branch.
+__device__ __forceinline__ double ddiv_rare(double a, double b) {
+  double r;
+  asm volatile("div.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
+  return r;
+}
+__device__ __forceinline__ double dsqrt_rare(double a) {
+  double r;
+  asm volatile("sqrt.rn.f64 %0, %1;" : "=d"(r) : "d"(a));
+  return r;
+}
+
+// |x| in [2^-120, 2^120) (false for zeros, subnormals, infinities and NaNs)
+__device__ __forceinline__ bool seed_range(double x) {
+  const unsigned e = ((unsigned)__double2hiint(x) >> 20) & 0x7FFu;
+  return e - (1023u - 120u) < 240u;
+}
+
+// x truncated to FP32 (sign kept), for x with seed_range(x)
+__device__ __forceinline__ float seed_f32(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  return __uint_as_float((hi & 0x80000000u) | (((hi & 0x7FFFFFFFu) - (896u << 20)) << 3) |
+                         (lo >> 29));
+}
+
+// a normal FP32 value widened to FP64 (exact)
+__device__ __forceinline__ double widen_f32(float f) {
+  const unsigned x = __float_as_uint(f);
+  const unsigned hi = (((x & 0x7FFFFFFFu) >> 3) + (896u << 20)) | (x & 0x80000000u);
+  return __hiloint2double((int)hi, (int)(x << 29));
+}
+
+// 1 / d
+__device__ __forceinline__ double recip_nr(double d) {
+  if (!seed_range(d)) return ddiv_rare(1.0, d);
+  float s;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(seed_f32(d)));
+  double y = widen_f32(s);
+  double e = fma(-d, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-d, y, 1.0);
+  return fma(y, e, y);
+}
+
+// sqrt(t / r) for the sound speed, t = gamma p: evaluated as t / sqrt(t r),
+// i.e. t times the inverse square root of u = t r (no division).  Negative
+// or zero operands, and t, r or t r outside the seed range, take the IEEE
+// form, so non-physical states give what it gives (NaN for a negative
+// quotient).
+__device__ __forceinline__ double sound_speed_nr(double t, double r) {
+  const double u = t * r;
+  if ((__double2hiint(t) | __double2hiint(r)) < 0 || !seed_range(t) || !seed_range(r) ||
+      !seed_range(u))
+    return dsqrt_rare(ddiv_rare(t, r));
+  float s;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(seed_f32(u)));
+  double y = widen_f32(s);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double e = fma(-(u * y), y, 1.0);
+    y = fma(half(y), e, y);
+  }
+  return t * y;
+}
+
 // ---------------------------------------------------------------- physics
 struct Prim { double r, vx, vy, vz, p; };
 
@@ -124,7 +201,11 @@ __device__ __forceinline__ double comp(const Prim& w, int q) {
 // p = (gamma-1) * (E - 0.5*((mx*vx + my*vy) + mz*vz))
 __device__ __forceinline__ Prim cons_to_prim(const double u[NF], const Params& P) {
   Prim w;
+#ifdef FV_NEWTON_DIVSQRT
+  double ir = recip_nr(u[0]);
+#else
   double ir = 1.0 / u[0];
+#endif
   w.r = u[0];
   w.vx = u[1] * ir;
   w.vy = u[2] * ir;
@@ -157,7 +238,11 @@ __device__ __forceinline__ void euler_side(const Prim& w, const Params& P, Side<
   double vn = AXIS == 0 ? w.vx : AXIS == 1 ? w.vy : w.vz;
   double mn = AXIS == 0 ? mx : AXIS == 1 ? my : mz;
   s.vn = vn;
+#ifdef FV_NEWTON_DIVSQRT
+  s.c = sound_speed_nr(P.gamma * w.p, w.r);
+#else
   s.c = sqrt(P.gamma * w.p / w.r);
+#endif
   s.f[0] = mn;
   s.f[1] = mn * w.vx;
   s.f[2] = mn * w.vy;
@@ -177,7 +262,11 @@ __device__ __forceinline__ void hll_flux(const Prim& wl, const Prim& wr, const P
   euler_side<AXIS>(wr, P, R);
   double ap = max0(L.vn + L.c, R.vn + R.c);
   double am = max0(L.c - L.vn, R.c - R.vn);
+#ifdef FV_NEWTON_DIVSQRT
+  double r = recip_nr(ap + am);
+#else
   double r = 1.0 / (ap + am);
+#endif
   double apm = ap * am;
 #pragma unroll
   for (int q = 0; q < NF; ++q) F[q] = ((ap * L.f[q] + am * R.f[q]) - apm * (R.u[q] - L.u[q])) * r;

@@ -22,24 +22,39 @@ namespace fvd32 {
 
 using fvd::NF;
 
-// Hardware conversions for the rare operands.  As volatile asm they stay
-// behind their branch; a plain conversion would be if-converted by the
-// compiler and issued on the FP64 pipe for every value.
-__device__ __forceinline__ float d2f_rare(double x) {
+// Hardware conversions for the rare operands, as calls: inlined, the
+// conversion would be predicated into the common path, where every
+// predicated-off copy still takes an FP64 issue slot.
+static __device__ __noinline__ float d2f_rare(double x) {
   float r;
   asm volatile("cvt.rn.f32.f64 %0, %1;" : "=f"(r) : "d"(x));
   return r;
 }
-__device__ __forceinline__ double f2d_rare(float x) {
+static __device__ __noinline__ double f2d_rare(float x) {
   double r;
   asm volatile("cvt.f64.f32 %0, %1;" : "=d"(r) : "f"(x));
   return r;
 }
 
+static __device__ __noinline__ double dhalf_rare(double x) {
+  double r;
+  asm volatile("mul.rn.f64 %0, %1, 0d3FE0000000000000;" : "=d"(r) : "d"(x));
+  return r;
+}
+
+// x * 0.5 in FP64, bit-identical to the IEEE product, rare operands by call
+__device__ __forceinline__ double dhalf(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  if (e - 2u < 0x7FDu) return __hiloint2double((int)(hi - 0x00100000u), (int)lo);
+  if (((hi << 1) | lo) == 0u) return x;  // +-0 (tested on the halves: as a 64-bit
+                                         // test it becomes an FP64 compare)
+  return dhalf_rare(x);
+}
+
 // double -> float, round to nearest even
 __device__ __forceinline__ float d2f(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
   const unsigned e = (hi >> 20) & 0x7FFu;
   if (e - 897u < 254u) {  // result exponent 1..254 (a carry may round to inf)
     unsigned field = ((e - 896u) << 23) | ((hi & 0x000FFFFFu) << 3) | (lo >> 29);
@@ -47,8 +62,9 @@ __device__ __forceinline__ float d2f(double x) {
     field += (unsigned)(rem > 0x10000000u) | ((unsigned)(rem == 0x10000000u) & (field & 1u));
     return __uint_as_float(field | (hi & 0x80000000u));
   }
-  if ((b << 1) == 0ULL) return __uint_as_float(hi & 0x80000000u);  // +-0
-  return d2f_rare(x);  // tiny, huge, inf or NaN
+  // zeros and FP64 subnormals (below half the least FP32 subnormal) -> +-0
+  if (e == 0u) return __uint_as_float(hi & 0x80000000u);
+  return d2f_rare(x);  // FP32 subnormal range, huge, inf or NaN
 }
 
 // float -> double (exact)
@@ -110,6 +126,17 @@ __device__ __forceinline__ float half_slope(float theta, float dm, float dp) {
   return 0.5f * minmod3(theta * dm, 0.5f * (dm + dp), theta * dp);
 }
 
+// The same for theta = 2 (monotonised central limiter), where
+// 0.5 minmod(2 dm, (dm + dp)/2, 2 dp) = minmod(dm, (dm + dp)/4, dp) (exactly:
+// the factors are powers of two).  The middle argument shares the sign of dm
+// and dp whenever they agree, so the result is the least magnitude with
+// dm's sign if dm and dp have one sign, else 0 (a zero operand gives 0).
+__device__ __forceinline__ float half_slope_mc(float dm, float dp) {
+  const float m = fminf(fminf(fabsf(dm), fabsf(dp)), fabsf(0.25f * (dm + dp)));
+  const unsigned r = __float_as_uint(m) | (__float_as_uint(dm) & 0x80000000u);
+  return ((__float_as_uint(dm) ^ __float_as_uint(dp)) & 0x80000000u) ? 0.0f : __uint_as_float(r);
+}
+
 __device__ __forceinline__ bool physical(const Prim32& w) { return w.r > 0.0f && w.p > 0.0f; }
 
 __device__ __forceinline__ Prim32 operator+(const Prim32& a, const Prim32& b) {
@@ -119,7 +146,13 @@ __device__ __forceinline__ Prim32 operator-(const Prim32& a, const Prim32& b) {
   return Prim32{a.r - b.r, a.vx - b.vx, a.vy - b.vy, a.vz - b.vz, a.p - b.p};
 }
 
+// Half slopes of the five primitives; MC: theta is 2.
+template <bool MC>
 __device__ __forceinline__ Prim32 half_slopes(float theta, const Prim32& dm, const Prim32& dp) {
+  if (MC)
+    return Prim32{half_slope_mc(dm.r, dp.r), half_slope_mc(dm.vx, dp.vx),
+                  half_slope_mc(dm.vy, dp.vy), half_slope_mc(dm.vz, dp.vz),
+                  half_slope_mc(dm.p, dp.p)};
   return Prim32{half_slope(theta, dm.r, dp.r), half_slope(theta, dm.vx, dp.vx),
                 half_slope(theta, dm.vy, dp.vy), half_slope(theta, dm.vz, dp.vz),
                 half_slope(theta, dm.p, dp.p)};

@@ -15,7 +15,15 @@ struct DevCounters {
   unsigned long long np_step;      // non-physical interior cells seen by the step
   unsigned long long fallback;     // faces that fell back to first order
   unsigned long long np_dt;        // non-physical interior cells seen by the dt pass
+  unsigned long long faces;        // face fluxes evaluated (not reused) by the flux kernels
 };
+
+// Adds each lane's count to *ctr once per warp (the lanes present at the call).
+__device__ __forceinline__ void warp_count(unsigned long long* ctr, unsigned n) {
+  const unsigned mask = __activemask();
+  const unsigned sum = __reduce_add_sync(mask, n);
+  if ((threadIdx.x & 31u) == (unsigned)(__ffs(mask) - 1) && sum) atomicAdd(ctr, (unsigned long long)sum);
+}
 
 // Device buffers used by one RK2 substep.
 struct StepBuffers {
@@ -63,6 +71,7 @@ struct BatchDevice {
   int nghost_blocks;
   unsigned* next_item;  // two work counters (stage 1, stage 2)
   DevCounters* ctr;
+  bool all_mc;          // every mesh has limiter parameter 2
 };
 
 // fv_step32_kernels.cu: the FP32-bulk substep (one fused kernel; z chunks

@@ -40,6 +40,7 @@ struct Smem {
   float w[NF][PY][PX];
   float fx[NF][TY][TX + 1];
   float fy[NF][TY + 1][TX];
+  unsigned char same[PY][PX];   // cell equals (bit for bit) the cell one plane below
 };
 
 __device__ __forceinline__ void load_state(const double* __restrict__ U, long long nf,
@@ -60,6 +61,25 @@ __device__ __forceinline__ Prim32 smem_prim(const Smem& s, int row, int col) {
                 s.w[4][row][col]};
 }
 
+__device__ __forceinline__ bool same32(const Prim32& a, const Prim32& b) {
+  return __float_as_uint(a.r) == __float_as_uint(b.r) &&
+         __float_as_uint(a.vx) == __float_as_uint(b.vx) &&
+         __float_as_uint(a.vy) == __float_as_uint(b.vy) &&
+         __float_as_uint(a.vz) == __float_as_uint(b.vz) && __float_as_uint(a.p) == __float_as_uint(b.p);
+}
+
+// Stores the plane's primitives of one cell and whether they equal the
+// previous plane's in that slot (`valid`: the slot holds the previous plane).
+__device__ __forceinline__ void smem_store_flag(Smem& s, int row, int col, const Prim32& w,
+                                                bool valid) {
+  s.same[row][col] = valid && same32(smem_prim(s, row, col), w);
+  s.w[0][row][col] = w.r;
+  s.w[1][row][col] = w.vx;
+  s.w[2][row][col] = w.vy;
+  s.w[3][row][col] = w.vz;
+  s.w[4][row][col] = w.p;
+}
+
 __device__ __forceinline__ void smem_store(Smem& s, int row, int col, const Prim32& w) {
   s.w[0][row][col] = w.r;
   s.w[1][row][col] = w.vx;
@@ -70,13 +90,13 @@ __device__ __forceinline__ void smem_store(Smem& s, int row, int col, const Prim
 
 // Face flux between cells a1 and a2 given the four cells a0..a3 along the
 // face normal; falls back to first order if a face state is non-physical.
-template <int AXIS>
+template <int AXIS, bool MC>
 __device__ __forceinline__ void face_flux(const Prim32& a0, const Prim32& a1, const Prim32& a2,
                                           const Prim32& a3, const Params32& Q, float F[NF],
                                           unsigned& fallbacks) {
   const Prim32 d0 = a1 - a0, d1 = a2 - a1, d2 = a3 - a2;
-  Prim32 wl = a1 + half_slopes(Q.theta, d0, d1);
-  Prim32 wr = a2 - half_slopes(Q.theta, d1, d2);
+  Prim32 wl = a1 + half_slopes<MC>(Q.theta, d0, d1);
+  Prim32 wr = a2 - half_slopes<MC>(Q.theta, d1, d2);
   if (!(physical(wl) && physical(wr))) {
     wl = a1;
     wr = a2;
@@ -89,12 +109,13 @@ __device__ __forceinline__ void face_flux(const Prim32& a0, const Prim32& a1, co
 // STAGE 1: U1 = U + dU.  STAGE 2: U = ((U + U1) + dU) / 2.  The input of the
 // substep (U for stage 1, U1 for stage 2) has its ghosts filled.  Counts of
 // face fallbacks and non-physical cells accumulate in the caller's counters.
-template <int STAGE>
+// MC: the limiter parameter is 2.
+template <int STAGE, bool MC>
 __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
                                              double* __restrict__ U1, const fvd::Params& P,
                                              const Params32& Q, float dt, int i0, int j0,
                                              int k0, int k1, unsigned& fallbacks_out,
-                                             unsigned long long& bad_out) {
+                                             unsigned long long& bad_out, unsigned& evaluated) {
   const double* __restrict__ src = STAGE == 1 ? U : U1;
   const int tid = threadIdx.x;
   const int ti = tid % TX, tj = tid / TX;
@@ -132,18 +153,27 @@ __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
   Prim32 w0 = load_prim(src, nf, col + (long long)(k0 + 2) * P.sz, Q);    // plane k0
   Prim32 w1 = load_prim(src, nf, col + (long long)(k0 + 3) * P.sz, Q);    // plane k0+1
   Prim32 d1 = w1 - w0;                                                    // D(k0+1)
-  Prim32 h0 = half_slopes(Q.theta, w0 - wm1, d1);                         // cell k0
+  Prim32 h0 = half_slopes<MC>(Q.theta, w0 - wm1, d1);                         // cell k0
   float fz_lo[NF];
+  bool zfb;   // the last z face fell back to first order
   {
-    Prim32 hm1 = half_slopes(Q.theta, wm1 - wm2, w0 - wm1);               // cell k0-1
+    Prim32 hm1 = half_slopes<MC>(Q.theta, wm1 - wm2, w0 - wm1);               // cell k0-1
     Prim32 wl = wm1 + hm1, wr = w0 - h0;
-    if (!(physical(wl) && physical(wr))) {
+    zfb = !(physical(wl) && physical(wr));
+    if (zfb) {
       wl = wm1;
       wr = w0;
       ++fallbacks;
     }
     hll_flux<2>(wl, wr, Q, fz_lo);
+    ++evaluated;
   }
+  // cells of the column equal bit for bit to the newest cell of the window,
+  // counted from plane k0-2
+  int run = same32(wm1, wm2) ? 2 : 1;
+  run = same32(w0, wm1) ? run + 1 : 1;
+  run = same32(w1, w0) ? run + 1 : 1;
+  unsigned xyfb = 0;   // fallbacks of this thread's x (bits 0, 1) and y (2, 3) faces
   // the first chunk's lower face is the domain boundary face; later chunks
   // recompute a face the previous chunk counted
   if (k0 != 0 || !owner) fallbacks = 0;
@@ -177,45 +207,82 @@ __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
         rk1[q] = STAGE == 2 ? U1[q * nf + g] : 0.0;
       }
     }
-    // (a) z: plane k+2 enters the window; flux of face k+1/2
+    // (a) z: plane k+2 enters the window; flux of face k+1/2.  Face k+1/2
+    // reads planes k-1 .. k+2; when planes k-2 .. k+2 of the column are
+    // equal, its slopes are +0 and its face states are those of face k-1/2:
+    // its flux and fallback are the previous face's, bit for bit (reused when
+    // the whole warp can).
     const Prim32 w2 = prim_from_state(cur_col, Q);
-    const Prim32 d2 = w2 - w1;
-    const Prim32 h1 = half_slopes(Q.theta, d1, d2);
+    run = same32(w2, w1) ? run + 1 : 1;
+    Prim32 d2, h1;
     float fz_hi[NF];
-    {
+    if (__all_sync(__activemask(), run >= 5)) {
+      d2 = Prim32{0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+      h1 = d2;
+#pragma unroll
+      for (int q = 0; q < NF; ++q) fz_hi[q] = fz_lo[q];
+      if (zfb && owner) ++fallbacks;
+    } else {
+      d2 = w2 - w1;
+      h1 = half_slopes<MC>(Q.theta, d1, d2);
       Prim32 wl = w0 + h0, wr = w1 - h1;
-      if (!(physical(wl) && physical(wr))) {
+      zfb = !(physical(wl) && physical(wr));
+      if (zfb) {
         wl = w0;
         wr = w1;
         if (owner) ++fallbacks;
       }
       hll_flux<2>(wl, wr, Q, fz_hi);
+      ++evaluated;
     }
-    // (b) the plane's primitives into shared memory
-    smem_store(s, tj + 2, ti + 2, w0);
-    if (tid < kHalo) smem_store(s, hrow + 2, hcol + 2, prim_from_state(cur_halo, Q));
+    // (b) the plane's primitives into shared memory, each with a flag: equal
+    // to the previous plane's in its slot (never on a chunk's first plane,
+    // where the slot holds another tile's data)
+    smem_store_flag(s, tj + 2, ti + 2, w0, k > k0);
+    if (tid < kHalo) smem_store_flag(s, hrow + 2, hcol + 2, prim_from_state(cur_halo, Q), k > k0);
     __syncthreads();
-    // (c) x faces: face fi (between columns fi-1 and fi) of row r
-    for (int f = tid; f < kXFaces; f += kThreads) {
+    // (c) x faces: face fi (between columns fi-1 and fi) of row r.  A face
+    // whose four cells all equal the previous plane's has that plane's
+    // inputs, so its flux (still in s.fx) and fallback stand.
+    for (int f = tid, pass = 0; f < kXFaces; f += kThreads, ++pass) {
       const int r = f / (TX + 1), fi = f % (TX + 1);
-      float F[NF];
-      unsigned fb = 0;
-      face_flux<0>(smem_prim(s, r + 2, fi), smem_prim(s, r + 2, fi + 1),
-                   smem_prim(s, r + 2, fi + 2), smem_prim(s, r + 2, fi + 3), Q, F, fb);
-      if (i0 + fi <= P.nx && j0 + r < P.ny) fallbacks += fb;
+      const bool keep = s.same[r + 2][fi] & s.same[r + 2][fi + 1] & s.same[r + 2][fi + 2] &
+                        s.same[r + 2][fi + 3];
+      unsigned fb;
+      if (__all_sync(__activemask(), keep)) {
+        fb = (xyfb >> pass) & 1u;
+      } else {
+        float F[NF];
+        fb = 0;
+        face_flux<0, MC>(smem_prim(s, r + 2, fi), smem_prim(s, r + 2, fi + 1),
+                         smem_prim(s, r + 2, fi + 2), smem_prim(s, r + 2, fi + 3), Q, F, fb);
+        xyfb = (xyfb & ~(1u << pass)) | (fb << pass);
+        ++evaluated;
 #pragma unroll
-      for (int q = 0; q < NF; ++q) s.fx[q][r][fi] = F[q];
+        for (int q = 0; q < NF; ++q) s.fx[q][r][fi] = F[q];
+      }
+      // each face counted by one tile: face TX of a tile is face 0 of the next
+      if (i0 + fi <= P.nx && (fi < TX || i0 + fi == P.nx) && j0 + r < P.ny) fallbacks += fb;
     }
     // (d) y faces: face fj (between rows fj-1 and fj) of column c
-    for (int f = tid; f < kYFaces; f += kThreads) {
+    for (int f = tid, pass = 2; f < kYFaces; f += kThreads, ++pass) {
       const int fj = f / TX, c = f % TX;
-      float F[NF];
-      unsigned fb = 0;
-      face_flux<1>(smem_prim(s, fj, c + 2), smem_prim(s, fj + 1, c + 2),
-                   smem_prim(s, fj + 2, c + 2), smem_prim(s, fj + 3, c + 2), Q, F, fb);
-      if (i0 + c < P.nx && j0 + fj <= P.ny) fallbacks += fb;
+      const bool keep = s.same[fj][c + 2] & s.same[fj + 1][c + 2] & s.same[fj + 2][c + 2] &
+                        s.same[fj + 3][c + 2];
+      unsigned fb;
+      if (__all_sync(__activemask(), keep)) {
+        fb = (xyfb >> pass) & 1u;
+      } else {
+        float F[NF];
+        fb = 0;
+        face_flux<1, MC>(smem_prim(s, fj, c + 2), smem_prim(s, fj + 1, c + 2),
+                         smem_prim(s, fj + 2, c + 2), smem_prim(s, fj + 3, c + 2), Q, F, fb);
+        xyfb = (xyfb & ~(1u << pass)) | (fb << pass);
+        ++evaluated;
 #pragma unroll
-      for (int q = 0; q < NF; ++q) s.fy[q][fj][c] = F[q];
+        for (int q = 0; q < NF; ++q) s.fy[q][fj][c] = F[q];
+      }
+      if (i0 + c < P.nx && j0 + fj <= P.ny && (fj < TY || j0 + fj == P.ny)) fallbacks += fb;
     }
     __syncthreads();
     // (e) update of cell (i, j, k): FP32 divergence, FP64 RK combine
@@ -229,7 +296,7 @@ __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
         if (STAGE == 1) {
           U1[q * nf + g] = rk0[q] + du;
         } else {
-          U[q * nf + g] = fvd::half((rk0[q] + rk1[q]) + du);
+          U[q * nf + g] = dhalf((rk0[q] + rk1[q]) + du);
         }
       }
     }
@@ -244,31 +311,32 @@ __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
   bad_out += bad;
 }
 
-template <int STAGE, int MINB>
+template <int STAGE, int MINB, bool MC>
 __global__ void __launch_bounds__(kThreads, MINB)
 k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params32 Q, float dt,
           int kchunk, DevCounters* ctr) {
   __shared__ Smem s;
-  unsigned fallbacks = 0;
+  unsigned fallbacks = 0, evaluated = 0;
   unsigned long long bad = 0;
   const int k0 = blockIdx.z * kchunk;
-  stage32_tile<STAGE>(s, U, U1, P, Q, dt, blockIdx.x * TX, blockIdx.y * TY, k0,
-                      min(k0 + kchunk, P.nz), fallbacks, bad);
+  stage32_tile<STAGE, MC>(s, U, U1, P, Q, dt, blockIdx.x * TX, blockIdx.y * TY, k0,
+                          min(k0 + kchunk, P.nz), fallbacks, bad, evaluated);
   if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
   if (bad) atomicAdd(&ctr->np_step, bad);
+  warp_count(&ctr->faces, evaluated);
 }
 
 // ---------------------------------------------------------------- batches
 // Persistent kernel over the tiles of many meshes: each CTA takes work items
 // (mesh, tile x, tile y, z chunk) from an atomic counter until none is left.
-template <int STAGE, int MINB>
+template <int STAGE, int MINB, bool MC>
 __global__ void __launch_bounds__(kThreads, MINB)
 k_stage32_batch(double* __restrict__ U, double* __restrict__ U1,
                 const BatchMesh* __restrict__ meshes, const int4* __restrict__ items, int nitems,
                 int kchunk, unsigned* __restrict__ next_item, DevCounters* ctr) {
   __shared__ Smem s;
   __shared__ int s_item;
-  unsigned fallbacks = 0;
+  unsigned fallbacks = 0, evaluated = 0;
   unsigned long long bad = 0;
   for (;;) {
     __syncthreads();
@@ -279,11 +347,12 @@ k_stage32_batch(double* __restrict__ U, double* __restrict__ U1,
     const int4 w = items[it];       // mesh, tile x, tile y, chunk
     const BatchMesh& m = meshes[w.x];
     const int k0 = w.w * kchunk;
-    stage32_tile<STAGE>(s, U + m.offset, U1 + m.offset, m.P, m.Q, (float)m.dt, w.y * TX,
-                        w.z * TY, k0, min(k0 + kchunk, m.P.nz), fallbacks, bad);
+    stage32_tile<STAGE, MC>(s, U + m.offset, U1 + m.offset, m.P, m.Q, (float)m.dt, w.y * TX,
+                            w.z * TY, k0, min(k0 + kchunk, m.P.nz), fallbacks, bad, evaluated);
   }
   if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
   if (bad) atomicAdd(&ctr->np_step, bad);
+  warp_count(&ctr->faces, evaluated);
 }
 
 // CFL signal speed of interior cell m of a mesh in FP32 (bits of a
@@ -417,12 +486,23 @@ cudaError_t launch_stage(int stage, const StepBuffers& b, const fvd::Params& P, 
   if (kchunk < 1) kchunk = 1;
   const dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + kchunk - 1) / kchunk);
   const float fdt = (float)dt;
-  if (occupancy == 3) {  // 3 CTAs per SM: 80 registers, a few spills
-    if (stage == 1) k_stage32<1, 3><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
-    else k_stage32<2, 3><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
-  } else {               // 2 CTAs per SM: up to 128 registers
-    if (stage == 1) k_stage32<1, 2><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
-    else k_stage32<2, 2><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+  // 3 CTAs per SM: 80 registers, a few spills; 2 CTAs per SM: up to 128
+  if (Q.theta == 2.0f) {
+    if (occupancy == 3) {
+      if (stage == 1) k_stage32<1, 3, true><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+      else k_stage32<2, 3, true><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+    } else {
+      if (stage == 1) k_stage32<1, 2, true><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+      else k_stage32<2, 2, true><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+    }
+  } else {
+    if (occupancy == 3) {
+      if (stage == 1) k_stage32<1, 3, false><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+      else k_stage32<2, 3, false><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+    } else {
+      if (stage == 1) k_stage32<1, 2, false><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+      else k_stage32<2, 2, false><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+    }
   }
   return cudaGetLastError();
 }
@@ -449,25 +529,34 @@ cudaError_t launch_batch_dt(const BatchDevice& b, double cfl, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <bool MC>
+static void batch_stage(int stage, const BatchDevice& b, int kchunk, int occupancy, int grid,
+                        unsigned* counter, cudaStream_t s) {
+  if (occupancy == 3) {
+    if (stage == 1)
+      k_stage32_batch<1, 3, MC><<<grid, kThreads, 0, s>>>(b.U, b.U1, b.meshes, b.items,
+                                                           b.nitems, kchunk, counter, b.ctr);
+    else
+      k_stage32_batch<2, 3, MC><<<grid, kThreads, 0, s>>>(b.U, b.U1, b.meshes, b.items,
+                                                           b.nitems, kchunk, counter, b.ctr);
+  } else {
+    if (stage == 1)
+      k_stage32_batch<1, 2, MC><<<grid, kThreads, 0, s>>>(b.U, b.U1, b.meshes, b.items,
+                                                           b.nitems, kchunk, counter, b.ctr);
+    else
+      k_stage32_batch<2, 2, MC><<<grid, kThreads, 0, s>>>(b.U, b.U1, b.meshes, b.items,
+                                                           b.nitems, kchunk, counter, b.ctr);
+  }
+}
+
+// The MC form when every mesh of the batch has limiter parameter 2, else the
+// general form for all (same results as each mesh's single-mesh kernel).
 cudaError_t launch_batch_stage(int stage, const BatchDevice& b, int kchunk, int occupancy,
                                int num_sms, cudaStream_t s) {
   const int grid = num_sms * (occupancy == 3 ? 3 : 2);
   unsigned* counter = b.next_item + (stage == 1 ? 0 : 1);
-  if (occupancy == 3) {
-    if (stage == 1)
-      k_stage32_batch<1, 3><<<grid, kThreads, 0, s>>>(b.U, b.U1, b.meshes, b.items, b.nitems,
-                                                       kchunk, counter, b.ctr);
-    else
-      k_stage32_batch<2, 3><<<grid, kThreads, 0, s>>>(b.U, b.U1, b.meshes, b.items, b.nitems,
-                                                       kchunk, counter, b.ctr);
-  } else {
-    if (stage == 1)
-      k_stage32_batch<1, 2><<<grid, kThreads, 0, s>>>(b.U, b.U1, b.meshes, b.items, b.nitems,
-                                                       kchunk, counter, b.ctr);
-    else
-      k_stage32_batch<2, 2><<<grid, kThreads, 0, s>>>(b.U, b.U1, b.meshes, b.items, b.nitems,
-                                                       kchunk, counter, b.ctr);
-  }
+  if (b.all_mc) batch_stage<true>(stage, b, kchunk, occupancy, grid, counter, s);
+  else batch_stage<false>(stage, b, kchunk, occupancy, grid, counter, s);
   return cudaGetLastError();
 }
 

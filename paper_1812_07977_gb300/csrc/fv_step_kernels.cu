@@ -34,15 +34,26 @@ constexpr int kPrimThreads = 256;
 constexpr int kSweepThreads = 64;
 constexpr int kSweepMinBlocks = 8;   // 16 warps per SM: at most 128 registers
 
+// A cell equal bit for bit to the thread's previous cell has its primitives;
+// when the whole warp has such cells (uniform regions), it reuses them.
 __global__ void __launch_bounds__(kPrimThreads)
 k_prim(const double* __restrict__ U, double* __restrict__ W, Params P, DevCounters* ctr) {
   const long long nf = P.nfield;
+  double up[NF] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  Prim w = Prim{0.0, 0.0, 0.0, 0.0, 0.0};
+  bool have = false;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nf;
        c += (long long)gridDim.x * blockDim.x) {
     double u[NF];
+    bool eq = have;
 #pragma unroll
-    for (int q = 0; q < NF; ++q) u[q] = U[q * nf + c];
-    Prim w = cons_to_prim(u, P);
+    for (int q = 0; q < NF; ++q) {
+      u[q] = U[q * nf + c];
+      eq = eq && bits(u[q]) == bits(up[q]);
+      up[q] = u[q];
+    }
+    have = true;
+    if (!__all_sync(__activemask(), eq)) w = cons_to_prim(u, P);
     W[c] = w.r;
     W[nf + c] = w.vx;
     W[2 * nf + c] = w.vy;
@@ -68,6 +79,12 @@ __device__ __forceinline__ Prim load_prim(const double* __restrict__ W, long lon
   w.vz = W[3 * nf + off];
   w.p = W[4 * nf + off];
   return w;
+}
+
+// a and b equal bit for bit (all five components)
+__device__ __forceinline__ bool same(const Prim& a, const Prim& b) {
+  return bits(a.r) == bits(b.r) && bits(a.vx) == bits(b.vx) && bits(a.vy) == bits(b.vy) &&
+         bits(a.vz) == bits(b.vz) && bits(a.p) == bits(b.p);
 }
 
 __device__ __forceinline__ Prim sub(const Prim& a, const Prim& b) {
@@ -120,21 +137,44 @@ k_sweep(const double* __restrict__ W, double* __restrict__ ACC, double* __restri
   double Fprev[NF];
 #pragma unroll
   for (int q = 0; q < NF; ++q) Fprev[q] = 0.0;
+  // length of the run of cells equal bit for bit to the newest cell of the
+  // window (counted from cell -2), and whether the last face fell back
+  int run = same(wm1, wm2) ? 2 : 1;
+  run = same(wc, wm1) ? run + 1 : 1;
+  bool fell_back = false;
+  unsigned evaluated = 0;
 
   for (int f = 0; f <= n; ++f) {
     Prim wn = load_prim(W, g0 + (long long)(f + 1) * gs, nf);  // W(f+1)
-    Prim dnext = sub(wn, wc);                                 // D(f+1)
-    Prim hcur = half_slopes<TK>(theta, dcur, dnext);          // cell f
-    // face f-1/2 between cells f-1 and f
-    Prim wl = add(wprev, hprev);
-    Prim wr = sub(wc, hcur);
-    if (!(is_pos(wl.r) && is_pos(wl.p) && is_pos(wr.r) && is_pos(wr.p))) {
-      wl = wprev;
-      wr = wc;
-      atomicAdd(&ctr->fallback, 1ULL);
-    }
+    run = same(wn, wc) ? run + 1 : 1;
     double F[NF];
-    hll_flux<AXIS>(wl, wr, P, F);
+    Prim dnext, hcur;
+    // Face f-1/2 reads cells f-2 .. f+1.  When cells f-3 .. f+1 are equal,
+    // its differences and slopes are +0 and its face states are those of
+    // face f-3/2, so its flux (and fallback) is the previous face's, bit for
+    // bit: reuse it.  (run >= 5 implies f >= 1.)  Decided per warp, so the
+    // warp skips the flux only when every line can.
+    if (__all_sync(__activemask(), run >= 5)) {
+      dnext = Prim{0.0, 0.0, 0.0, 0.0, 0.0};
+      hcur = dnext;
+#pragma unroll
+      for (int q = 0; q < NF; ++q) F[q] = Fprev[q];
+      if (fell_back) atomicAdd(&ctr->fallback, 1ULL);
+    } else {
+      dnext = sub(wn, wc);                                    // D(f+1)
+      hcur = half_slopes<TK>(theta, dcur, dnext);             // cell f
+      // face f-1/2 between cells f-1 and f
+      Prim wl = add(wprev, hprev);
+      Prim wr = sub(wc, hcur);
+      fell_back = !(is_pos(wl.r) && is_pos(wl.p) && is_pos(wr.r) && is_pos(wr.p));
+      if (fell_back) {
+        wl = wprev;
+        wr = wc;
+        atomicAdd(&ctr->fallback, 1ULL);
+      }
+      hll_flux<AXIS>(wl, wr, P, F);
+      ++evaluated;
+    }
     if (f > 0) {  // cell f-1 has both of its faces
       const long long dc = d0 + (long long)(f - 1) * ds;
 #pragma unroll
@@ -160,6 +200,7 @@ k_sweep(const double* __restrict__ W, double* __restrict__ ACC, double* __restri
     dcur = dnext;
     hprev = hcur;
   }
+  warp_count(&ctr->faces, evaluated);
 }
 
 }  // namespace

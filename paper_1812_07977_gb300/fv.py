@@ -23,7 +23,8 @@ PRECISION = {"fp64": 0, "fp64_fma": 1, "fp32_bulk": 2}
 ABI_SYMBOLS = (
     "fv_create_mesh", "fv_destroy_mesh", "fv_set_state", "fv_get_state",
     "fv_get_ghosted_state", "fv_reduce_dt", "fv_step", "fv_substep", "fv_fill_ghosts",
-    "fv_conserved_sums", "fv_get_counters", "fv_set_tuning", "fv_profile_enable",
+    "fv_conserved_sums", "fv_get_counters", "fv_get_face_counts", "fv_set_tuning",
+    "fv_profile_enable",
     "fv_profile_read",
     "fv_mesh_info", "fv_status_string", "fv_last_error", "fv_conserved_sums_noalloc",
     "fv_batch_create", "fv_batch_destroy", "fv_batch_set_state", "fv_batch_get_state",
@@ -77,6 +78,8 @@ def load_library(path: str | None = None):
         "fv_conserved_sums": ([vp, dp], i),
         "fv_get_counters": ([vp, ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(ctypes.c_longlong)], i),
+        "fv_get_face_counts": ([vp, ctypes.POINTER(ctypes.c_longlong),
+                                ctypes.POINTER(ctypes.c_longlong)], i),
         "fv_set_tuning": ([vp, i, d], i),
         "fv_profile_enable": ([vp, i], i),
         "fv_profile_read": ([vp, dp, ctypes.POINTER(ctypes.c_longlong)], i),
@@ -252,6 +255,13 @@ class Mesh:
         a, b = ctypes.c_longlong(), ctypes.c_longlong()
         _check(self._lib.fv_get_counters(self._h, ctypes.byref(a), ctypes.byref(b)),
                "fv_get_counters")
+        return a.value, b.value
+
+    def face_counts(self):
+        """(evaluated, defined) face fluxes since the last set_state."""
+        a, b = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(self._lib.fv_get_face_counts(self._h, ctypes.byref(a), ctypes.byref(b)),
+               "fv_get_face_counts")
         return a.value, b.value
 
     def set_tuning(self, key: str, value):
