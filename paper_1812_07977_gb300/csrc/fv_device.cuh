@@ -46,6 +46,11 @@ __device__ __forceinline__ bool is_pos(double x) {
   return b > 0 && b <= kInfBits;
 }
 
+// x is neither infinite nor NaN
+__device__ __forceinline__ bool is_finite(double x) {
+  return (((unsigned)__double2hiint(x) >> 20) & 0x7FFu) != 0x7FFu;
+}
+
 // IEEE product on the FP64 pipe for the rare operands of half() and
 // twice().  A volatile asm statement cannot be executed speculatively, so
 // the compiler keeps it behind its branch instead of issuing the multiply

@@ -174,6 +174,17 @@ __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
   run = same32(w0, wm1) ? run + 1 : 1;
   run = same32(w1, w0) ? run + 1 : 1;
   unsigned xyfb = 0;   // fallbacks of this thread's x (bits 0, 1) and y (2, 3) faces
+  // which of those faces this tile counts: each face of the mesh is counted
+  // by one tile (face TX of a tile is face 0 of the next)
+  unsigned counted = 0;
+  for (int f = tid, pass = 0; f < kXFaces; f += kThreads, ++pass) {
+    const int r = f / (TX + 1), fi = f % (TX + 1);
+    if (i0 + fi <= P.nx && (fi < TX || i0 + fi == P.nx) && j0 + r < P.ny) counted |= 1u << pass;
+  }
+  for (int f = tid, pass = 2; f < kYFaces; f += kThreads, ++pass) {
+    const int fj = f / TX, c = f % TX;
+    if (i0 + c < P.nx && j0 + fj <= P.ny && (fj < TY || j0 + fj == P.ny)) counted |= 1u << pass;
+  }
   // the first chunk's lower face is the domain boundary face; later chunks
   // recompute a face the previous chunk counted
   if (k0 != 0 || !owner) fallbacks = 0;
@@ -261,8 +272,7 @@ __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
 #pragma unroll
         for (int q = 0; q < NF; ++q) s.fx[q][r][fi] = F[q];
       }
-      // each face counted by one tile: face TX of a tile is face 0 of the next
-      if (i0 + fi <= P.nx && (fi < TX || i0 + fi == P.nx) && j0 + r < P.ny) fallbacks += fb;
+      fallbacks += fb & (counted >> pass);
     }
     // (d) y faces: face fj (between rows fj-1 and fj) of column c
     for (int f = tid, pass = 2; f < kYFaces; f += kThreads, ++pass) {
@@ -282,7 +292,7 @@ __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
 #pragma unroll
         for (int q = 0; q < NF; ++q) s.fy[q][fj][c] = F[q];
       }
-      if (i0 + c < P.nx && j0 + fj <= P.ny && (fj < TY || j0 + fj == P.ny)) fallbacks += fb;
+      fallbacks += fb & (counted >> pass);
     }
     __syncthreads();
     // (e) update of cell (i, j, k): FP32 divergence, FP64 RK combine

@@ -102,6 +102,14 @@ __device__ __forceinline__ Prim half_slopes(double theta, const Prim& dm, const 
               half_slope<TK>(theta, dm.p, dp.p)};
 }
 
+// RK combine of one value: stage 1 U1 = U + du; stage 2 U = ((U + U1) + du) / 2
+template <int STAGE>
+__device__ __forceinline__ void rk_combine(double* __restrict__ U, double* __restrict__ U1,
+                                           long long gc, double du) {
+  if (STAGE == 1) U1[gc] = U[gc] + du;
+  else U[gc] = half((U[gc] + U1[gc]) + du);
+}
+
 // AXIS: 0, 1, 2.  STAGE: 0 for the x and y sweeps; 1 or 2 (the RK stage)
 // for the z sweep, which finishes the update.
 template <int AXIS, int STAGE, int TK>
@@ -154,7 +162,8 @@ k_sweep(const double* __restrict__ W, double* __restrict__ ACC, double* __restri
     // face f-3/2, so its flux (and fallback) is the previous face's, bit for
     // bit: reuse it.  (run >= 5 implies f >= 1.)  Decided per warp, so the
     // warp skips the flux only when every line can.
-    if (__all_sync(__activemask(), run >= 5)) {
+    const bool reused = __all_sync(__activemask(), run >= 5);
+    if (reused) {
       dnext = Prim{0.0, 0.0, 0.0, 0.0, 0.0};
       hcur = dnext;
 #pragma unroll
@@ -175,21 +184,35 @@ k_sweep(const double* __restrict__ W, double* __restrict__ ACC, double* __restri
       hll_flux<AXIS>(wl, wr, P, F);
       ++evaluated;
     }
+    // With the flux reused and finite, F - Fprev is +0 for every component:
+    // the x part of the divergence is -0 * inv = -0, and subtracting
+    // +0 * inv leaves ACC as it is (both exactly what the arithmetic gives),
+    // so the warp skips that arithmetic (and the y sweep its ACC update).
+    bool finite_f = reused;
+#pragma unroll
+    for (int q = 0; q < NF; ++q) finite_f = finite_f && is_finite(F[q]);
+    const bool zero_diff = __all_sync(__activemask(), finite_f);
     if (f > 0) {  // cell f-1 has both of its faces
       const long long dc = d0 + (long long)(f - 1) * ds;
+      if (zero_diff) {
 #pragma unroll
-      for (int q = 0; q < NF; ++q) {
-        const double diff = F[q] - Fprev[q];
-        if (AXIS == 0) {
-          ACC[q * nd + dc] = -diff * inv;
-        } else if (AXIS == 1) {
-          ACC[q * nd + dc] = ACC[q * nd + dc] - diff * inv;
-        } else {
-          const double acc = ACC[q * nd + dc] - diff * inv;
-          const double du = dt * acc;
-          const long long gc = q * nf + g0 + (long long)(f - 1) * gs;
-          if (STAGE == 1) U1[gc] = U[gc] + du;
-          else U[gc] = half((U[gc] + U1[gc]) + du);
+        for (int q = 0; q < NF; ++q) {
+          if (AXIS == 0) ACC[q * nd + dc] = -0.0;
+          if (AXIS == 2) rk_combine<STAGE>(U, U1, q * nf + g0 + (long long)(f - 1) * gs,
+                                            dt * ACC[q * nd + dc]);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+          const double diff = F[q] - Fprev[q];
+          if (AXIS == 0) {
+            ACC[q * nd + dc] = -diff * inv;
+          } else if (AXIS == 1) {
+            ACC[q * nd + dc] = ACC[q * nd + dc] - diff * inv;
+          } else {
+            const double acc = ACC[q * nd + dc] - diff * inv;
+            rk_combine<STAGE>(U, U1, q * nf + g0 + (long long)(f - 1) * gs, dt * acc);
+          }
         }
       }
     }

@@ -174,13 +174,23 @@ def rollout_error(net: Net, ref, gamma: float = 1.4, precision: str = "fp64_fma"
 
 
 def train(net: Net, data, epochs: int, lr: float, gamma: float = 1.4, seed: int = 0,
-          precision: str = "fp64_fma", val=None, log=None):
+          precision: str = "fp64_fma", val=None, log=None, noise: float = 0.0):
     """Adam over the samples for `epochs` epochs.  With a validation
     reference run `val`, the parameters of the epoch with the lowest mean
-    validation rollout error are kept (model selection by the judge)."""
+    validation rollout error are kept (model selection by the judge).
+
+    With `noise` > 0 each sample's input is perturbed by Gaussian noise of
+    `noise` times each conserved field's standard deviation, and the target
+    becomes what brings the coarse step of the perturbed state to the
+    averaged fine state: the network also learns to pull states that have
+    drifted off the training data back (noise injection against rollout
+    drift)."""
+    import torch
     cn = data[0][0].shape[-1]
     mesh = Mesh(cn, cn, cn, gamma=gamma, bc=PERIODIC, precision=precision)
     rng = np.random.default_rng(seed)
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    sd = torch.stack([U for U, _, _ in data]).std(dim=(0, 2, 3, 4))[:, None, None, None]
     losses, val_err = [], []
     best = (float("inf"), None, -1)
     t0 = time.perf_counter()
@@ -189,6 +199,18 @@ def train(net: Net, data, epochs: int, lr: float, gamma: float = 1.4, seed: int 
         tot = 0.0
         for i in rng.permutation(len(data)):
             Uc, dt, r = data[i]
+            if noise > 0.0:
+                # target state = coarse step of Uc + r; the residual of the
+                # perturbed input against it
+                mesh.set_state(Uc)
+                mesh.step(dt)
+                target = mesh.get_state() + r
+                Un = Uc + noise * sd * torch.randn(Uc.shape, generator=gen, device="cuda",
+                                                   dtype=Uc.dtype)
+                mesh.set_state(Un)
+                mesh.step(dt)
+                r = (target - mesh.get_state()).contiguous()
+                Uc = Un
             mesh.set_state(Uc)
             tot += net.train_step(mesh, r, dt, lr)
             steps += 1
@@ -218,7 +240,7 @@ def evaluate(net: Net, fine_n: int, factor: int, amp: float, nsteps: int, cfl: f
 
 def run(fine_n=256, factor=4, train_amps=(0.01, 0.04, 0.07, 0.1), val_amp=0.085,
         test_amp=0.055, samples=24, every=2, epochs=20, lr=1e-3, eval_steps=48, val_steps=16,
-        seed=0, rollout=False, log=None):
+        seed=0, rollout=False, log=None, noise=0.0):
     """The whole workflow: data from fine runs, training with model selection
     on a validation amplitude, evaluation on a held-out test amplitude.  If no
     epoch's correction beats the plain solver on the validation run, the
@@ -232,7 +254,7 @@ def run(fine_n=256, factor=4, train_amps=(0.01, 0.04, 0.07, 0.1), val_amp=0.085,
         net.set_params(initial_params(seed, net.nparam, scale=0.5))
         net.set_scales(*fit_scales(data))
         losses, t_train, train_steps, val_err, best_ep = train(net, data, epochs, lr, seed=seed,
-                                                               val=val, log=log)
+                                                               val=val, log=log, noise=noise)
         ev = evaluate(net, fine_n, factor, test_amp, eval_steps)
     use = min(val_err) < val_plain
     return {"fine": fine_n, "coarse": fine_n // factor, "samples": len(data),
@@ -240,7 +262,7 @@ def run(fine_n=256, factor=4, train_amps=(0.01, 0.04, 0.07, 0.1), val_amp=0.085,
             "train_steps": train_steps, "train_step_ms": 1e3 * t_train / max(train_steps, 1),
             "loss_first": losses[0], "loss_last": losses[-1], "best_epoch": best_ep,
             "val_l1_rho_plain": val_plain, "val_l1_rho_learned_best": min(val_err),
-            "use_learned": bool(use), **ev}
+            "use_learned": bool(use), "noise": noise, **ev}
 
 
 def initial_params(seed: int, nparam: int, scale: float = 1.0):
