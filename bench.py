@@ -61,7 +61,7 @@ BYTES_PER_ZONE_UPDATE = 200
 # DRAM bytes (read + write) per sweep launch, mean of the x, y and z sweeps of
 # the FP64-FMA build at 256^3 from one ncu capture
 # (profiles/k_sweep_fp64_fma_oblique256.md); None for builds not captured.
-SWEEP_TRAFFIC = {"fp64_fma": 2.56e9}
+SWEEP_TRAFFIC = {"fp64_fma": 2.18e9}
 
 
 def fp64_probe():
@@ -310,13 +310,13 @@ def run_learned(args):
     """The learned-correction workload: periodic shear layers (rho 1 and 2,
     vx +-0.5, vy = A sin(4 pi x), p = 2.5, gamma 1.4), fine 256^3 FP64 runs
     block-averaged 4x onto a 64^3 coarse mesh; training by the library's
-    kernels; evaluation on a held-out amplitude against the averaged fine
-    run, with and without the correction."""
+    kernels (with input-noise injection); evaluation on a held-out amplitude
+    against the averaged fine run, with and without the correction."""
     from paper_1812_07977_gb300 import learned
     r = learned.run(fine_n=args.learned_fine, factor=4, train_amps=(0.01, 0.04, 0.07, 0.1),
                     val_amp=0.085, test_amp=0.055, samples=args.learned_samples, every=2,
                     epochs=args.learned_epochs, lr=1e-3, eval_steps=args.learned_eval_steps,
-                    val_steps=args.learned_eval_steps)
+                    val_steps=args.learned_eval_steps, noise=args.learned_noise)
     out = {k: v for k, v in r.items() if not isinstance(v, list)}
     out["l1_rho_plain_mean"] = float(np.mean(r["l1_rho_plain"]))
     out["l1_rho_learned_mean"] = float(np.mean(r["l1_rho_learned"]))
@@ -556,6 +556,8 @@ def main():
     ap.add_argument("--learned-fine", type=int, default=256)
     ap.add_argument("--learned-samples", type=int, default=16)
     ap.add_argument("--learned-eval-steps", type=int, default=32)
+    ap.add_argument("--learned-noise", type=float, default=0.5,
+                    help="training-input noise, in units of each field's standard deviation")
     ap.add_argument("--shear-n", type=int, default=512)
     ap.add_argument("--shear-steps", type=int, default=100,
                     help="steps of the 512^3 shear-layer FP32-graph vs FP64 comparison (0: skip)")

@@ -57,7 +57,7 @@ typedef enum {
   FV_ERR_OOM = 2,           /* device or pinned host allocation failed */
   FV_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed */
   FV_ERR_NONPHYSICAL = 4,   /* a cell average had rho <= 0, p <= 0 or NaN */
-  FV_ERR_TIMEOUT = 5,       /* reserved: a bounded device wait gave up */
+  FV_ERR_TIMEOUT = 5,       /* a bounded device wait gave up (tensor-core convolutions) */
   FV_ERR_BAD_HANDLE = 6     /* NULL, destroyed or foreign mesh handle */
 } fv_status;
 
@@ -256,7 +256,13 @@ FV_API fv_status fv_batch_info(fv_batch_t b, int* nmesh, long long* total_cells,
  * phi(right cell) - phi(left cell), so a cell's state changes by
  *   dU = -sum_d dt/dx_d (phi(i+e_d) - 2 phi(i) + phi(i-e_d)),
  * which is conservative and zero for uniform states.  Weights and
- * activations are BF16, accumulation FP32.  Periodic meshes only.
+ * activations are BF16, accumulation FP32: the forward convolutions and
+ * the input-gradient (adjoint) convolutions of training run on the tensor
+ * cores (tcgen05 MMAs, accumulators in tensor memory); the backward pass
+ * feeds them its FP32 gradients rounded to BF16.  A convolution whose wait
+ * for its MMAs runs out records it; the next synchronising net call
+ * (fv_net_forward with o_out, fv_net_train_step) returns FV_ERR_TIMEOUT.
+ * Periodic meshes only.
  * Parameters (FP32, fv_net_param_count() of them) in the order
  *   w1 [32][5][27], b1 [32], w2 [32][32][27], b2 [32], w3 [5][32][27], b3 [5]
  * with kernel index o = 9 dz + 3 dy + dx for offsets (dz, dy, dx) - 1.

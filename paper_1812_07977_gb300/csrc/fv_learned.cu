@@ -21,6 +21,7 @@
 
 #include "fv.h"
 #include "fv_internal.h"
+#include "fv_umma.cuh"
 
 using bf16 = __nv_bfloat16;
 
@@ -67,50 +68,127 @@ __device__ __forceinline__ void load_tile(const TI* __restrict__ in, TI* s, cons
   }
 }
 
-template <int CI, int CO, class TI>
-constexpr size_t conv_smem() {
-  return (size_t)CI * 27 * CO * sizeof(float) + (size_t)CI * HN * sizeof(TI);
-}
+__device__ __forceinline__ bf16 to_bf(float v) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ bf16 to_bf(bf16 v) { return v; }
 
-// out[co][cell] = act(bias[co] + sum_{ci, o} w[co][ci][o] in[ci][cell + o - 1])
-// One thread per cell of an 8x8x4 tile; weights as FP32 in shared memory,
-// laid out [ci][o][co] so each thread reads 4 output channels at a time.
+// ---------------------------------------------------------------- tcgen05 conv
+// out[co][cell] = act(bias[co] + sum_{ci, o} w[co][ci][o] in[ci][cell + o - 1]) as an
+// implicit GEMM on the tensor cores: per output plane of a CTA tile, D (128 cells x CO, FP32
+// in TMEM) = sum over the 27 offsets o and over 16-channel K steps of A_o (128 x 16) B_o
+// (16 x CO), BF16 operands.  The tile's input (8 x 16 x 4 cells plus a one-cell periodic
+// halo) sits in shared memory channel-last in 8-channel slabs, [slab][halo cell][8 ch], so
+// every A_o is the same no-swizzle K-major layout at a shifted start: 8 consecutive x cells
+// form a core matrix, the next row of the tile is one halo row (160 B) further, the next 8
+// channels one slab further.  The weights are [offset][slab][co][8 ch] in shared memory.
+constexpr int UX = 8, UY = 16, UZ = 4;                 // output tile: UZ planes of 128 cells
+constexpr int UHX = UX + 2, UHY = UY + 2, UHZ = UZ + 2, UHN = UHX * UHY * UHZ;
+constexpr int UThreads = 128;                          // 4 warps: TMEM lanes 0..127
+constexpr int kMmaPolls = 1 << 20;                     // bounded wait for the MMAs
+
+template <int CI, int CO>
+struct UConv {
+  static constexpr int CIP = (CI + 15) / 16 * 16;      // K per offset (padded with zeros)
+  static constexpr int NP = (CO + 15) / 16 * 16;       // N (padded)
+  static constexpr int KC = CIP / 8;                   // 8-channel slabs
+  static constexpr size_t in_bytes = (size_t)KC * UHN * 16;
+  static constexpr size_t w_bytes = (size_t)27 * KC * NP * 16;
+  static constexpr size_t smem = in_bytes + w_bytes;
+  static constexpr uint32_t tmem_cols = UZ * NP <= 32 ? 32 : UZ * NP <= 64 ? 64 : 128;
+  static_assert(NP <= 32 && UZ * NP <= 128, "accumulator layout");
+};
+
 template <int CI, int CO, class TI, class TO, bool TANH>
-__global__ void __launch_bounds__(BT)
-k_conv_fwd(const TI* __restrict__ in, const bf16* __restrict__ w, const float* __restrict__ bias,
-           TO* __restrict__ out, Grid3 g) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  float* ws = reinterpret_cast<float*>(smem);
-  TI* is = reinterpret_cast<TI*>(smem + (size_t)CI * 27 * CO * sizeof(float));
-  const int ntx = tiles(g.nx, BX), nty = tiles(g.ny, BY);
-  const int bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, bz = blockIdx.x / (ntx * nty);
-  const int x0 = bx * BX, y0 = by * BY, z0 = bz * BZ;
-  for (int t = threadIdx.x; t < CO * CI * 27; t += blockDim.x) {
-    const int co = t / (CI * 27), r = t - co * CI * 27;  // r = ci * 27 + o
-    ws[r * CO + co] = __bfloat162float(w[t]);
+__global__ void __launch_bounds__(UThreads)
+k_conv_umma(const TI* __restrict__ in, const bf16* __restrict__ w, const float* __restrict__ bias,
+            TO* __restrict__ out, Grid3 g, unsigned* __restrict__ status) {
+  using C = UConv<CI, CO>;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint4* xs = reinterpret_cast<uint4*>(smem);
+  uint4* ws = reinterpret_cast<uint4*>(smem + C::in_bytes);
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int ntx = tiles(g.nx, UX), nty = tiles(g.ny, UY);
+  const int x0 = (blockIdx.x % ntx) * UX, y0 = ((blockIdx.x / ntx) % nty) * UY,
+            z0 = (blockIdx.x / (ntx * nty)) * UZ;
+  // weights: slab kc of offset o, row n = channels kc*8 .. kc*8+7 of w[n][.][o]
+  for (int t = tid; t < 27 * C::KC * C::NP; t += UThreads) {
+    const int n = t % C::NP, kc = (t / C::NP) % C::KC, o = t / (C::NP * C::KC);
+    __align__(16) bf16 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int ci = kc * 8 + j;
+      v[j] = (n < CO && ci < CI) ? w[(n * CI + ci) * 27 + o] : __float2bfloat16_rn(0.0f);
+    }
+    ws[t] = *reinterpret_cast<const uint4*>(v);
   }
-  load_tile<CI, TI>(in, is, g, x0, y0, z0);
+  // input halo tile (periodic), as BF16 slabs
+  for (int t = tid; t < C::KC * UHN; t += UThreads) {
+    const int c = t % UHN, kc = t / UHN;
+    const int lz = c / (UHX * UHY), ly = (c / UHX) % UHY, lx = c % UHX;
+    const long long cell = ((long long)wrap(z0 + lz - 1, g.nz) * g.ny + wrap(y0 + ly - 1, g.ny)) *
+                               g.nx + wrap(x0 + lx - 1, g.nx);
+    __align__(16) bf16 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int ci = kc * 8 + j;
+      v[j] = ci < CI ? to_bf(in[ci * g.n + cell]) : __float2bfloat16_rn(0.0f);
+    }
+    xs[t] = *reinterpret_cast<const uint4*>(v);
+  }
+  if (tid == 0) umma::mbar_init(&mbar, 1);
+  if (warp == 0) umma::tmem_alloc(&tmem_slot, C::tmem_cols);
+  umma::fence_smem_for_mma();
+  umma::fence_before_sync();
   __syncthreads();
-  const int lx = threadIdx.x % BX, ly = (threadIdx.x / BX) % BY, lz = threadIdx.x / (BX * BY);
-  float acc[CO];
+  umma::fence_after_sync();
+  const uint32_t tmem = tmem_slot;
+  if (tid == 0) {
+    constexpr uint32_t idesc = umma::idesc_bf16(128, C::NP);
+    const uint32_t xa = umma::smem_addr(xs), wa = umma::smem_addr(ws);
+    for (int z = 0; z < UZ; ++z) {
+      uint32_t acc = 0;
+      for (int o = 0; o < 27; ++o) {
+        const int dz = o / 9, dy = (o / 3) % 3, dx = o % 3;
+        const uint32_t cell0 = ((z + dz) * UHY + dy) * UHX + dx;
 #pragma unroll
-  for (int co = 0; co < CO; ++co) acc[co] = bias ? bias[co] : 0.0f;
-  for (int ci = 0; ci < CI; ++ci) {
+        for (int kk = 0; kk < C::CIP / 16; ++kk) {
+          const uint64_t a = umma::desc(xa + ((2 * kk) * UHN + cell0) * 16, UHN * 16, UHX * 16);
+          const uint64_t b = umma::desc(wa + ((o * C::KC + 2 * kk) * C::NP) * 16, C::NP * 16, 128);
+          umma::mma_bf16(tmem + z * C::NP, a, b, idesc, acc);
+          acc = 1;
+        }
+      }
+    }
+    umma::commit(&mbar);
+  }
+  const bool ok = __all_sync(0xffffffffu, umma::mbar_wait(&mbar, 0, kMmaPolls));
+  umma::fence_after_sync();
+  if (!ok) {
+    if ((tid & 31) == 0) atomicOr(status, 1u);
+  } else {
+    // row m of plane z's accumulator is cell (m % 8, m / 8) of that plane
+    const int gx = x0 + tid % UX, gy = y0 + tid / UX;
+#pragma unroll 1
+    for (int z = 0; z < UZ; ++z) {
+      float v[32];
+      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + z * C::NP;
+      umma::ld16(ta, v);
+      if (C::NP > 16) umma::ld16(ta + 16, v + 16);
+      const int gz = z0 + z;
+      if (gx < g.nx && gy < g.ny && gz < g.nz) {
+        const long long cell = ((long long)gz * g.ny + gy) * g.nx + gx;
 #pragma unroll
-    for (int o = 0; o < 27; ++o) {
-      const int dz = o / 9, dy = (o / 3) % 3, dx = o % 3;
-      const float x = to_f(is[ci * HN + ((lz + dz) * HY + (ly + dy)) * HX + (lx + dx)]);
-      const float* wp = ws + (ci * 27 + o) * CO;
-#pragma unroll
-      for (int co = 0; co < CO; ++co) acc[co] = fmaf(wp[co], x, acc[co]);
+        for (int co = 0; co < CO; ++co) {
+          const float a = v[co] + (bias ? bias[co] : 0.0f);
+          out[co * g.n + cell] = from_f<TO>(TANH ? tanhf(a) : a);
+        }
+      }
     }
   }
-  const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
-  if (gx < g.nx && gy < g.ny && gz < g.nz) {
-    const long long cell = ((long long)gz * g.ny + gy) * g.nx + gx;
-#pragma unroll
-    for (int co = 0; co < CO; ++co) out[co * g.n + cell] = from_f<TO>(TANH ? tanhf(acc[co]) : acc[co]);
-  }
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) umma::tmem_free(tmem, C::tmem_cols);
 }
 
 // Per-tile partial weight gradients: partial[tile][p][co] = sum over the
@@ -351,6 +429,8 @@ struct fv_net_s {
   float* partial = nullptr;
   double* loss_partial = nullptr;
   double* host_loss = nullptr;
+  unsigned* status = nullptr;       // device: set by a convolution whose MMA wait ran out
+  unsigned* host_status = nullptr;  // pinned mirror
 };
 
 namespace {
@@ -362,6 +442,15 @@ fv_status check(fv_net_t n) {
   std::lock_guard<std::mutex> lk(g_net_mutex);
   if (!g_nets.count(n)) return fail(FV_ERR_BAD_HANDLE, "network handle %p is not live", (void*)n);
   return FV_OK;
+}
+
+// Reports (and clears) a convolution whose tensor-core wait ran out; the
+// caller has copied the device word to host_status and synchronised.
+fv_status take_status(fv_net_s* n, cudaStream_t s) {
+  if (*n->host_status == 0u) return FV_OK;
+  *n->host_status = 0u;
+  cudaMemsetAsync(n->status, 0, sizeof(unsigned), s);
+  return fail(FV_ERR_TIMEOUT, "a tensor-core convolution did not complete within its wait limit");
 }
 
 void free_act(fv_net_s* n) {
@@ -391,6 +480,8 @@ void free_net(fv_net_s* n) {
   cudaFree(n->norm);
   cudaFree(n->loss_partial);
   cudaFreeHost(n->host_loss);
+  cudaFree(n->status);
+  cudaFreeHost(n->host_status);
   delete n;
 }
 
@@ -426,13 +517,13 @@ fv_status ensure_capacity(fv_net_s* n, const Grid3& g) {
 
 template <int CI, int CO, class TI, class TO, bool TANH>
 cudaError_t conv_fwd(const TI* in, const bf16* w, const float* bias, TO* out, const Grid3& g,
-                     cudaStream_t s) {
-  const size_t smem = conv_smem<CI, CO, TI>();
-  auto k = k_conv_fwd<CI, CO, TI, TO, TANH>;
+                     unsigned* status, cudaStream_t s) {
+  const size_t smem = UConv<CI, CO>::smem;
+  auto k = k_conv_umma<CI, CO, TI, TO, TANH>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int nb = tiles(g.nx, BX) * tiles(g.ny, BY) * tiles(g.nz, BZ);
-  k<<<nb, BT, smem, s>>>(in, w, bias, out, g);
+  const int nb = tiles(g.nx, UX) * tiles(g.ny, UY) * tiles(g.nz, UZ);
+  k<<<nb, UThreads, smem, s>>>(in, w, bias, out, g, status);
   return cudaGetLastError();
 }
 
@@ -464,11 +555,14 @@ fv_status forward(fv_net_s* n, const MeshView& v, const Grid3& g) {
                                            n->x, g.n);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess)
-    e = conv_fwd<CIN, CH, bf16, bf16, true>(n->x, n->wb + OW1, n->params + OB1, n->h1, g, s);
+    e = conv_fwd<CIN, CH, bf16, bf16, true>(n->x, n->wb + OW1, n->params + OB1, n->h1, g,
+                                            n->status, s);
   if (e == cudaSuccess)
-    e = conv_fwd<CH, CH, bf16, bf16, true>(n->h1, n->wb + OW2, n->params + OB2, n->h2, g, s);
+    e = conv_fwd<CH, CH, bf16, bf16, true>(n->h1, n->wb + OW2, n->params + OB2, n->h2, g,
+                                           n->status, s);
   if (e == cudaSuccess)
-    e = conv_fwd<CH, COUT, bf16, float, false>(n->h2, n->wb + OW3, n->params + OB3, n->o, g, s);
+    e = conv_fwd<CH, COUT, bf16, float, false>(n->h2, n->wb + OW3, n->params + OB3, n->o, g,
+                                               n->status, s);
   if (e != cudaSuccess) return cuda_fail(e, "network forward pass");
   return FV_OK;
 }
@@ -502,6 +596,9 @@ fv_status fv_net_create(fv_net_t* out) {
   if (e == cudaSuccess) e = cudaMalloc(&n->norm, 10 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&n->loss_partial, kLossBlocks * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&n->host_loss, kLossBlocks * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&n->status, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMallocHost(&n->host_status, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(n->status, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(n->params, 0, NPARAM * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(n->grads, 0, NPARAM * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(n->adam_m, 0, NPARAM * sizeof(float));
@@ -595,8 +692,12 @@ fv_status fv_net_forward(fv_net_t n, fv_mesh_t m, float* o_out) {
   if (o_out) {
     cudaError_t e = cudaMemcpyAsync(o_out, n->o, COUT * g.n * sizeof(float),
                                     cudaMemcpyDeviceToDevice, v.stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(n->host_status, n->status, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                          v.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(v.stream);
     if (e != cudaSuccess) return cuda_fail(e, "copying the network output");
+    if ((st = take_status(n, v.stream)) != FV_OK) return st;
   }
   return FV_OK;
 }
@@ -623,7 +724,7 @@ fv_status fv_net_train_step(fv_net_t n, fv_mesh_t m, const double* residual, dou
     e = conv_wgrad<CH, COUT, bf16>(n->h2, n->go, n->partial, n->grads, OW3, OB3, g, s);
   if (e == cudaSuccess) {
     k_flip_weights<<<(COUT * CH * 27 + 255) / 256, 256, 0, s>>>(n->wb + OW3, n->wt3, COUT, CH);
-    e = conv_fwd<COUT, CH, float, float, false>(n->go, n->wt3, nullptr, n->g2, g, s);
+    e = conv_fwd<COUT, CH, float, float, false>(n->go, n->wt3, nullptr, n->g2, g, n->status, s);
   }
   if (e == cudaSuccess) {
     k_tanh_bwd<<<grid_for(CH * g.n), 256, 0, s>>>(n->g2, n->h2, CH * g.n);
@@ -631,7 +732,7 @@ fv_status fv_net_train_step(fv_net_t n, fv_mesh_t m, const double* residual, dou
   }
   if (e == cudaSuccess) {
     k_flip_weights<<<(CH * CH * 27 + 255) / 256, 256, 0, s>>>(n->wb + OW2, n->wt2, CH, CH);
-    e = conv_fwd<CH, CH, float, float, false>(n->g2, n->wt2, nullptr, n->g1, g, s);
+    e = conv_fwd<CH, CH, float, float, false>(n->g2, n->wt2, nullptr, n->g1, g, n->status, s);
   }
   if (e == cudaSuccess) {
     k_tanh_bwd<<<grid_for(CH * g.n), 256, 0, s>>>(n->g1, n->h1, CH * g.n);
@@ -648,8 +749,11 @@ fv_status fv_net_train_step(fv_net_t n, fv_mesh_t m, const double* residual, dou
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(n->host_loss, n->loss_partial, kLossBlocks * sizeof(double),
                         cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(n->host_status, n->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "network training step");
+  if ((st = take_status(n, s)) != FV_OK) return st;
   if (loss_out) {
     double L = 0.0;
     for (int b = 0; b < kLossBlocks; ++b) L += n->host_loss[b];

@@ -174,17 +174,20 @@ def rollout_error(net: Net, ref, gamma: float = 1.4, precision: str = "fp64_fma"
 
 
 def train(net: Net, data, epochs: int, lr: float, gamma: float = 1.4, seed: int = 0,
-          precision: str = "fp64_fma", val=None, log=None, noise: float = 0.0):
+          precision: str = "fp64_fma", val=None, log=None, noise: float = 0.0,
+          denoise: bool = False):
     """Adam over the samples for `epochs` epochs.  With a validation
     reference run `val`, the parameters of the epoch with the lowest mean
     validation rollout error are kept (model selection by the judge).
 
     With `noise` > 0 each sample's input is perturbed by Gaussian noise of
-    `noise` times each conserved field's standard deviation, and the target
-    becomes what brings the coarse step of the perturbed state to the
-    averaged fine state: the network also learns to pull states that have
-    drifted off the training data back (noise injection against rollout
-    drift)."""
+    `noise` times each conserved field's standard deviation while the target
+    stays the sample's residual: training-noise injection against the drift
+    of long rollouts (as in Sanchez-Gonzalez et al. 2020, "Learning to
+    Simulate Complex Physics with Graph Networks").  With `denoise`, the
+    target instead becomes what brings the coarse step of the perturbed state
+    to the averaged fine state; a flux-form correction cannot remove white
+    noise, so that variant does not train."""
     import torch
     cn = data[0][0].shape[-1]
     mesh = Mesh(cn, cn, cn, gamma=gamma, bc=PERIODIC, precision=precision)
@@ -200,16 +203,17 @@ def train(net: Net, data, epochs: int, lr: float, gamma: float = 1.4, seed: int 
         for i in rng.permutation(len(data)):
             Uc, dt, r = data[i]
             if noise > 0.0:
-                # target state = coarse step of Uc + r; the residual of the
-                # perturbed input against it
-                mesh.set_state(Uc)
-                mesh.step(dt)
-                target = mesh.get_state() + r
                 Un = Uc + noise * sd * torch.randn(Uc.shape, generator=gen, device="cuda",
                                                    dtype=Uc.dtype)
-                mesh.set_state(Un)
-                mesh.step(dt)
-                r = (target - mesh.get_state()).contiguous()
+                if denoise:
+                    # target state = coarse step of Uc + r; the residual of
+                    # the perturbed input against it
+                    mesh.set_state(Uc)
+                    mesh.step(dt)
+                    target = mesh.get_state() + r
+                    mesh.set_state(Un)
+                    mesh.step(dt)
+                    r = (target - mesh.get_state()).contiguous()
                 Uc = Un
             mesh.set_state(Uc)
             tot += net.train_step(mesh, r, dt, lr)
@@ -240,7 +244,7 @@ def evaluate(net: Net, fine_n: int, factor: int, amp: float, nsteps: int, cfl: f
 
 def run(fine_n=256, factor=4, train_amps=(0.01, 0.04, 0.07, 0.1), val_amp=0.085,
         test_amp=0.055, samples=24, every=2, epochs=20, lr=1e-3, eval_steps=48, val_steps=16,
-        seed=0, rollout=False, log=None, noise=0.0):
+        seed=0, rollout=False, log=None, noise=0.0, denoise=False):
     """The whole workflow: data from fine runs, training with model selection
     on a validation amplitude, evaluation on a held-out test amplitude.  If no
     epoch's correction beats the plain solver on the validation run, the
@@ -254,7 +258,8 @@ def run(fine_n=256, factor=4, train_amps=(0.01, 0.04, 0.07, 0.1), val_amp=0.085,
         net.set_params(initial_params(seed, net.nparam, scale=0.5))
         net.set_scales(*fit_scales(data))
         losses, t_train, train_steps, val_err, best_ep = train(net, data, epochs, lr, seed=seed,
-                                                               val=val, log=log, noise=noise)
+                                                               val=val, log=log, noise=noise,
+                                                               denoise=denoise)
         ev = evaluate(net, fine_n, factor, test_amp, eval_steps)
     use = min(val_err) < val_plain
     return {"fine": fine_n, "coarse": fine_n // factor, "samples": len(data),

@@ -30,3 +30,20 @@ def test_trained_correction_beats_the_plain_coarse_solver():
     assert r["l1_rho_learned"][-1] < r["l1_rho_plain"][-1]
     assert r["fallbacks"] == 0
     assert r["use_learned"] and r["val_l1_rho_learned_best"] < r["val_l1_rho_plain"]
+
+
+def test_trained_correction_gains_at_the_configured_workload():
+    """The configured workload: 256^3 fine runs averaged to a 64^3 coarse
+    mesh, 32-step rollouts.  Without noise injection the corrected run
+    drifts past the plain one over 32 steps; with training-input noise of
+    half a standard deviation the correction must cut the mean L1 density
+    error at least 3x on the held-out amplitude and be kept by the judge."""
+    from paper_1812_07977_gb300 import learned
+    r = learned.run(fine_n=256, factor=4, train_amps=(0.01, 0.04, 0.07, 0.1), val_amp=0.085,
+                    test_amp=0.055, samples=16, every=2, epochs=16, lr=1e-3, eval_steps=32,
+                    val_steps=32, noise=0.5)
+    plain, corr = np.mean(r["l1_rho_plain"]), np.mean(r["l1_rho_learned"])
+    print("64^3: L1 density error plain", plain, "learned", corr)
+    assert r["use_learned"] and r["fallbacks"] == 0
+    assert corr < plain / 3.0
+    assert r["l1_rho_learned"][-1] < 0.5 * r["l1_rho_plain"][-1]
