@@ -62,6 +62,9 @@ BYTES_PER_ZONE_UPDATE = 200
 # the FP64-FMA build at 256^3 from one ncu capture
 # (profiles/k_sweep_fp64_fma_oblique256.md); None for builds not captured.
 SWEEP_TRAFFIC = {"fp64_fma": 2.18e9}
+# The same for the fused FP32-bulk substep kernel (mean of stage 1 and 2;
+# profiles/k_stage32_fp32_oblique256.md).
+FUSED_TRAFFIC = 1.71e9
 
 
 def fp64_probe():
@@ -453,7 +456,8 @@ def run_ours(args):
                 "achieved": fused_bytes / (fused_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                 "frac": fused_bytes / (fused_ms / 1e3) / 1e9 / hbm,
                 "avg_launch_ms": fused_ms / fused_launches,
-                "bytes_per_launch": 100 * zones, "traffic": None}
+                "bytes_per_launch": 100 * zones,
+                "traffic": FUSED_TRAFFIC if n == N else None}
             variants[prec]["hbm_roofline_whole_step"] = {
                 "achieved": BYTES_PER_ZONE_UPDATE * vval / 1e9, "peak": hbm, "unit": "GB/s",
                 "frac": BYTES_PER_ZONE_UPDATE * vval / 1e9 / hbm}
@@ -493,7 +497,8 @@ def run_ours(args):
     roofline = {"bound": "alu", "kernel": "k_sweep (x, y, z)", "achieved": achieved,
                 "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp64_peak if achieved else None,
-                "traffic": args.traffic if args.traffic else SWEEP_TRAFFIC.get(args.precision),
+                "traffic": args.traffic if args.traffic else
+                (SWEEP_TRAFFIC.get(args.precision) if n == N else None),
                 "peak_source": peak_source, "derived_peak": derived_peak,
                 "flops_per_launch": executed_flops / max(sweep_launches, 1),
                 "avg_launch_ms": sweep_ms / max(sweep_launches, 1),
