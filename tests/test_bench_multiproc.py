@@ -26,7 +26,8 @@ import bench
 rank, world, local = bench._dist()
 bench._barrier(world)
 m = bench._max_over_ranks(10.0 + rank, world, "cpu")
-print("RESULT", rank, world, m, flush=True)
+sys.stdout.write(f"RESULT {{rank}} {{world}} {{m}}\n")   # one write: ranks share the pipe
+sys.stdout.flush()
 """
 
 
