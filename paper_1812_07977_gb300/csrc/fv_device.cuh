@@ -46,6 +46,11 @@ __device__ __forceinline__ bool is_pos(double x) {
   return b > 0 && b <= kInfBits;
 }
 
+// x is -0 (bit pattern 0x8000000000000000; tested on the two halves)
+__device__ __forceinline__ bool is_neg_zero(double x) {
+  return (unsigned)__double2hiint(x) == 0x80000000u && (unsigned)__double2loint(x) == 0u;
+}
+
 // x is neither infinite nor NaN
 __device__ __forceinline__ bool is_finite(double x) {
   return (((unsigned)__double2hiint(x) >> 20) & 0x7FFu) != 0x7FFu;

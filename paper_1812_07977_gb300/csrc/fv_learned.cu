@@ -194,46 +194,59 @@ k_conv_umma(const TI* __restrict__ in, const bf16* __restrict__ w, const float* 
 // Per-tile partial weight gradients: partial[tile][p][co] = sum over the
 // tile's cells of gout[co][cell] * in[ci][cell + o - 1], p = ci * 27 + o, and
 // p = CI * 27 for the bias (in = 1).  A second kernel sums the tiles in a
-// fixed order, so the gradient is deterministic.
+// fixed order, so the gradient is deterministic.  The tile's output
+// gradients sit in shared memory as [cell][co] (CO padded to a multiple of
+// 4), so a thread reads a cell's CO values as broadcast 16-byte loads.
+template <int CO>
+__host__ __device__ constexpr int padded4() { return (CO + 3) / 4 * 4; }
+
 template <int CI, int CO, class TI>
 __global__ void __launch_bounds__(BT)
 k_conv_wgrad(const TI* __restrict__ in, const float* __restrict__ gout,
              float* __restrict__ partial, Grid3 g) {
+  constexpr int CP = padded4<CO>();
   extern __shared__ __align__(16) unsigned char smem[];
-  float* gs = reinterpret_cast<float*>(smem);  // [CO][BT]
-  TI* is = reinterpret_cast<TI*>(smem + (size_t)CO * BT * sizeof(float));
+  float* gs = reinterpret_cast<float*>(smem);  // [BT][CP]
+  TI* is = reinterpret_cast<TI*>(smem + (size_t)CP * BT * sizeof(float));
   const int ntx = tiles(g.nx, BX), nty = tiles(g.ny, BY);
   const int bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, bz = blockIdx.x / (ntx * nty);
   const int x0 = bx * BX, y0 = by * BY, z0 = bz * BZ;
-  for (int t = threadIdx.x; t < CO * BT; t += blockDim.x) {
+  for (int t = threadIdx.x; t < CP * BT; t += blockDim.x) {
     const int co = t / BT, c = t - co * BT;
     const int gx = x0 + c % BX, gy = y0 + (c / BX) % BY, gz = z0 + c / (BX * BY);
-    gs[t] = (gx < g.nx && gy < g.ny && gz < g.nz)
-                ? gout[co * g.n + ((long long)gz * g.ny + gy) * g.nx + gx]
-                : 0.0f;
+    gs[c * CP + co] = (co < CO && gx < g.nx && gy < g.ny && gz < g.nz)
+                          ? gout[co * g.n + ((long long)gz * g.ny + gy) * g.nx + gx]
+                          : 0.0f;
   }
   load_tile<CI, TI>(in, is, g, x0, y0, z0);
   __syncthreads();
   constexpr int NP = CI * 27 + 1;
   float* dst = partial + (size_t)blockIdx.x * NP * CO;
   for (int p = threadIdx.x; p < NP; p += blockDim.x) {
-    float acc[CO];
+    float acc[CP];
 #pragma unroll
-    for (int co = 0; co < CO; ++co) acc[co] = 0.0f;
-    if (p == CI * 27) {
-      for (int c = 0; c < BT; ++c)
+    for (int co = 0; co < CP; ++co) acc[co] = 0.0f;
+    const bool is_bias = p == CI * 27;
+    const int ci = is_bias ? 0 : p / 27, o = is_bias ? 0 : p % 27;
+    const int dz = o / 9, dy = (o / 3) % 3, dx = o % 3;
+    int c = 0;
+    for (int lz = 0; lz < BZ; ++lz)
+      for (int ly = 0; ly < BY; ++ly) {
+        const TI* row = is + ci * HN + ((lz + dz) * HY + (ly + dy)) * HX + dx;
 #pragma unroll
-        for (int co = 0; co < CO; ++co) acc[co] += gs[co * BT + c];
-    } else {
-      const int ci = p / 27, o = p % 27;
-      const int dz = o / 9, dy = (o / 3) % 3, dx = o % 3;
-      for (int c = 0; c < BT; ++c) {
-        const int lx = c % BX, ly = (c / BX) % BY, lz = c / (BX * BY);
-        const float x = to_f(is[ci * HN + ((lz + dz) * HY + (ly + dy)) * HX + (lx + dx)]);
+        for (int lx = 0; lx < BX; ++lx, ++c) {
+          const float x = is_bias ? 1.0f : to_f(row[lx]);
+          const float4* gv = reinterpret_cast<const float4*>(gs + c * CP);
 #pragma unroll
-        for (int co = 0; co < CO; ++co) acc[co] = fmaf(gs[co * BT + c], x, acc[co]);
+          for (int v = 0; v < CP / 4; ++v) {
+            const float4 q = gv[v];
+            acc[4 * v] = fmaf(q.x, x, acc[4 * v]);
+            acc[4 * v + 1] = fmaf(q.y, x, acc[4 * v + 1]);
+            acc[4 * v + 2] = fmaf(q.z, x, acc[4 * v + 2]);
+            acc[4 * v + 3] = fmaf(q.w, x, acc[4 * v + 3]);
+          }
+        }
       }
-    }
 #pragma unroll
     for (int co = 0; co < CO; ++co) dst[p * CO + co] = acc[co];
   }
@@ -530,7 +543,7 @@ cudaError_t conv_fwd(const TI* in, const bf16* w, const float* bias, TO* out, co
 template <int CI, int CO, class TI>
 cudaError_t conv_wgrad(const TI* in, const float* gout, float* partial, float* grads, int woff,
                        int boff, const Grid3& g, cudaStream_t s) {
-  const size_t smem = (size_t)CO * BT * sizeof(float) + (size_t)CI * HN * sizeof(TI);
+  const size_t smem = (size_t)padded4<CO>() * BT * sizeof(float) + (size_t)CI * HN * sizeof(TI);
   auto k = k_conv_wgrad<CI, CO, TI>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

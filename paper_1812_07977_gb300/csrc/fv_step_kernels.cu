@@ -195,11 +195,33 @@ k_sweep(const double* __restrict__ W, double* __restrict__ ACC, double* __restri
     if (f > 0) {  // cell f-1 has both of its faces
       const long long dc = d0 + (long long)(f - 1) * ds;
       if (zero_diff) {
+        if (AXIS == 0) {
 #pragma unroll
-        for (int q = 0; q < NF; ++q) {
-          if (AXIS == 0) ACC[q * nd + dc] = -0.0;
-          if (AXIS == 2) rk_combine<STAGE>(U, U1, q * nf + g0 + (long long)(f - 1) * gs,
-                                            dt * ACC[q * nd + dc]);
+          for (int q = 0; q < NF; ++q) ACC[q * nd + dc] = -0.0;
+        }
+        if (AXIS == 2) {
+          // acc = ACC.  Where no axis had a flux difference every component
+          // is -0 (the x sweep stored -0, the others subtracted nothing), so
+          // du = dt * acc = -0 and x + du = x for every x: stage 1 is the copy
+          // U1 = U and stage 2 is U = (U + U1) / 2, bit for bit.
+          double acc[NF];
+          bool neg_zero = true;
+#pragma unroll
+          for (int q = 0; q < NF; ++q) {
+            acc[q] = ACC[q * nd + dc];
+            neg_zero = neg_zero && is_neg_zero(acc[q]);
+          }
+          const long long gc0 = g0 + (long long)(f - 1) * gs;
+          if (__all_sync(__activemask(), neg_zero)) {
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+              if (STAGE == 1) U1[q * nf + gc0] = U[q * nf + gc0];
+              else U[q * nf + gc0] = half(U[q * nf + gc0] + U1[q * nf + gc0]);
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < NF; ++q) rk_combine<STAGE>(U, U1, q * nf + gc0, dt * acc[q]);
+          }
         }
       } else {
 #pragma unroll
