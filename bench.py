@@ -61,7 +61,7 @@ BYTES_PER_ZONE_UPDATE = 200
 # DRAM bytes (read + write) per sweep launch, mean of the x, y and z sweeps of
 # the FP64-FMA build at 256^3 from one ncu capture
 # (profiles/k_sweep_fp64_fma_oblique256.md); None for builds not captured.
-SWEEP_TRAFFIC = {"fp64_fma": 2.18e9}
+SWEEP_TRAFFIC = {"fp64_fma": 2.17e9}
 # The same for the fused FP32-bulk substep kernel (mean of stage 1 and 2;
 # profiles/k_stage32_fp32_oblique256.md).
 FUSED_TRAFFIC = 1.71e9
