@@ -1,7 +1,7 @@
-// fv_aux.cu -- ghost fill (GhostExchange), CFL time step (ComputeTimeStep),
-// conservation sums, and the interior <-> ghosted copies of set/get state.
-// Built without FMA contraction: the time step's arithmetic is the method's
-// definition operation by operation.
+// fv_aux.cu -- ghost fill (GhostExchange), conservation sums, and the
+// interior <-> ghosted copies of set/get state.  Built without FMA
+// contraction.  (The FP64 time step, ComputeTimeStep, is compiled with the
+// step kernels, in both of their arithmetic variants.)
 #include "fv_device.cuh"
 #include "fv_internal.h"
 
@@ -25,70 +25,6 @@ k_fill_ghosts(double* __restrict__ U, Params P) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x)
     fill_ghost_cell(U, P, t);
-}
-
-// ---------------------------------------------------------------- time step
-// s = ((|vx|+c)/dx + (|vy|+c)/dy) + (|vz|+c)/dz per interior cell; the
-// maximum over cells is exact in any order.  Non-negative doubles order
-// like their bit patterns, so the grid-wide maximum is an integer atomicMax.
-// A NaN s never wins, as in a plain `if (s > smax)` loop.
-// A cell equal bit for bit to the thread's previous cell has the same speed
-// (already in smax) and the same validity; when the whole warp has such
-// cells (uniform regions), it skips the arithmetic.
-__global__ void __launch_bounds__(kThreads)
-k_reduce_dt(const double* __restrict__ U, Params P, DevCounters* ctr) {
-  const long long n = (long long)P.nx * P.ny * P.nz;
-  double smax = 0.0;
-  unsigned long long bad = 0;
-  double up[NF] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  bool have = false, bad_prev = false;
-  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < n;
-       m += (long long)gridDim.x * blockDim.x) {
-    const long long k = m / ((long long)P.nx * P.ny);
-    const long long r = m - k * ((long long)P.nx * P.ny);
-    const long long j = r / P.nx, i = r - j * P.nx;
-    const long long g = (k + 2) * P.sz + (j + 2) * P.sy + (i + 2);
-    double u[NF];
-    bool eq = have;
-#pragma unroll
-    for (int q = 0; q < NF; ++q) {
-      u[q] = U[q * P.nfield + g];
-      eq = eq && bits(u[q]) == bits(up[q]);
-      up[q] = u[q];
-    }
-    have = true;
-    if (__all_sync(__activemask(), eq)) {
-      bad += bad_prev;
-      continue;
-    }
-    const Prim w = cons_to_prim(u, P);
-    bad_prev = !(is_pos(w.r) && is_pos(w.p));
-    bad += bad_prev;
-    const double c = sqrt(P.gamma * w.p / w.r);
-    const double s = ((fabs(w.vx) + c) * P.inv_d[0] + (fabs(w.vy) + c) * P.inv_d[1]) +
-                     (fabs(w.vz) + c) * P.inv_d[2];
-    if (s > smax) smax = s;
-  }
-  unsigned long long sb = (unsigned long long)__double_as_longlong(smax);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long v = __shfl_xor_sync(0xffffffffu, sb, o);
-    sb = v > sb ? v : sb;
-  }
-  __shared__ unsigned long long warp_max[kThreads / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) warp_max[wid] = sb;
-  if (bad) atomicAdd(&ctr->np_dt, bad);
-  __syncthreads();
-  if (wid == 0) {
-    sb = lane < kThreads / 32 ? warp_max[lane] : 0ULL;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long v = __shfl_xor_sync(0xffffffffu, sb, o);
-      sb = v > sb ? v : sb;
-    }
-    if (lane == 0) atomicMax(&ctr->smax_bits, sb);
-  }
 }
 
 // ---------------------------------------------------------------- copies
@@ -190,13 +126,6 @@ long long next_pow2(long long n) {
 
 cudaError_t launch_fill_ghosts(double* U, const Params& P, cudaStream_t s) {
   k_fill_ghosts<<<grid_for(ring_cells(P)), kThreads, 0, s>>>(U, P);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_reduce_dt(const double* U, const Params& P, DevCounters* ctr, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(&ctr->smax_bits, 0, sizeof(unsigned long long), s);
-  if (e != cudaSuccess) return e;
-  k_reduce_dt<<<grid_for((long long)P.nx * P.ny * P.nz), kThreads, 0, s>>>(U, P, ctr);
   return cudaGetLastError();
 }
 

@@ -431,7 +431,9 @@ fv_status fv_reduce_dt(fv_mesh_t m, double cfl, double* dt_out) {
     return m->desc.precision == FV_PREC_FP32_BULK
                ? fv_fp32::launch_reduce_dt(m->buf.U, m->P, m->vacuum_ratio, m->buf.ctr,
                                            m->stream)
-               : launch_reduce_dt(m->buf.U, m->P, m->buf.ctr, m->stream);
+               : m->desc.precision == FV_PREC_FP64_FMA
+                     ? fv_fp64_fma::launch_reduce_dt(m->buf.U, m->P, m->buf.ctr, m->stream)
+                     : fv_fp64_exact::launch_reduce_dt(m->buf.U, m->P, m->buf.ctr, m->stream);
   });
   if (e != cudaSuccess) return cuda_fail(e, "time-step kernel");
   if ((st = read_counters(m)) != FV_OK) return st;

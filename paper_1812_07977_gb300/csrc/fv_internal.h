@@ -44,6 +44,8 @@ struct StepBuffers {
                           cudaStream_t s);                                                 \
   cudaError_t launch_sweep(int axis, int stage, const StepBuffers& b, const fvd::Params& P, \
                            double dt, cudaStream_t s);                                     \
+  cudaError_t launch_reduce_dt(const double* U, const fvd::Params& P, DevCounters* ctr,     \
+                               cudaStream_t s);                                            \
   }
 FV_DECLARE_STEP_VARIANT(fv_fp64_exact)
 FV_DECLARE_STEP_VARIANT(fv_fp64_fma)
@@ -95,8 +97,6 @@ fvd32::Params32 make_params32(const fvd::Params& P, double vacuum_ratio);
 
 // fv_aux.cu (always built without contraction)
 cudaError_t launch_fill_ghosts(double* U, const fvd::Params& P, cudaStream_t s);
-cudaError_t launch_reduce_dt(const double* U, const fvd::Params& P, DevCounters* ctr,
-                             cudaStream_t s);
 cudaError_t launch_scatter_interior(const double* dense, double* U, const fvd::Params& P,
                                     cudaStream_t s);
 cudaError_t launch_gather_interior(const double* U, double* dense, const fvd::Params& P,
