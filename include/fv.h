@@ -67,8 +67,14 @@ typedef enum { FV_BC_OUTFLOW = 0, FV_BC_PERIODIC = 1 } fv_bc;
  *  FV_PREC_FP64      FP64, every operation rounded separately in the order
  *                    of the method's definition (no fused multiply-add):
  *                    bitwise reproducible against a plain IEEE FP64 code.
- *  FV_PREC_FP64_FMA  FP64 with fused multiply-add contraction: the same
- *                    method, a few ulp per operation away from FV_PREC_FP64.
+ *  FV_PREC_FP64_FMA  FP64 with fused multiply-add contraction, and each
+ *                    divide and square root (sound speeds, HLL weights, 1/rho)
+ *                    as an FP32 seed refined by two Newton-Raphson steps in
+ *                    FP64: the same method, a few ulp per operation away from
+ *                    FV_PREC_FP64 (held to 1e-12 relative of each field).
+ *  Both FP64 forms evaluate a face's flux once and reuse it, bit for bit, for
+ *  the next face of a grid line when the cells around both are equal (see
+ *  fv_get_face_counts).
  */
 /*  FV_PREC_FP32_BULK FP64 state, FP32 bulk arithmetic: reconstruction, wave
  *                    speeds, HLL fluxes and the flux divergence in FP32 (one
@@ -122,8 +128,11 @@ FV_API fv_status fv_get_state(fv_mesh_t m, double* U, int on_device);
 FV_API fv_status fv_get_ghosted_state(fv_mesh_t m, double* U, int on_device);
 
 /* ComputeTimeStep (Algorithm 1): *dt_out = cfl / max over interior
- * cells of sum_d (|v_d| + c) / dx_d with c = sqrt(gamma p / rho).  The
- * maximum is exact (order-free).  Only valid at a step boundary.
+ * cells of sum_d (|v_d| + c) / dx_d with c = sqrt(gamma p / rho), in the
+ * mesh's arithmetic (FP64: IEEE operations in the method's order, bit for
+ * bit; FP64_FMA: contracted, Newton-Raphson divide and square root, within
+ * a few ulps; FP32_BULK: per-cell speeds in FP32).  The maximum is exact
+ * (order-free).  Only valid at a step boundary.
  * Synchronising (one 24-byte device-to-host read).  Errors: INVALID_ARG
  * (cfl <= 0, dt_out NULL, stage pending), NONPHYSICAL. */
 FV_API fv_status fv_reduce_dt(fv_mesh_t m, double cfl, double* dt_out);

@@ -19,6 +19,11 @@
 //        memory;
 //   update: dU = dt * (-(Fx(i+1/2)-Fx(i-1/2))/dx - (..)/dy - (..)/dz) in FP32,
 //        then the RK combine in FP64 on the FP64 state.
+// Flux reuse (bit for bit what evaluating gives): a z face whose column has
+// five equal cells around it takes the previous z flux; an x or y face whose
+// four cells all equal those one plane below keeps that plane's flux (each
+// plane's primitives are stored with a per-cell "equal to the plane below"
+// flag).  Both are decided per warp.
 #include "fv_device32.cuh"
 #include "fv_internal.h"
 
@@ -73,14 +78,6 @@ __device__ __forceinline__ bool same32(const Prim32& a, const Prim32& b) {
 __device__ __forceinline__ void smem_store_flag(Smem& s, int row, int col, const Prim32& w,
                                                 bool valid) {
   s.same[row][col] = valid && same32(smem_prim(s, row, col), w);
-  s.w[0][row][col] = w.r;
-  s.w[1][row][col] = w.vx;
-  s.w[2][row][col] = w.vy;
-  s.w[3][row][col] = w.vz;
-  s.w[4][row][col] = w.p;
-}
-
-__device__ __forceinline__ void smem_store(Smem& s, int row, int col, const Prim32& w) {
   s.w[0][row][col] = w.r;
   s.w[1][row][col] = w.vx;
   s.w[2][row][col] = w.vy;

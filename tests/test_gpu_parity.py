@@ -415,3 +415,64 @@ def test_full_size_256_sampled_windows(precision):
         else:
             err = np.abs(win - ref).reshape(5, -1).max(1)
             assert np.all(err <= 1e-12 * scale), (where, err / np.maximum(scale, 1e-300))
+
+
+def _window_refs(U0_dev, n, dts, windows, w, gamma):
+    """Oracle runs on the sub-boxes around each window (outflow at their cut:
+    the window depends only on inputs within 4 cells per step)."""
+    halo = 4 * len(dts)
+    refs = []
+    for (i0, j0, k0) in windows:
+        lo = [c - halo for c in (i0, j0, k0)]
+        hi = [c + w + halo for c in (i0, j0, k0)]
+        sub = U0_dev[:, lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]].cpu().numpy()
+        ns = [hi[a] - lo[a] for a in range(3)]
+        om = oracle.mesh(*ns, lx=ns[0] / n, ly=ns[1] / n, lz=ns[2] / n, gamma=gamma)
+        Uo = oracle.ghosted_from_interior(om, np.ascontiguousarray(sub))
+        for dt in dts:
+            oracle.step(om, Uo, dt)
+        refs.append(oracle.interior(Uo)[:, halo:halo + w, halo:halo + w, halo:halo + w])
+    return refs
+
+
+def test_shear_layer_512_sampled_windows():
+    """The 512^3 periodic shear-layer workload (gamma 5/3, 8-mode seeded
+    perturbation): two FP64 steps (exact build) match the oracle bit for bit
+    on interior windows, and two FP32-bulk steps of the graph-replayed batch
+    of one mesh (its own CFL steps) stay within FP32 rounding of the oracle
+    run on the same steps."""
+    from paper_1812_07977_gb300.fv import Batch, Mesh
+    n, g53, w = 512, 5.0 / 3.0, 8
+    U0 = problems.shear_layer_device(n, 0.01, gamma=g53, modes=8, seed=2024, device="cuda")
+    rng = np.random.default_rng(1)
+    windows = [(100, 100, 100), (250, 120, 380), (400, 255, 60)] + \
+        [tuple(int(v) for v in rng.integers(16, n - 16 - w, 3)) for _ in range(3)]
+    m = Mesh(n, n, n, gamma=g53, bc=("periodic",) * 3)
+    m.set_state(U0)
+    dts = []
+    for _ in range(2):
+        dts.append(m.reduce_dt(0.4))
+        m.step(dts[-1])
+    got = m.get_state()
+    m.close()
+    for (i0, j0, k0), ref in zip(windows, _window_refs(U0, n, dts, windows, w, g53)):
+        win = got[:, k0:k0 + w, j0:j0 + w, i0:i0 + w].cpu().numpy()
+        assert np.array_equal(win, ref), (i0, j0, k0)
+    del got
+    stream = torch.cuda.Stream()
+    b = Batch([(n, n, n)], gamma=g53, bc=("periodic",) * 3, stream=stream)
+    b.set_state(0, U0)
+    dts32 = []
+    for _ in range(2):
+        b.step(0.4, use_graph=True)
+        dts32.append(float(b.dts()[0]))
+    got = b.get_state(0)
+    b.close()
+    # field scales; the three momenta share the momentum magnitude's (vy and
+    # vz are 1% perturbations, FP32 rounds the O(1) fluxes that move them)
+    scale = U0.abs().reshape(5, -1).amax(1).cpu().numpy()
+    scale[1:4] = scale[1:4].max()
+    for (i0, j0, k0), ref in zip(windows, _window_refs(U0, n, dts32, windows, w, g53)):
+        win = got[:, k0:k0 + w, j0:j0 + w, i0:i0 + w].cpu().numpy()
+        err = np.abs(win - ref).reshape(5, -1).max(1) / scale
+        assert np.all(err < 1e-6), ((i0, j0, k0), err)
