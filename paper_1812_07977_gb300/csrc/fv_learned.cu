@@ -82,7 +82,8 @@ __device__ __forceinline__ bf16 to_bf(bf16 v) { return v; }
 // channels one slab further.  The weights are [offset][slab][co][8 ch] in shared memory.
 constexpr int UX = 8, UY = 16, UZ = 4;                 // output tile: UZ planes of 128 cells
 constexpr int UHX = UX + 2, UHY = UY + 2, UHZ = UZ + 2, UHN = UHX * UHY * UHZ;
-constexpr int UThreads = 128;                          // 4 warps: TMEM lanes 0..127
+constexpr int UThreads = 384;                          // 12 warps gather the operands; warps
+                                                       // 0..3 read TMEM lanes 0..127 back
 constexpr int kMmaPolls = 1 << 20;                     // bounded wait for the MMAs
 
 template <int CI, int CO>
@@ -97,10 +98,29 @@ struct UConv {
   static_assert(NP <= 32 && UZ * NP <= 128, "accumulator layout");
 };
 
+// The weights in the convolution's shared-memory layout: entry (o, kc, n) =
+// channels kc*8 .. kc*8+7 of w[n][.][o] (zero beyond CI and CO).  Laid out
+// once per call, so every CTA copies them with 16-byte loads.
+template <int CI, int CO>
+__global__ void k_umma_weights(const bf16* __restrict__ w, uint4* __restrict__ wl) {
+  using C = UConv<CI, CO>;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 27 * C::KC * C::NP) return;
+  const int n = t % C::NP, kc = (t / C::NP) % C::KC, o = t / (C::NP * C::KC);
+  __align__(16) bf16 v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int ci = kc * 8 + j;
+    v[j] = (n < CO && ci < CI) ? w[(n * CI + ci) * 27 + o] : __float2bfloat16_rn(0.0f);
+  }
+  wl[t] = *reinterpret_cast<const uint4*>(v);
+}
+
 template <int CI, int CO, class TI, class TO, bool TANH>
 __global__ void __launch_bounds__(UThreads)
-k_conv_umma(const TI* __restrict__ in, const bf16* __restrict__ w, const float* __restrict__ bias,
-            TO* __restrict__ out, Grid3 g, unsigned* __restrict__ status) {
+k_conv_umma(const TI* __restrict__ in, const uint4* __restrict__ wl,
+            const float* __restrict__ bias, TO* __restrict__ out, Grid3 g,
+            unsigned* __restrict__ status) {
   using C = UConv<CI, CO>;
   extern __shared__ __align__(1024) unsigned char smem[];
   uint4* xs = reinterpret_cast<uint4*>(smem);
@@ -111,17 +131,7 @@ k_conv_umma(const TI* __restrict__ in, const bf16* __restrict__ w, const float* 
   const int ntx = tiles(g.nx, UX), nty = tiles(g.ny, UY);
   const int x0 = (blockIdx.x % ntx) * UX, y0 = ((blockIdx.x / ntx) % nty) * UY,
             z0 = (blockIdx.x / (ntx * nty)) * UZ;
-  // weights: slab kc of offset o, row n = channels kc*8 .. kc*8+7 of w[n][.][o]
-  for (int t = tid; t < 27 * C::KC * C::NP; t += UThreads) {
-    const int n = t % C::NP, kc = (t / C::NP) % C::KC, o = t / (C::NP * C::KC);
-    __align__(16) bf16 v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int ci = kc * 8 + j;
-      v[j] = (n < CO && ci < CI) ? w[(n * CI + ci) * 27 + o] : __float2bfloat16_rn(0.0f);
-    }
-    ws[t] = *reinterpret_cast<const uint4*>(v);
-  }
+  for (int t = tid; t < 27 * C::KC * C::NP; t += UThreads) ws[t] = wl[t];
   // input halo tile (periodic), as BF16 slabs
   for (int t = tid; t < C::KC * UHN; t += UThreads) {
     const int c = t % UHN, kc = t / UHN;
@@ -166,7 +176,7 @@ k_conv_umma(const TI* __restrict__ in, const bf16* __restrict__ w, const float* 
   umma::fence_after_sync();
   if (!ok) {
     if ((tid & 31) == 0) atomicOr(status, 1u);
-  } else {
+  } else if (warp < 4) {
     // row m of plane z's accumulator is cell (m % 8, m / 8) of that plane
     const int gx = x0 + tid % UX, gy = y0 + tid / UX;
 #pragma unroll 1
@@ -442,6 +452,7 @@ struct fv_net_s {
   float* partial = nullptr;
   double* loss_partial = nullptr;
   double* host_loss = nullptr;
+  uint4* wlay = nullptr;            // laid-out weights of the convolution being run
   unsigned* status = nullptr;       // device: set by a convolution whose MMA wait ran out
   unsigned* host_status = nullptr;  // pinned mirror
 };
@@ -495,6 +506,7 @@ void free_net(fv_net_s* n) {
   cudaFreeHost(n->host_loss);
   cudaFree(n->status);
   cudaFreeHost(n->host_status);
+  cudaFree(n->wlay);
   delete n;
 }
 
@@ -528,15 +540,19 @@ fv_status ensure_capacity(fv_net_s* n, const Grid3& g) {
   return FV_OK;
 }
 
+// wl: scratch for the laid-out weights (at least UConv<CI, CO>::w_bytes)
 template <int CI, int CO, class TI, class TO, bool TANH>
 cudaError_t conv_fwd(const TI* in, const bf16* w, const float* bias, TO* out, const Grid3& g,
-                     unsigned* status, cudaStream_t s) {
-  const size_t smem = UConv<CI, CO>::smem;
+                     uint4* wl, unsigned* status, cudaStream_t s) {
+  using C = UConv<CI, CO>;
+  const int nw = 27 * C::KC * C::NP;
+  k_umma_weights<CI, CO><<<(nw + 255) / 256, 256, 0, s>>>(w, wl);
+  const size_t smem = C::smem;
   auto k = k_conv_umma<CI, CO, TI, TO, TANH>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int nb = tiles(g.nx, UX) * tiles(g.ny, UY) * tiles(g.nz, UZ);
-  k<<<nb, UThreads, smem, s>>>(in, w, bias, out, g, status);
+  k<<<nb, UThreads, smem, s>>>(in, wl, bias, out, g, status);
   return cudaGetLastError();
 }
 
@@ -569,13 +585,13 @@ fv_status forward(fv_net_s* n, const MeshView& v, const Grid3& g) {
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess)
     e = conv_fwd<CIN, CH, bf16, bf16, true>(n->x, n->wb + OW1, n->params + OB1, n->h1, g,
-                                            n->status, s);
+                                            n->wlay, n->status, s);
   if (e == cudaSuccess)
     e = conv_fwd<CH, CH, bf16, bf16, true>(n->h1, n->wb + OW2, n->params + OB2, n->h2, g,
-                                           n->status, s);
+                                           n->wlay, n->status, s);
   if (e == cudaSuccess)
     e = conv_fwd<CH, COUT, bf16, float, false>(n->h2, n->wb + OW3, n->params + OB3, n->o, g,
-                                               n->status, s);
+                                               n->wlay, n->status, s);
   if (e != cudaSuccess) return cuda_fail(e, "network forward pass");
   return FV_OK;
 }
@@ -610,6 +626,7 @@ fv_status fv_net_create(fv_net_t* out) {
   if (e == cudaSuccess) e = cudaMalloc(&n->loss_partial, kLossBlocks * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&n->host_loss, kLossBlocks * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&n->status, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc(&n->wlay, UConv<CH, CH>::w_bytes);
   if (e == cudaSuccess) e = cudaMallocHost(&n->host_status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(n->status, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(n->params, 0, NPARAM * sizeof(float));
@@ -737,7 +754,8 @@ fv_status fv_net_train_step(fv_net_t n, fv_mesh_t m, const double* residual, dou
     e = conv_wgrad<CH, COUT, bf16>(n->h2, n->go, n->partial, n->grads, OW3, OB3, g, s);
   if (e == cudaSuccess) {
     k_flip_weights<<<(COUT * CH * 27 + 255) / 256, 256, 0, s>>>(n->wb + OW3, n->wt3, COUT, CH);
-    e = conv_fwd<COUT, CH, float, float, false>(n->go, n->wt3, nullptr, n->g2, g, n->status, s);
+    e = conv_fwd<COUT, CH, float, float, false>(n->go, n->wt3, nullptr, n->g2, g, n->wlay,
+                                                n->status, s);
   }
   if (e == cudaSuccess) {
     k_tanh_bwd<<<grid_for(CH * g.n), 256, 0, s>>>(n->g2, n->h2, CH * g.n);
@@ -745,7 +763,8 @@ fv_status fv_net_train_step(fv_net_t n, fv_mesh_t m, const double* residual, dou
   }
   if (e == cudaSuccess) {
     k_flip_weights<<<(CH * CH * 27 + 255) / 256, 256, 0, s>>>(n->wb + OW2, n->wt2, CH, CH);
-    e = conv_fwd<CH, CH, float, float, false>(n->g2, n->wt2, nullptr, n->g1, g, n->status, s);
+    e = conv_fwd<CH, CH, float, float, false>(n->g2, n->wt2, nullptr, n->g1, g, n->wlay,
+                                              n->status, s);
   }
   if (e == cudaSuccess) {
     k_tanh_bwd<<<grid_for(CH * g.n), 256, 0, s>>>(n->g1, n->h1, CH * g.n);
