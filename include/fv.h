@@ -265,10 +265,11 @@ FV_API fv_status fv_batch_info(fv_batch_t b, int* nmesh, long long* total_cells,
  * phi(right cell) - phi(left cell), so a cell's state changes by
  *   dU = -sum_d dt/dx_d (phi(i+e_d) - 2 phi(i) + phi(i-e_d)),
  * which is conservative and zero for uniform states.  Weights and
- * activations are BF16, accumulation FP32: the forward convolutions and
- * the input-gradient (adjoint) convolutions of training run on the tensor
- * cores (tcgen05 MMAs, accumulators in tensor memory); the backward pass
- * feeds them its FP32 gradients rounded to BF16.  A convolution whose wait
+ * activations are BF16, accumulation FP32: the forward convolutions, the
+ * input-gradient (adjoint) convolutions and the weight gradients of
+ * training run on the tensor cores (tcgen05 MMAs, accumulators in tensor
+ * memory); the backward pass feeds them its FP32 gradients rounded to BF16
+ * (bias gradients are summed in FP32).  A convolution whose wait
  * for its MMAs runs out records it; the next synchronising net call
  * (fv_net_forward with o_out, fv_net_train_step) returns FV_ERR_TIMEOUT.
  * Periodic meshes only.

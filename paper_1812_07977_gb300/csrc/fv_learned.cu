@@ -34,16 +34,12 @@ constexpr int OW1 = 0, OB1 = OW1 + CH * CIN * 27, OW2 = OB1 + CH, OB2 = OW2 + CH
               OW3 = OB2 + CH, OB3 = OW3 + COUT * CH * 27, NPARAM = OB3 + COUT;
 static_assert(NPARAM == 36357, "parameter layout");
 
-constexpr int BX = 8, BY = 8, BZ = 4, BT = BX * BY * BZ;      // 256 cells per tile
-constexpr int HX = BX + 2, HY = BY + 2, HZ = BZ + 2, HN = HX * HY * HZ;
 
 struct Grid3 {
   int nx, ny, nz;
   long long n;
 };
 
-__device__ __forceinline__ float to_f(float v) { return v; }
-__device__ __forceinline__ float to_f(bf16 v) { return __bfloat162float(v); }
 template <class T> __device__ __forceinline__ T from_f(float v);
 template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
 template <> __device__ __forceinline__ bf16 from_f<bf16>(float v) { return __float2bfloat16_rn(v); }
@@ -54,19 +50,6 @@ __device__ __forceinline__ int wrap(int v, int n) {
 }
 
 __host__ __device__ inline int tiles(int n, int b) { return (n + b - 1) / b; }
-
-// Loads the tile's input with a one-cell periodic halo, CI channels.
-template <int CI, class TI>
-__device__ __forceinline__ void load_tile(const TI* __restrict__ in, TI* s, const Grid3& g, int x0,
-                                          int y0, int z0) {
-  for (int t = threadIdx.x; t < CI * HN; t += blockDim.x) {
-    const int c = t / HN, r = t - c * HN;
-    const int lz = r / (HX * HY), ly = (r / HX) % HY, lx = r % HX;
-    const int gx = wrap(x0 + lx - 1, g.nx), gy = wrap(y0 + ly - 1, g.ny),
-              gz = wrap(z0 + lz - 1, g.nz);
-    s[t] = in[c * g.n + ((long long)gz * g.ny + gy) * g.nx + gx];
-  }
-}
 
 __device__ __forceinline__ bf16 to_bf(float v) { return __float2bfloat16_rn(v); }
 __device__ __forceinline__ bf16 to_bf(bf16 v) { return v; }
@@ -201,65 +184,163 @@ k_conv_umma(const TI* __restrict__ in, const uint4* __restrict__ wl,
   if (warp == 0) umma::tmem_free(tmem, C::tmem_cols);
 }
 
-// Per-tile partial weight gradients: partial[tile][p][co] = sum over the
-// tile's cells of gout[co][cell] * in[ci][cell + o - 1], p = ci * 27 + o, and
-// p = CI * 27 for the bias (in = 1).  A second kernel sums the tiles in a
-// fixed order, so the gradient is deterministic.  The tile's output
-// gradients sit in shared memory as [cell][co] (CO padded to a multiple of
-// 4), so a thread reads a cell's CO values as broadcast 16-byte loads.
-template <int CO>
-__host__ __device__ constexpr int padded4() { return (CO + 3) / 4 * 4; }
+// ---------------------------------------------------------------- tcgen05 weight gradient
+// Per tile of the convolution's 8 x 16 x 4 output cells, the partial weight
+// gradients partial[tile][p][co], p = ci * 27 + o (layout of k_conv_wgrad),
+//   sum over the tile's cells c of gout[co][c] * in[ci][c + o - 1],
+// as MMAs D[(o, ci)][co] += A[(o, ci)][c] B[c][co] with MN-major operands:
+// G offsets stacked along M (128 rows = G x CIP channels), K = the cells of
+// one plane (128), N = CO.  A is built per (offset group, plane) in shared
+// memory from the input tile (channel-last slabs, as in k_conv_umma) shifted
+// by each offset, so every 8-row group of M is one 2 KB slab of 128 cells;
+// B is the tile's output gradient as BF16 slabs [co slab][cell][8 co].  The
+// accumulators of all offset groups stay in TMEM for the tile's four planes.
+// Bias gradients (sum of gout over the tile) are summed in FP32.
+template <int CI, int CO>
+struct UWgrad {
+  static constexpr int CIP = (CI + 7) / 8 * 8;     // M rows per offset
+  static constexpr int KC = CIP / 8;               // input slabs
+  static constexpr int G = 128 / CIP;              // offsets per MMA
+  static constexpr int NG = (27 + G - 1) / G;      // offset groups
+  static constexpr int NP = (CO + 15) / 16 * 16;   // N
+  static constexpr int PC = UX * UY;               // cells of a plane (K of a plane)
+  static constexpr int TC = PC * UZ;               // cells of the tile
+  static constexpr size_t x_bytes = (size_t)KC * UHN * 16;
+  static constexpr size_t g_bytes = (size_t)(NP / 8) * TC * 16;
+  static constexpr size_t a_bytes = (size_t)G * KC * PC * 16;   // 128 rows x 128 cells
+  static constexpr size_t smem = x_bytes + g_bytes + a_bytes;
+  static constexpr uint32_t tmem_cols = NG * NP <= 32 ? 32 : NG * NP <= 64 ? 64 :
+                                        NG * NP <= 128 ? 128 : 256;
+  static_assert(G * CIP == 128 && NG * NP <= 256, "accumulator layout");
+};
 
 template <int CI, int CO, class TI>
-__global__ void __launch_bounds__(BT)
-k_conv_wgrad(const TI* __restrict__ in, const float* __restrict__ gout,
-             float* __restrict__ partial, Grid3 g) {
-  constexpr int CP = padded4<CO>();
-  extern __shared__ __align__(16) unsigned char smem[];
-  float* gs = reinterpret_cast<float*>(smem);  // [BT][CP]
-  TI* is = reinterpret_cast<TI*>(smem + (size_t)CP * BT * sizeof(float));
-  const int ntx = tiles(g.nx, BX), nty = tiles(g.ny, BY);
-  const int bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, bz = blockIdx.x / (ntx * nty);
-  const int x0 = bx * BX, y0 = by * BY, z0 = bz * BZ;
-  for (int t = threadIdx.x; t < CP * BT; t += blockDim.x) {
-    const int co = t / BT, c = t - co * BT;
-    const int gx = x0 + c % BX, gy = y0 + (c / BX) % BY, gz = z0 + c / (BX * BY);
-    gs[c * CP + co] = (co < CO && gx < g.nx && gy < g.ny && gz < g.nz)
-                          ? gout[co * g.n + ((long long)gz * g.ny + gy) * g.nx + gx]
-                          : 0.0f;
+__global__ void __launch_bounds__(UThreads)
+k_wgrad_umma(const TI* __restrict__ in, const float* __restrict__ gout,
+             float* __restrict__ partial, Grid3 g, unsigned* __restrict__ status) {
+  using C = UWgrad<CI, CO>;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint4* xs = reinterpret_cast<uint4*>(smem);
+  uint4* gs = reinterpret_cast<uint4*>(smem + C::x_bytes);
+  uint4* as = reinterpret_cast<uint4*>(smem + C::x_bytes + C::g_bytes);
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ float bsum[UThreads / 32][32];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntx = tiles(g.nx, UX), nty = tiles(g.ny, UY);
+  const int x0 = (blockIdx.x % ntx) * UX, y0 = ((blockIdx.x / ntx) % nty) * UY,
+            z0 = (blockIdx.x / (ntx * nty)) * UZ;
+  // input halo tile (periodic) as BF16 slabs [kc][halo cell][8 ch]
+  for (int t = tid; t < C::KC * UHN; t += UThreads) {
+    const int c = t % UHN, kc = t / UHN;
+    const int lz = c / (UHX * UHY), ly = (c / UHX) % UHY, lx = c % UHX;
+    const long long cell = ((long long)wrap(z0 + lz - 1, g.nz) * g.ny + wrap(y0 + ly - 1, g.ny)) *
+                               g.nx + wrap(x0 + lx - 1, g.nx);
+    __align__(16) bf16 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int ci = kc * 8 + j;
+      v[j] = ci < CI ? to_bf(in[ci * g.n + cell]) : __float2bfloat16_rn(0.0f);
+    }
+    xs[t] = *reinterpret_cast<const uint4*>(v);
   }
-  load_tile<CI, TI>(in, is, g, x0, y0, z0);
+  // output gradients of the tile's cells (0 outside the mesh) as BF16 slabs
+  // [co slab][cell][8 co]; cell = (z * UY + y) * UX + x
+  for (int t = tid; t < (C::NP / 8) * C::TC; t += UThreads) {
+    const int c = t % C::TC, cs = t / C::TC;
+    const int gx = x0 + c % UX, gy = y0 + (c / UX) % UY, gz = z0 + c / C::PC;
+    const bool in_mesh = gx < g.nx && gy < g.ny && gz < g.nz;
+    const long long cell = ((long long)gz * g.ny + gy) * g.nx + gx;
+    __align__(16) bf16 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int co = cs * 8 + j;
+      v[j] = __float2bfloat16_rn(in_mesh && co < CO ? gout[co * g.n + cell] : 0.0f);
+    }
+    gs[t] = *reinterpret_cast<const uint4*>(v);
+  }
+  // bias gradients in FP32: warp w sums outputs co = w, w + 12, ... over the tile
+  for (int co = warp; co < CO; co += UThreads / 32) {
+    float acc = 0.0f;
+    for (int c = lane; c < C::TC; c += 32) {
+      const int gx = x0 + c % UX, gy = y0 + (c / UX) % UY, gz = z0 + c / C::PC;
+      if (gx < g.nx && gy < g.ny && gz < g.nz)
+        acc += gout[co * g.n + ((long long)gz * g.ny + gy) * g.nx + gx];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) bsum[warp][co / (UThreads / 32)] = acc;
+  }
+  if (tid == 0) umma::mbar_init(&mbar, 1);
+  if (warp == 0) umma::tmem_alloc(&tmem_slot, C::tmem_cols);
+  umma::fence_before_sync();
   __syncthreads();
-  constexpr int NP = CI * 27 + 1;
-  float* dst = partial + (size_t)blockIdx.x * NP * CO;
-  for (int p = threadIdx.x; p < NP; p += blockDim.x) {
-    float acc[CP];
-#pragma unroll
-    for (int co = 0; co < CP; ++co) acc[co] = 0.0f;
-    const bool is_bias = p == CI * 27;
-    const int ci = is_bias ? 0 : p / 27, o = is_bias ? 0 : p % 27;
-    const int dz = o / 9, dy = (o / 3) % 3, dx = o % 3;
-    int c = 0;
-    for (int lz = 0; lz < BZ; ++lz)
-      for (int ly = 0; ly < BY; ++ly) {
-        const TI* row = is + ci * HN + ((lz + dz) * HY + (ly + dy)) * HX + dx;
-#pragma unroll
-        for (int lx = 0; lx < BX; ++lx, ++c) {
-          const float x = is_bias ? 1.0f : to_f(row[lx]);
-          const float4* gv = reinterpret_cast<const float4*>(gs + c * CP);
-#pragma unroll
-          for (int v = 0; v < CP / 4; ++v) {
-            const float4 q = gv[v];
-            acc[4 * v] = fmaf(q.x, x, acc[4 * v]);
-            acc[4 * v + 1] = fmaf(q.y, x, acc[4 * v + 1]);
-            acc[4 * v + 2] = fmaf(q.z, x, acc[4 * v + 2]);
-            acc[4 * v + 3] = fmaf(q.w, x, acc[4 * v + 3]);
-          }
+  umma::fence_after_sync();
+  const uint32_t tmem = tmem_slot;
+  constexpr uint32_t idesc = umma::idesc_bf16(128, C::NP) | (1u << 15) | (1u << 16);  // MN-major
+  bool ok = true;
+  int phase = 0;
+  for (int gi = 0; gi < C::NG; ++gi) {
+    for (int z = 0; z < UZ; ++z) {
+      // A for (group gi, plane z): slab (j, kc) holds channels kc*8.. of the
+      // plane's cells shifted by offset o = gi * G + j (zero past 26)
+      for (int t = tid; t < C::G * C::KC * C::PC; t += UThreads) {
+        const int c = t % C::PC, jk = t / C::PC, kc = jk % C::KC, j = jk / C::KC;
+        const int o = gi * C::G + j;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (o < 27) {
+          const int dz = o / 9, dy = (o / 3) % 3, dx = o % 3;
+          const int hc = ((z + dz) * UHY + (c / UX + dy)) * UHX + (c % UX + dx);
+          v = xs[kc * UHN + hc];
         }
+        as[t] = v;
       }
+      umma::fence_smem_for_mma();
+      umma::fence_before_sync();
+      __syncthreads();
+      umma::fence_after_sync();
+      if (tid == 0) {
+        const uint32_t aa = umma::smem_addr(as), ga = umma::smem_addr(gs);
 #pragma unroll
-    for (int co = 0; co < CO; ++co) dst[p * CO + co] = acc[co];
+        for (int ks = 0; ks < C::PC / 16; ++ks) {
+          const uint64_t a = umma::desc(aa + ks * 256, 128, C::PC * 16);
+          const uint64_t b = umma::desc(ga + (z * C::PC + ks * 16) * 16, 128, C::TC * 16);
+          umma::mma_bf16(tmem + gi * C::NP, a, b, idesc, (z > 0 || ks > 0) ? 1u : 0u);
+        }
+        umma::commit(&mbar);
+      }
+      // the MMAs must finish reading A before it is rebuilt; the whole block
+      // agrees on the outcome (a wait that ran out ends the loop for all)
+      ok = __syncthreads_and(umma::mbar_wait(&mbar, (uint32_t)(phase & 1), kMmaPolls)) != 0;
+      ++phase;
+      umma::fence_after_sync();
+      if (!ok) break;
+    }
+    if (!ok) break;
   }
+  float* dst = partial + (size_t)blockIdx.x * (CI * 27 + 1) * CO;
+  if (!ok) {
+    if (lane == 0) atomicOr(status, 1u);
+  } else if (warp < 4) {
+    // TMEM lane m = (j, ci) of group gi holds D[(o, ci)][0 .. NP)
+    const int m = tid, j = m / C::CIP, ci = m % C::CIP;
+#pragma unroll 1
+    for (int gi = 0; gi < C::NG; ++gi) {
+      float v[32];
+      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + gi * C::NP;
+      umma::ld16(ta, v);
+      if (C::NP > 16) umma::ld16(ta + 16, v + 16);
+      const int o = gi * C::G + j;
+      if (o < 27 && ci < CI) {
+#pragma unroll
+        for (int co = 0; co < CO; ++co) dst[(ci * 27 + o) * CO + co] = v[co];
+      }
+    }
+  }
+  if (tid < CO) dst[(CI * 27) * CO + tid] = bsum[tid % (UThreads / 32)][tid / (UThreads / 32)];
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) umma::tmem_free(tmem, C::tmem_cols);
 }
 
 // Sums the per-tile partials in tile order and scatters them into the flat
@@ -510,8 +591,9 @@ void free_net(fv_net_s* n) {
   delete n;
 }
 
+// tiles of the tensor-core kernels (one partial-gradient block each)
 long long tile_count(const Grid3& g) {
-  return (long long)tiles(g.nx, BX) * tiles(g.ny, BY) * tiles(g.nz, BZ);
+  return (long long)tiles(g.nx, UX) * tiles(g.ny, UY) * tiles(g.nz, UZ);
 }
 
 // Activation and gradient buffers for a mesh of g.n cells (grown on demand).
@@ -556,15 +638,17 @@ cudaError_t conv_fwd(const TI* in, const bf16* w, const float* bias, TO* out, co
   return cudaGetLastError();
 }
 
+// Weight gradients of one convolution: per-tile partials on the tensor
+// cores, then the fixed-order sum over tiles.
 template <int CI, int CO, class TI>
 cudaError_t conv_wgrad(const TI* in, const float* gout, float* partial, float* grads, int woff,
-                       int boff, const Grid3& g, cudaStream_t s) {
-  const size_t smem = (size_t)padded4<CO>() * BT * sizeof(float) + (size_t)CI * HN * sizeof(TI);
-  auto k = k_conv_wgrad<CI, CO, TI>;
+                       int boff, const Grid3& g, unsigned* status, cudaStream_t s) {
+  const size_t smem = UWgrad<CI, CO>::smem;
+  auto k = k_wgrad_umma<CI, CO, TI>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int nb = tiles(g.nx, BX) * tiles(g.ny, BY) * tiles(g.nz, BZ);
-  k<<<nb, BT, smem, s>>>(in, gout, partial, g);
+  const int nb = tiles(g.nx, UX) * tiles(g.ny, UY) * tiles(g.nz, UZ);
+  k<<<nb, UThreads, smem, s>>>(in, gout, partial, g, status);
   constexpr int NW = (CI * 27 + 1) * CO;
   k_wgrad_reduce<CI, CO><<<(NW + 255) / 256, 256, 0, s>>>(partial, nb, grads, woff, boff);
   return cudaGetLastError();
@@ -751,7 +835,7 @@ fv_status fv_net_train_step(fv_net_t n, fv_mesh_t m, const double* residual, dou
   cudaError_t e = cudaGetLastError();
   // layer 3: o = conv(h2; w3, b3)
   if (e == cudaSuccess)
-    e = conv_wgrad<CH, COUT, bf16>(n->h2, n->go, n->partial, n->grads, OW3, OB3, g, s);
+    e = conv_wgrad<CH, COUT, bf16>(n->h2, n->go, n->partial, n->grads, OW3, OB3, g, n->status, s);
   if (e == cudaSuccess) {
     k_flip_weights<<<(COUT * CH * 27 + 255) / 256, 256, 0, s>>>(n->wb + OW3, n->wt3, COUT, CH);
     e = conv_fwd<COUT, CH, float, float, false>(n->go, n->wt3, nullptr, n->g2, g, n->wlay,
@@ -759,7 +843,7 @@ fv_status fv_net_train_step(fv_net_t n, fv_mesh_t m, const double* residual, dou
   }
   if (e == cudaSuccess) {
     k_tanh_bwd<<<grid_for(CH * g.n), 256, 0, s>>>(n->g2, n->h2, CH * g.n);
-    e = conv_wgrad<CH, CH, bf16>(n->h1, n->g2, n->partial, n->grads, OW2, OB2, g, s);
+    e = conv_wgrad<CH, CH, bf16>(n->h1, n->g2, n->partial, n->grads, OW2, OB2, g, n->status, s);
   }
   if (e == cudaSuccess) {
     k_flip_weights<<<(CH * CH * 27 + 255) / 256, 256, 0, s>>>(n->wb + OW2, n->wt2, CH, CH);
@@ -768,7 +852,7 @@ fv_status fv_net_train_step(fv_net_t n, fv_mesh_t m, const double* residual, dou
   }
   if (e == cudaSuccess) {
     k_tanh_bwd<<<grid_for(CH * g.n), 256, 0, s>>>(n->g1, n->h1, CH * g.n);
-    e = conv_wgrad<CIN, CH, bf16>(n->x, n->g1, n->partial, n->grads, OW1, OB1, g, s);
+    e = conv_wgrad<CIN, CH, bf16>(n->x, n->g1, n->partial, n->grads, OW1, OB1, g, n->status, s);
   }
   if (e == cudaSuccess && lr > 0.0) {
     n->adam_t += 1;
