@@ -52,7 +52,51 @@ __device__ __forceinline__ int wrap(int v, int n) {
 __host__ __device__ inline int tiles(int n, int b) { return (n + b - 1) / b; }
 
 __device__ __forceinline__ bf16 to_bf(float v) { return __float2bfloat16_rn(v); }
-__device__ __forceinline__ bf16 to_bf(bf16 v) { return v; }
+
+// Activation layouts: channel-first [c][cell] (the network output and the
+// loss-side 5-channel gradients) or channel-last [cell][P], P = C rounded up
+// to 8 with zero pads (the 32-channel activations, their gradients and the
+// input features), where 8 channels of a cell are one 16-byte (BF16) or
+// two 16-byte (FP32) loads.
+template <int C>
+__host__ __device__ constexpr int pitch8() { return (C + 7) / 8 * 8; }
+
+// Channels kc*8 .. kc*8+7 of one cell as 8 BF16 (zero beyond C).
+template <int C, bool CL>
+__device__ __forceinline__ uint4 gather8(const bf16* __restrict__ in, long long n, long long cell,
+                                         int kc) {
+  if constexpr (CL) {
+    if (kc * 8 >= C) return make_uint4(0u, 0u, 0u, 0u);
+    return *reinterpret_cast<const uint4*>(in + cell * pitch8<C>() + kc * 8);
+  } else {
+    __align__(16) bf16 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = kc * 8 + j;
+      v[j] = c < C ? in[c * n + cell] : __float2bfloat16_rn(0.0f);
+    }
+    return *reinterpret_cast<const uint4*>(v);
+  }
+}
+template <int C, bool CL>
+__device__ __forceinline__ uint4 gather8(const float* __restrict__ in, long long n, long long cell,
+                                         int kc) {
+  __align__(16) bf16 v[8];
+  if constexpr (CL) {
+    if (kc * 8 >= C) return make_uint4(0u, 0u, 0u, 0u);
+    const float4 a = *reinterpret_cast<const float4*>(in + cell * pitch8<C>() + kc * 8);
+    const float4 b = *reinterpret_cast<const float4*>(in + cell * pitch8<C>() + kc * 8 + 4);
+    v[0] = to_bf(a.x); v[1] = to_bf(a.y); v[2] = to_bf(a.z); v[3] = to_bf(a.w);
+    v[4] = to_bf(b.x); v[5] = to_bf(b.y); v[6] = to_bf(b.z); v[7] = to_bf(b.w);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = kc * 8 + j;
+      v[j] = c < C ? to_bf(in[c * n + cell]) : __float2bfloat16_rn(0.0f);
+    }
+  }
+  return *reinterpret_cast<const uint4*>(v);
+}
 
 // ---------------------------------------------------------------- tcgen05 conv
 // out[co][cell] = act(bias[co] + sum_{ci, o} w[co][ci][o] in[ci][cell + o - 1]) as an
@@ -99,7 +143,7 @@ __global__ void k_umma_weights(const bf16* __restrict__ w, uint4* __restrict__ w
   wl[t] = *reinterpret_cast<const uint4*>(v);
 }
 
-template <int CI, int CO, class TI, class TO, bool TANH>
+template <int CI, int CO, class TI, class TO, bool TANH, bool ICL, bool OCL>
 __global__ void __launch_bounds__(UThreads)
 k_conv_umma(const TI* __restrict__ in, const uint4* __restrict__ wl,
             const float* __restrict__ bias, TO* __restrict__ out, Grid3 g,
@@ -114,20 +158,16 @@ k_conv_umma(const TI* __restrict__ in, const uint4* __restrict__ wl,
   const int ntx = tiles(g.nx, UX), nty = tiles(g.ny, UY);
   const int x0 = (blockIdx.x % ntx) * UX, y0 = ((blockIdx.x / ntx) % nty) * UY,
             z0 = (blockIdx.x / (ntx * nty)) * UZ;
+#pragma unroll 4
   for (int t = tid; t < 27 * C::KC * C::NP; t += UThreads) ws[t] = wl[t];
   // input halo tile (periodic), as BF16 slabs
+#pragma unroll 4
   for (int t = tid; t < C::KC * UHN; t += UThreads) {
     const int c = t % UHN, kc = t / UHN;
     const int lz = c / (UHX * UHY), ly = (c / UHX) % UHY, lx = c % UHX;
     const long long cell = ((long long)wrap(z0 + lz - 1, g.nz) * g.ny + wrap(y0 + ly - 1, g.ny)) *
                                g.nx + wrap(x0 + lx - 1, g.nx);
-    __align__(16) bf16 v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int ci = kc * 8 + j;
-      v[j] = ci < CI ? to_bf(in[ci * g.n + cell]) : __float2bfloat16_rn(0.0f);
-    }
-    xs[t] = *reinterpret_cast<const uint4*>(v);
+    xs[t] = gather8<CI, ICL>(in, g.n, cell, kc);
   }
   if (tid == 0) umma::mbar_init(&mbar, 1);
   if (warp == 0) umma::tmem_alloc(&tmem_slot, C::tmem_cols);
@@ -174,7 +214,24 @@ k_conv_umma(const TI* __restrict__ in, const uint4* __restrict__ wl,
 #pragma unroll
         for (int co = 0; co < CO; ++co) {
           const float a = v[co] + (bias ? bias[co] : 0.0f);
-          out[co * g.n + cell] = from_f<TO>(TANH ? tanhf(a) : a);
+          v[co] = TANH ? tanhf(a) : a;
+        }
+        if constexpr (OCL) {
+          // the row's channels as 16-byte stores ([cell][pitch], zero pads)
+          static_assert(sizeof(TO) == 2 || sizeof(TO) == 4, "output type");
+          constexpr int P = pitch8<CO>(), PER = 16 / (int)sizeof(TO);
+          uint4* dst = reinterpret_cast<uint4*>(out + cell * P);
+#pragma unroll
+          for (int q = 0; q < P / PER; ++q) {
+            __align__(16) TO w[PER];
+#pragma unroll
+            for (int e = 0; e < PER; ++e)
+              w[e] = from_f<TO>(q * PER + e < CO ? v[q * PER + e] : 0.0f);
+            dst[q] = *reinterpret_cast<const uint4*>(w);
+          }
+        } else {
+#pragma unroll
+          for (int co = 0; co < CO; ++co) out[co * g.n + cell] = from_f<TO>(v[co]);
         }
       }
     }
@@ -214,7 +271,7 @@ struct UWgrad {
   static_assert(G * CIP == 128 && NG * NP <= 256, "accumulator layout");
 };
 
-template <int CI, int CO, class TI>
+template <int CI, int CO, class TI, bool ICL, bool GCL>
 __global__ void __launch_bounds__(UThreads)
 k_wgrad_umma(const TI* __restrict__ in, const float* __restrict__ gout,
              float* __restrict__ partial, Grid3 g, unsigned* __restrict__ status) {
@@ -231,41 +288,33 @@ k_wgrad_umma(const TI* __restrict__ in, const float* __restrict__ gout,
   const int x0 = (blockIdx.x % ntx) * UX, y0 = ((blockIdx.x / ntx) % nty) * UY,
             z0 = (blockIdx.x / (ntx * nty)) * UZ;
   // input halo tile (periodic) as BF16 slabs [kc][halo cell][8 ch]
+#pragma unroll 4
   for (int t = tid; t < C::KC * UHN; t += UThreads) {
     const int c = t % UHN, kc = t / UHN;
     const int lz = c / (UHX * UHY), ly = (c / UHX) % UHY, lx = c % UHX;
     const long long cell = ((long long)wrap(z0 + lz - 1, g.nz) * g.ny + wrap(y0 + ly - 1, g.ny)) *
                                g.nx + wrap(x0 + lx - 1, g.nx);
-    __align__(16) bf16 v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int ci = kc * 8 + j;
-      v[j] = ci < CI ? to_bf(in[ci * g.n + cell]) : __float2bfloat16_rn(0.0f);
-    }
-    xs[t] = *reinterpret_cast<const uint4*>(v);
+    xs[t] = gather8<CI, ICL>(in, g.n, cell, kc);
   }
   // output gradients of the tile's cells (0 outside the mesh) as BF16 slabs
   // [co slab][cell][8 co]; cell = (z * UY + y) * UX + x
+#pragma unroll 4
   for (int t = tid; t < (C::NP / 8) * C::TC; t += UThreads) {
     const int c = t % C::TC, cs = t / C::TC;
     const int gx = x0 + c % UX, gy = y0 + (c / UX) % UY, gz = z0 + c / C::PC;
     const bool in_mesh = gx < g.nx && gy < g.ny && gz < g.nz;
     const long long cell = ((long long)gz * g.ny + gy) * g.nx + gx;
-    __align__(16) bf16 v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int co = cs * 8 + j;
-      v[j] = __float2bfloat16_rn(in_mesh && co < CO ? gout[co * g.n + cell] : 0.0f);
-    }
-    gs[t] = *reinterpret_cast<const uint4*>(v);
+    gs[t] = in_mesh ? gather8<CO, GCL>(gout, g.n, cell, cs) : make_uint4(0u, 0u, 0u, 0u);
   }
   // bias gradients in FP32: warp w sums outputs co = w, w + 12, ... over the tile
   for (int co = warp; co < CO; co += UThreads / 32) {
     float acc = 0.0f;
     for (int c = lane; c < C::TC; c += 32) {
       const int gx = x0 + c % UX, gy = y0 + (c / UX) % UY, gz = z0 + c / C::PC;
-      if (gx < g.nx && gy < g.ny && gz < g.nz)
-        acc += gout[co * g.n + ((long long)gz * g.ny + gy) * g.nx + gx];
+      if (gx < g.nx && gy < g.ny && gz < g.nz) {
+        const long long cell = ((long long)gz * g.ny + gy) * g.nx + gx;
+        acc += gout[GCL ? cell * pitch8<CO>() + co : co * g.n + cell];
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -284,6 +333,7 @@ k_wgrad_umma(const TI* __restrict__ in, const float* __restrict__ gout,
     for (int z = 0; z < UZ; ++z) {
       // A for (group gi, plane z): slab (j, kc) holds channels kc*8.. of the
       // plane's cells shifted by offset o = gi * G + j (zero past 26)
+#pragma unroll 4
       for (int t = tid; t < C::G * C::KC * C::PC; t += UThreads) {
         const int c = t % C::PC, jk = t / C::PC, kc = jk % C::KC, j = jk / C::KC;
         const int o = gi * C::G + j;
@@ -366,7 +416,8 @@ __global__ void k_flip_weights(const bf16* __restrict__ w, bf16* __restrict__ wt
   wt[(ci * CO + co) * 27 + (26 - o)] = w[t];
 }
 
-// Network input: normalised FP32 primitives of the interior cells, as BF16.
+// Network input: normalised FP32 primitives of the interior cells, as BF16,
+// channel-last with three zero pads ([cell][8]).
 __global__ void k_features(const double* __restrict__ U, fvd::Params P, fvd32::Params32 Q,
                            const float* __restrict__ norm /* mean[5], scale[5] */,
                            bf16* __restrict__ x, long long n) {
@@ -381,8 +432,11 @@ __global__ void k_features(const double* __restrict__ U, fvd::Params P, fvd32::P
     for (int q = 0; q < fvd::NF; ++q) u[q] = U[q * P.nfield + g];
     const fvd32::Prim32 w = fvd32::prim_from_state(u, Q);
     const float v[5] = {w.r, w.vx, w.vy, w.vz, w.p};
+    __align__(16) bf16 f[8];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) x[q * n + m] = __float2bfloat16_rn((v[q] - norm[q]) / norm[5 + q]);
+    for (int q = 0; q < 8; ++q)
+      f[q] = __float2bfloat16_rn(q < 5 ? (v[q] - norm[q]) / norm[5 + q] : 0.0f);
+    reinterpret_cast<uint4*>(x)[m] = *reinterpret_cast<const uint4*>(f);
   }
 }
 
@@ -603,7 +657,7 @@ fv_status ensure_capacity(fv_net_s* n, const Grid3& g) {
   free_act(n);
   const long long cc = std::max(cells, n->cap), tt = std::max(nt, n->cap_tiles);
   cudaError_t e;
-  if ((e = cudaMalloc(&n->x, CIN * cc * sizeof(bf16))) != cudaSuccess ||
+  if ((e = cudaMalloc(&n->x, pitch8<CIN>() * cc * sizeof(bf16))) != cudaSuccess ||
       (e = cudaMalloc(&n->h1, CH * cc * sizeof(bf16))) != cudaSuccess ||
       (e = cudaMalloc(&n->h2, CH * cc * sizeof(bf16))) != cudaSuccess ||
       (e = cudaMalloc(&n->o, COUT * cc * sizeof(float))) != cudaSuccess ||
@@ -623,14 +677,14 @@ fv_status ensure_capacity(fv_net_s* n, const Grid3& g) {
 }
 
 // wl: scratch for the laid-out weights (at least UConv<CI, CO>::w_bytes)
-template <int CI, int CO, class TI, class TO, bool TANH>
+template <int CI, int CO, class TI, class TO, bool TANH, bool ICL, bool OCL>
 cudaError_t conv_fwd(const TI* in, const bf16* w, const float* bias, TO* out, const Grid3& g,
                      uint4* wl, unsigned* status, cudaStream_t s) {
   using C = UConv<CI, CO>;
   const int nw = 27 * C::KC * C::NP;
   k_umma_weights<CI, CO><<<(nw + 255) / 256, 256, 0, s>>>(w, wl);
   const size_t smem = C::smem;
-  auto k = k_conv_umma<CI, CO, TI, TO, TANH>;
+  auto k = k_conv_umma<CI, CO, TI, TO, TANH, ICL, OCL>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int nb = tiles(g.nx, UX) * tiles(g.ny, UY) * tiles(g.nz, UZ);
@@ -640,11 +694,11 @@ cudaError_t conv_fwd(const TI* in, const bf16* w, const float* bias, TO* out, co
 
 // Weight gradients of one convolution: per-tile partials on the tensor
 // cores, then the fixed-order sum over tiles.
-template <int CI, int CO, class TI>
+template <int CI, int CO, class TI, bool ICL, bool GCL>
 cudaError_t conv_wgrad(const TI* in, const float* gout, float* partial, float* grads, int woff,
                        int boff, const Grid3& g, unsigned* status, cudaStream_t s) {
   const size_t smem = UWgrad<CI, CO>::smem;
-  auto k = k_wgrad_umma<CI, CO, TI>;
+  auto k = k_wgrad_umma<CI, CO, TI, ICL, GCL>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int nb = tiles(g.nx, UX) * tiles(g.ny, UY) * tiles(g.nz, UZ);
@@ -668,13 +722,13 @@ fv_status forward(fv_net_s* n, const MeshView& v, const Grid3& g) {
                                            n->x, g.n);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess)
-    e = conv_fwd<CIN, CH, bf16, bf16, true>(n->x, n->wb + OW1, n->params + OB1, n->h1, g,
+    e = conv_fwd<CIN, CH, bf16, bf16, true, true, true>(n->x, n->wb + OW1, n->params + OB1, n->h1, g,
                                             n->wlay, n->status, s);
   if (e == cudaSuccess)
-    e = conv_fwd<CH, CH, bf16, bf16, true>(n->h1, n->wb + OW2, n->params + OB2, n->h2, g,
+    e = conv_fwd<CH, CH, bf16, bf16, true, true, true>(n->h1, n->wb + OW2, n->params + OB2, n->h2, g,
                                            n->wlay, n->status, s);
   if (e == cudaSuccess)
-    e = conv_fwd<CH, COUT, bf16, float, false>(n->h2, n->wb + OW3, n->params + OB3, n->o, g,
+    e = conv_fwd<CH, COUT, bf16, float, false, true, false>(n->h2, n->wb + OW3, n->params + OB3, n->o, g,
                                                n->wlay, n->status, s);
   if (e != cudaSuccess) return cuda_fail(e, "network forward pass");
   return FV_OK;
@@ -835,24 +889,24 @@ fv_status fv_net_train_step(fv_net_t n, fv_mesh_t m, const double* residual, dou
   cudaError_t e = cudaGetLastError();
   // layer 3: o = conv(h2; w3, b3)
   if (e == cudaSuccess)
-    e = conv_wgrad<CH, COUT, bf16>(n->h2, n->go, n->partial, n->grads, OW3, OB3, g, n->status, s);
+    e = conv_wgrad<CH, COUT, bf16, true, false>(n->h2, n->go, n->partial, n->grads, OW3, OB3, g, n->status, s);
   if (e == cudaSuccess) {
     k_flip_weights<<<(COUT * CH * 27 + 255) / 256, 256, 0, s>>>(n->wb + OW3, n->wt3, COUT, CH);
-    e = conv_fwd<COUT, CH, float, float, false>(n->go, n->wt3, nullptr, n->g2, g, n->wlay,
+    e = conv_fwd<COUT, CH, float, float, false, false, true>(n->go, n->wt3, nullptr, n->g2, g, n->wlay,
                                                 n->status, s);
   }
   if (e == cudaSuccess) {
     k_tanh_bwd<<<grid_for(CH * g.n), 256, 0, s>>>(n->g2, n->h2, CH * g.n);
-    e = conv_wgrad<CH, CH, bf16>(n->h1, n->g2, n->partial, n->grads, OW2, OB2, g, n->status, s);
+    e = conv_wgrad<CH, CH, bf16, true, true>(n->h1, n->g2, n->partial, n->grads, OW2, OB2, g, n->status, s);
   }
   if (e == cudaSuccess) {
     k_flip_weights<<<(CH * CH * 27 + 255) / 256, 256, 0, s>>>(n->wb + OW2, n->wt2, CH, CH);
-    e = conv_fwd<CH, CH, float, float, false>(n->g2, n->wt2, nullptr, n->g1, g, n->wlay,
+    e = conv_fwd<CH, CH, float, float, false, true, true>(n->g2, n->wt2, nullptr, n->g1, g, n->wlay,
                                               n->status, s);
   }
   if (e == cudaSuccess) {
     k_tanh_bwd<<<grid_for(CH * g.n), 256, 0, s>>>(n->g1, n->h1, CH * g.n);
-    e = conv_wgrad<CIN, CH, bf16>(n->x, n->g1, n->partial, n->grads, OW1, OB1, g, n->status, s);
+    e = conv_wgrad<CIN, CH, bf16, true, true>(n->x, n->g1, n->partial, n->grads, OW1, OB1, g, n->status, s);
   }
   if (e == cudaSuccess && lr > 0.0) {
     n->adam_t += 1;

@@ -158,3 +158,20 @@ def test_rejects_non_periodic_mesh():
         m.set_state(problems.uniform(8, 8, 8, 1.0, (0, 0, 0), 1.0))
         with pytest.raises(FvError):
             net.forward(m)
+
+
+def test_bounded_mbarrier_wait(tmp_path):
+    """The tensor-core kernels' wait for their MMAs is bounded: on an
+    mbarrier that nothing arrives at it gives up after its poll limit (the
+    kernel then records FV_ERR_TIMEOUT instead of hanging), and on a completed
+    phase it returns at once (tests/cuda/mbar_wait_check.cu)."""
+    import os
+    import subprocess
+    from paper_1812_07977_gb300.build import ARCH, CSRC, INCLUDE, nvcc
+    here = os.path.dirname(os.path.abspath(__file__))
+    exe = str(tmp_path / "mbar_wait_check")
+    subprocess.run([nvcc(), *ARCH, "-O3", "-std=c++17", "-I", CSRC, "-I", INCLUDE,
+                    os.path.join(here, "cuda", "mbar_wait_check.cu"), "-o", exe], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    print(r.stdout)
+    assert r.returncode == 0 and "expired 1 completed 1" in r.stdout, r.stdout + r.stderr
