@@ -343,8 +343,20 @@ FV_API fv_status fv_conserved_sums_noalloc(const double* U, int nx, int ny, int 
  *                        0.99; a value > 1 turns the recovery off)
  *  FV_TUNE_OCCUPANCY     CTAs per SM the fused FP32-bulk kernel is built for:
  *                        2 (up to 128 registers, default) or 3 (80 registers)
+ *  FV_TUNE_SWEEP_SEGMENTS  FP64 paths: pieces each grid line of a sweep is
+ *                        cut into, to run more, shorter work items (integer
+ *                        in [0, 4096], capped at the line's length; 0, the
+ *                        default, picks by mesh size).  The results are the
+ *                        same bits for every value; each extra piece
+ *                        evaluates one face flux twice, which
+ *                        fv_get_face_counts counts.
  * Errors: INVALID_ARG for an unknown key or a value out of range. */
-typedef enum { FV_TUNE_KCHUNK = 0, FV_TUNE_VACUUM_RATIO = 1, FV_TUNE_OCCUPANCY = 2 } fv_tuning_key;
+typedef enum {
+  FV_TUNE_KCHUNK = 0,
+  FV_TUNE_VACUUM_RATIO = 1,
+  FV_TUNE_OCCUPANCY = 2,
+  FV_TUNE_SWEEP_SEGMENTS = 3
+} fv_tuning_key;
 FV_API fv_status fv_set_tuning(fv_mesh_t m, int key, double value);
 
 /* Mesh facts: interior sizes and the byte size of one device state. */

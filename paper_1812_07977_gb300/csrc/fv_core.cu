@@ -48,6 +48,7 @@ struct fv_mesh_s {
   fvd::Params P;
   cudaStream_t stream;
   int device;
+  int num_sms;              // multiprocessors of the device
   size_t state_doubles;     // 5 * nfield
   size_t dense_doubles;     // 5 * nx * ny * nz
   StepBuffers buf;
@@ -59,6 +60,7 @@ struct fv_mesh_s {
   int kchunk;               // z planes per CTA of the fused FP32-bulk kernel
   double vacuum_ratio;      // FP32-bulk FP64 pressure-recovery threshold
   int occupancy;            // CTAs per SM the fused kernel is compiled for (2 or 3)
+  int segments;             // pieces per grid line of the FP64 sweeps (0: automatic)
   // profiling
   bool prof_on;
   std::vector<cudaEvent_t> event_pool;
@@ -259,8 +261,10 @@ cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
   });
   for (int axis = 0; axis < 3 && e == cudaSuccess; ++axis) {
     e = timed(m, FV_KERNEL_SWEEP_X + axis, 1, [&] {
-      return fma ? fv_fp64_fma::launch_sweep(axis, stage, m->buf, m->P, dt, m->stream)
-                 : fv_fp64_exact::launch_sweep(axis, stage, m->buf, m->P, dt, m->stream);
+      return fma ? fv_fp64_fma::launch_sweep(axis, stage, m->buf, m->P, dt, m->segments,
+                                             m->num_sms, m->stream)
+                 : fv_fp64_exact::launch_sweep(axis, stage, m->buf, m->P, dt, m->segments,
+                                               m->num_sms, m->stream);
     });
   }
   if (e != cudaSuccess) return e;
@@ -291,9 +295,12 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   m->kchunk = desc->nz >= 64 ? 32 : desc->nz;
   m->vacuum_ratio = 0.99;
   m->occupancy = 2;
+  m->segments = 0;
   for (int c = 0; c < FV_KERNEL_NCLASS; ++c) m->launches[c] = 0;
   m->faces_defined = 0;
   cudaError_t e = cudaGetDevice(&m->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device);
   if (e != cudaSuccess) {
     delete m;
     return cuda_fail(e, "cudaGetDevice");
@@ -557,6 +564,14 @@ fv_status fv_set_tuning(fv_mesh_t m, int key, double value) {
       return FV_ERR_INVALID_ARG;
     }
     m->occupancy = (int)value;
+    return FV_OK;
+  }
+  if (key == FV_TUNE_SWEEP_SEGMENTS) {
+    if (!(value >= 0.0 && value <= 4096.0) || value != (double)(int)value) {
+      set_error("FV_TUNE_SWEEP_SEGMENTS must be an integer in [0, 4096] (got %g)", value);
+      return FV_ERR_INVALID_ARG;
+    }
+    m->segments = (int)value;
     return FV_OK;
   }
   set_error("unknown tuning key %d", key);

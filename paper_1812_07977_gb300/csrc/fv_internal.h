@@ -38,12 +38,14 @@ struct StepBuffers {
 // and with (fma) fused multiply-add contraction.  A substep is launch_prim
 // on its input state (U for stage 1, U1 for stage 2), then launch_sweep for
 // axis 0, 1, 2; the z sweep (axis 2) applies the RK combine of `stage`.
+// `segments`: pieces each grid line of a sweep is cut into (0: chosen from
+// the mesh size and `num_sms`, the device's multiprocessor count).
 #define FV_DECLARE_STEP_VARIANT(ns)                                                        \
   namespace ns {                                                                           \
   cudaError_t launch_prim(const double* src, const StepBuffers& b, const fvd::Params& P,   \
                           cudaStream_t s);                                                 \
   cudaError_t launch_sweep(int axis, int stage, const StepBuffers& b, const fvd::Params& P, \
-                           double dt, cudaStream_t s);                                     \
+                           double dt, int segments, int num_sms, cudaStream_t s);          \
   cudaError_t launch_reduce_dt(const double* U, const fvd::Params& P, DevCounters* ctr,     \
                                cudaStream_t s);                                            \
   }

@@ -113,21 +113,30 @@ __device__ __forceinline__ void rk_combine(double* __restrict__ U, double* __res
 }
 
 // AXIS: 0, 1, 2.  STAGE: 0 for the x and y sweeps; 1 or 2 (the RK stage)
-// for the z sweep, which finishes the update.
+// for the z sweep, which finishes the update.  Each grid line is cut into
+// gridDim.y segments of `seg` cells (blockIdx.y picks one): a segment starts
+// its window two cells before its first cell and evaluates the face on its
+// left, which the segment before also evaluates (the same bits), so every
+// cell gets exactly the update of an unsegmented sweep.  More, shorter work
+// items keep more warps resident and let the block scheduler even out lines
+// of unequal cost.
 template <int AXIS, int STAGE, int TK>
 __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks)
 k_sweep(const double* __restrict__ W, double* __restrict__ ACC, double* __restrict__ U,
-        double* __restrict__ U1, Params P, double dt, DevCounters* ctr) {
-  const int n = AXIS == 0 ? P.nx : AXIS == 1 ? P.ny : P.nz;
+        double* __restrict__ U1, Params P, double dt, int seg, DevCounters* ctr) {
+  const int n_line = AXIS == 0 ? P.nx : AXIS == 1 ? P.ny : P.nz;
   const int na = AXIS == 0 ? P.ny : P.nx;
   const int nb = AXIS == 2 ? P.ny : P.nz;
   const long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (line >= (long long)na * nb) return;
+  const int c0 = (int)blockIdx.y * seg;  // first cell (and face) of the segment
+  if (c0 >= n_line) return;
+  const int n = n_line - c0 < seg ? n_line - c0 : seg;  // cells of the segment
   const int a = (int)(line % na);
   const int b = (int)(line / na);
-  const int i0 = AXIS == 0 ? 0 : a;
-  const int j0 = AXIS == 0 ? a : (AXIS == 1 ? 0 : b);
-  const int k0 = AXIS == 2 ? 0 : b;
+  const int i0 = AXIS == 0 ? c0 : a;
+  const int j0 = AXIS == 0 ? a : (AXIS == 1 ? c0 : b);
+  const int k0 = AXIS == 2 ? c0 : b;
   const long long nf = P.nfield;
   const long long gs = AXIS == 0 ? 1 : (AXIS == 1 ? P.sy : P.sz);
   const long long g0 = (k0 + 2) * P.sz + (j0 + 2) * P.sy + (i0 + 2);
@@ -148,7 +157,8 @@ k_sweep(const double* __restrict__ W, double* __restrict__ ACC, double* __restri
 #pragma unroll
   for (int q = 0; q < NF; ++q) Fprev[q] = 0.0;
   // length of the run of cells equal bit for bit to the newest cell of the
-  // window (counted from cell -2), and whether the last face fell back
+  // window (counted from cell -2 of the segment, so the segment's first face
+  // is always evaluated), and whether the last face fell back
   int run = same(wm1, wm2) ? 2 : 1;
   run = same(wc, wm1) ? run + 1 : 1;
   bool fell_back = false;
@@ -181,7 +191,9 @@ k_sweep(const double* __restrict__ W, double* __restrict__ ACC, double* __restri
       if (fell_back) {
         wl = wprev;
         wr = wc;
-        atomicAdd(&ctr->fallback, 1ULL);
+        // the first face of a later segment is the last face of the one
+        // before, which counted it
+        if (f > 0 || c0 == 0) atomicAdd(&ctr->fallback, 1ULL);
       }
       hll_flux<AXIS>(wl, wr, P, F);
       ++evaluated;
@@ -339,27 +351,46 @@ cudaError_t launch_prim(const double* src, const StepBuffers& b, const Params& P
   return cudaGetLastError();
 }
 
+// Default segments per line: enough work items for about kSweepWaves waves
+// of resident warps, each segment at least kMinSegment cells long (its
+// first face is evaluated twice, which costs most where the flux would
+// otherwise be reused).
+constexpr int kSweepWaves = 8;
+constexpr int kMinSegment = 16;
+
 template <int TK>
 static cudaError_t sweep_tk(int axis, int stage, const StepBuffers& b, const Params& P,
-                            double dt, cudaStream_t s) {
+                            double dt, int segments, int num_sms, cudaStream_t s) {
   const long long lines = axis == 0 ? (long long)P.ny * P.nz
                         : axis == 1 ? (long long)P.nx * P.nz : (long long)P.nx * P.ny;
-  const unsigned g = (unsigned)((lines + kSweepThreads - 1) / kSweepThreads);
+  const int n = axis == 0 ? P.nx : axis == 1 ? P.ny : P.nz;
+  if (segments < 1) {
+    const long long warps = (lines + kSweepThreads - 1) / kSweepThreads * (kSweepThreads / 32);
+    const long long target =
+        (long long)kSweepWaves * kSweepMinBlocks * (kSweepThreads / 32) * (num_sms > 0 ? num_sms : 1);
+    const long long want = (target + warps - 1) / warps;
+    const int most = n / kMinSegment > 1 ? n / kMinSegment : 1;
+    segments = want < most ? (int)want : most;
+  }
+  if (segments > n) segments = n;
+  const int seg = (n + segments - 1) / segments;
+  const dim3 g((unsigned)((lines + kSweepThreads - 1) / kSweepThreads),
+               (unsigned)((n + seg - 1) / seg));
   if (axis == 0)
-    k_sweep<0, 0, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, b.ctr);
+    k_sweep<0, 0, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, seg, b.ctr);
   else if (axis == 1)
-    k_sweep<1, 0, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, b.ctr);
+    k_sweep<1, 0, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, seg, b.ctr);
   else if (stage == 1)
-    k_sweep<2, 1, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, b.ctr);
+    k_sweep<2, 1, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, seg, b.ctr);
   else
-    k_sweep<2, 2, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, b.ctr);
+    k_sweep<2, 2, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, seg, b.ctr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(int axis, int stage, const StepBuffers& b, const Params& P, double dt,
-                         cudaStream_t s) {
-  if (P.theta == 2.0) return sweep_tk<THETA_TWO>(axis, stage, b, P, dt, s);
-  return sweep_tk<THETA_GENERAL>(axis, stage, b, P, dt, s);
+                         int segments, int num_sms, cudaStream_t s) {
+  if (P.theta == 2.0) return sweep_tk<THETA_TWO>(axis, stage, b, P, dt, segments, num_sms, s);
+  return sweep_tk<THETA_GENERAL>(axis, stage, b, P, dt, segments, num_sms, s);
 }
 
 }  // namespace FV_NS

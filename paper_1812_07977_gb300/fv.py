@@ -265,7 +265,7 @@ class Mesh:
         return a.value, b.value
 
     def set_tuning(self, key: str, value):
-        keys = {"kchunk": 0, "vacuum_ratio": 1, "occupancy": 2}
+        keys = {"kchunk": 0, "vacuum_ratio": 1, "occupancy": 2, "sweep_segments": 3}
         _check(self._lib.fv_set_tuning(self._h, keys[key], float(value)), "fv_set_tuning")
 
     def profile(self, on: bool = True):

@@ -290,12 +290,14 @@ def test_face_counts():
     lines = 2 * (ny * nz + nx * nz + nx * ny)
     for prec in ("fp64", "fp64_fma", "fp32_bulk"):
         with Mesh(*n, bc=("periodic",) * 3, precision=prec) as m:
+            m.set_tuning("sweep_segments", 1)
             m.set_state(problems.random_smooth_periodic(*n, seed=9))
             m.step(m.reduce_dt(0.4))
             ev, de = m.face_counts()
             assert de == defined
             assert (ev == de) if prec != "fp32_bulk" else (ev >= de)
         with Mesh(*n, precision=prec) as m:
+            m.set_tuning("sweep_segments", 1)
             m.set_state(problems.uniform(*n, 1.0, (0.3, 0.2, 0.1), 1.0))
             m.step(m.reduce_dt(0.4))
             ev, de = m.face_counts()
@@ -303,6 +305,60 @@ def test_face_counts():
             assert (ev == lines) if prec != "fp32_bulk" else (ev < de // 4)
             m.set_state(problems.uniform(*n, 1.0, (0.3, 0.2, 0.1), 1.0))
             assert m.face_counts() == (0, 0)
+
+
+def _segments_of(n, segments):
+    seg = -(-n // min(segments, n))
+    return -(-n // seg)
+
+
+@pytest.mark.parametrize("segments", [2, 3, 7, 64])
+def test_sweep_segments_bitwise_and_counted(segments):
+    """Grid lines cut into segments give the unsegmented sweeps' bits
+    (exact build against the oracle, FMA build against itself unsegmented);
+    each extra segment evaluates one face twice, which the face count shows,
+    and a fallback face on a segment boundary is counted once."""
+    from paper_1812_07977_gb300.fv import Mesh
+    n = (33, 17, 29)
+    U0 = problems.riemann_oblique(*n)
+    om, Uo, m = _pair(*n, U0)
+    m.set_tuning("sweep_segments", segments)
+    _run_both(om, Uo, m, 4)
+    got = m.get_state().cpu().numpy()
+    assert np.array_equal(got.view(np.uint64), oracle.interior(Uo).view(np.uint64))
+    m.close()
+    states = []
+    for sg in (1, segments):
+        with Mesh(*n, precision="fp64_fma") as mf:
+            mf.set_tuning("sweep_segments", sg)
+            mf.set_state(torch.from_numpy(U0).cuda())
+            for _ in range(4):
+                mf.step(mf.reduce_dt(0.4))
+            states.append(mf.get_state().cpu().numpy())
+    assert np.array_equal(states[0].view(np.uint64), states[1].view(np.uint64))
+    # a state without equal neighbours: every face evaluated, boundaries twice
+    nx, ny, nz = n
+    with Mesh(*n, bc=("periodic",) * 3, precision="fp64_fma") as mp:
+        mp.set_tuning("sweep_segments", segments)
+        mp.set_state(problems.random_smooth_periodic(*n, seed=9))
+        mp.step(mp.reduce_dt(0.4))
+        ev, de = mp.face_counts()
+    extra = 2 * sum((_segments_of(a, segments) - 1) * lines for a, lines in
+                    ((nx, ny * nz), (ny, nx * nz), (nz, nx * ny)))
+    assert ev == de + extra, (ev, de, extra)
+    # near-vacuum tube: the one fallback face (between cells 3 and 4) is a
+    # segment boundary for 2 segments of 4 cells
+    tx = 8
+    p = np.array([6.0, 6.0, 6.0, 1.0, 1e-20, 1e-20, 1e-20, 1e-20])
+    z = np.zeros(tx)
+    Ut = problems.conserved_from_primitive(np.ones(tx), z, z, z, p).reshape(5, 1, 1, tx)
+    om, Uo, m = _pair(tx, 1, 1, np.ascontiguousarray(Ut))
+    m.set_tuning("sweep_segments", 2 if segments == 64 else segments)
+    dU, bad, fb = oracle.compute_update(om, Uo, 1e-3)
+    m.substep(1, 1e-3)
+    assert np.array_equal(m.get_state().cpu().numpy(), oracle.interior(Uo) + oracle.interior(dU))
+    assert m.counters() == (0, fb) and fb == 1
+    m.close()
 
 
 def test_host_buffers_match_device_buffers():
