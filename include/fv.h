@@ -132,8 +132,15 @@ FV_API fv_status fv_get_ghosted_state(fv_mesh_t m, double* U, int on_device);
  * mesh's arithmetic (FP64: IEEE operations in the method's order, bit for
  * bit; FP64_FMA: contracted, Newton-Raphson divide and square root, within
  * a few ulps; FP32_BULK: per-cell speeds in FP32).  The maximum is exact
- * (order-free).  Only valid at a step boundary.
- * Synchronising (one 24-byte device-to-host read).  Errors: INVALID_ARG
+ * (order-free).  Only valid at a step boundary.  On the FP64 paths the same
+ * pass also converts the state to primitives, which the next fv_step /
+ * fv_substep(1) uses instead of converting again if the state has not
+ * changed since (fv_set_state and fv_fill_ghosts count as changes); a
+ * non-physical cell found there counts once, for the time step.
+ * On the FP32_BULK path the second substep of fv_step takes the maximum of
+ * the state it writes (and counts its non-physical cells), and
+ * fv_reduce_dt uses that maximum while the state has not changed since.
+ * Synchronising (one small device-to-host read).  Errors: INVALID_ARG
  * (cfl <= 0, dt_out NULL, stage pending), NONPHYSICAL. */
 FV_API fv_status fv_reduce_dt(fv_mesh_t m, double cfl, double* dt_out);
 

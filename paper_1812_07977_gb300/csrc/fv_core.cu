@@ -61,6 +61,8 @@ struct fv_mesh_s {
   double vacuum_ratio;      // FP32-bulk FP64 pressure-recovery threshold
   int occupancy;            // CTAs per SM the fused kernel is compiled for (2 or 3)
   int segments;             // pieces per grid line of the FP64 sweeps (0: automatic)
+  bool w_current;           // FP64: W holds the primitives of U (from the dt pass)
+  bool smax_current;        // FP32-bulk: ctr->smax_next is the CFL maximum of U
   // profiling
   bool prof_on;
   std::vector<cudaEvent_t> event_pool;
@@ -245,20 +247,34 @@ long long faces_normal_to(const fvd::Params& P, int axis) {
 cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
   for (int axis = 0; axis < 3; ++axis) m->faces_defined += faces_normal_to(m->P, axis);
   if (m->desc.precision == FV_PREC_FP32_BULK) {
-    cudaError_t e = timed(m, FV_KERNEL_FUSED, 1, [&] {
-      return fv_fp32::launch_stage(stage, m->buf, m->P, dt, m->kchunk, m->vacuum_ratio,
-                                   m->occupancy, m->stream);
-    });
+    // stage 2 also takes the CFL maximum of its output (the next dt's)
+    m->smax_current = false;
+    cudaError_t e = cudaSuccess;
+    if (stage == 2)
+      e = cudaMemsetAsync(&m->buf.ctr->smax_next, 0, sizeof(unsigned long long), m->stream);
+    if (e == cudaSuccess)
+      e = timed(m, FV_KERNEL_FUSED, 1, [&] {
+        return fv_fp32::launch_stage(stage, m->buf, m->P, dt, m->kchunk, m->vacuum_ratio,
+                                     m->occupancy, m->stream);
+      });
     if (e != cudaSuccess) return e;
     double* dst = stage == 1 ? m->buf.U1 : m->buf.U;
-    return timed(m, FV_KERNEL_GHOST, 1, [&] { return launch_fill_ghosts(dst, m->P, m->stream); });
+    e = timed(m, FV_KERNEL_GHOST, 1, [&] { return launch_fill_ghosts(dst, m->P, m->stream); });
+    m->smax_current = e == cudaSuccess && stage == 2;
+    return e;
   }
   const bool fma = m->desc.precision == FV_PREC_FP64_FMA;
   const double* src = stage == 1 ? m->buf.U : m->buf.U1;
-  cudaError_t e = timed(m, FV_KERNEL_PRIM, 1, [&] {
-    return fma ? fv_fp64_fma::launch_prim(src, m->buf, m->P, m->stream)
-               : fv_fp64_exact::launch_prim(src, m->buf, m->P, m->stream);
-  });
+  cudaError_t e = cudaSuccess;
+  // the dt pass since the state last changed left U's primitives in W
+  if (!(stage == 1 && m->w_current)) {
+    e = timed(m, FV_KERNEL_PRIM, 1, [&] {
+      return fma ? fv_fp64_fma::launch_prim(src, m->buf, m->P, m->stream)
+                 : fv_fp64_exact::launch_prim(src, m->buf, m->P, m->stream);
+    });
+  }
+  m->w_current = false;
+  m->smax_current = false;
   for (int axis = 0; axis < 3 && e == cudaSuccess; ++axis) {
     e = timed(m, FV_KERNEL_SWEEP_X + axis, 1, [&] {
       return fma ? fv_fp64_fma::launch_sweep(axis, stage, m->buf, m->P, dt, m->segments,
@@ -296,6 +312,8 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   m->vacuum_ratio = 0.99;
   m->occupancy = 2;
   m->segments = 0;
+  m->w_current = false;
+  m->smax_current = false;
   for (int c = 0; c < FV_KERNEL_NCLASS; ++c) m->launches[c] = 0;
   m->faces_defined = 0;
   cudaError_t e = cudaGetDevice(&m->device);
@@ -380,6 +398,8 @@ fv_status fv_set_state(fv_mesh_t m, const double* U, int on_device) {
     return cuda_fail(e, "clearing counters");
   m->faces_defined = 0;
   m->stage_pending = 0;
+  m->w_current = false;
+  m->smax_current = false;
   if (!on_device && (e = cudaStreamSynchronize(m->stream)) != cudaSuccess)
     return cuda_fail(e, "fv_set_state");
   return FV_OK;
@@ -434,18 +454,23 @@ fv_status fv_reduce_dt(fv_mesh_t m, double cfl, double* dt_out) {
     return FV_ERR_INVALID_ARG;
   }
   DeviceGuard g(m->device);
-  cudaError_t e = timed(m, FV_KERNEL_DT, 1, [&] {
-    return m->desc.precision == FV_PREC_FP32_BULK
-               ? fv_fp32::launch_reduce_dt(m->buf.U, m->P, m->vacuum_ratio, m->buf.ctr,
-                                           m->stream)
-               : m->desc.precision == FV_PREC_FP64_FMA
-                     ? fv_fp64_fma::launch_reduce_dt(m->buf.U, m->P, m->buf.ctr, m->stream)
-                     : fv_fp64_exact::launch_reduce_dt(m->buf.U, m->P, m->buf.ctr, m->stream);
-  });
-  if (e != cudaSuccess) return cuda_fail(e, "time-step kernel");
+  const bool fp32 = m->desc.precision == FV_PREC_FP32_BULK;
+  // FP32-bulk: the last stage 2 took the maximum of the current state
+  const bool cached = fp32 && m->smax_current;
+  if (!cached) {
+    cudaError_t e = timed(m, FV_KERNEL_DT, 1, [&] {
+      return fp32 ? fv_fp32::launch_reduce_dt(m->buf.U, m->P, m->vacuum_ratio, m->buf.ctr,
+                                              m->stream)
+             : m->desc.precision == FV_PREC_FP64_FMA
+                 ? fv_fp64_fma::launch_prim_dt(m->buf.U, m->buf, m->P, m->stream)
+                 : fv_fp64_exact::launch_prim_dt(m->buf.U, m->buf, m->P, m->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "time-step kernel");
+    m->w_current = !fp32;
+  }
   if ((st = read_counters(m)) != FV_OK) return st;
   double smax;
-  std::memcpy(&smax, &m->host_ctr->smax_bits, sizeof smax);
+  std::memcpy(&smax, cached ? &m->host_ctr->smax_next : &m->host_ctr->smax_bits, sizeof smax);
   *dt_out = cfl / smax;
   return nonphysical_status(m);
 }
@@ -489,6 +514,8 @@ fv_status fv_fill_ghosts(fv_mesh_t m) {
   if (st != FV_OK) return st;
   DeviceGuard g(m->device);
   double* cur = m->stage_pending ? m->buf.U1 : m->buf.U;
+  m->w_current = false;
+  m->smax_current = false;
   cudaError_t e = timed(m, FV_KERNEL_GHOST, 1, [&] { return launch_fill_ghosts(cur, m->P, m->stream); });
   if (e != cudaSuccess) return cuda_fail(e, "ghost-fill kernel");
   return FV_OK;
@@ -616,12 +643,19 @@ fv_status fv_internal_mesh(fv_mesh_t m, MeshView* out) {
     set_error("the mesh is between the two RK substeps");
     return FV_ERR_INVALID_ARG;
   }
+  m->w_current = false;  // the caller may write U
+  m->smax_current = false;
   out->P = m->P;
   out->U = m->buf.U;
   out->stream = m->stream;
   out->device = m->device;
   out->precision = m->desc.precision;
   return FV_OK;
+}
+
+void fv_internal_state_written(fv_mesh_t m) {
+  m->w_current = false;
+  m->smax_current = false;
 }
 
 fv_status fv_internal_step(fv_mesh_t m, double dt) { return fv_step(m, dt); }

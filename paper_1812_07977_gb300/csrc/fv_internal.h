@@ -16,6 +16,7 @@ struct DevCounters {
   unsigned long long fallback;     // faces that fell back to first order
   unsigned long long np_dt;        // non-physical interior cells seen by the dt pass
   unsigned long long faces;        // face fluxes evaluated (not reused) by the flux kernels
+  unsigned long long smax_next;    // FP32-bulk: CFL maximum of the last stage 2's output
 };
 
 // Adds each lane's count to *ctr once per warp (the lanes present at the call).
@@ -40,14 +41,17 @@ struct StepBuffers {
 // axis 0, 1, 2; the z sweep (axis 2) applies the RK combine of `stage`.
 // `segments`: pieces each grid line of a sweep is cut into (0: chosen from
 // the mesh size and `num_sms`, the device's multiprocessor count).
+// launch_prim_dt: the CFL maximum of U into ctr->smax_bits and, in the same
+// pass, U's primitives into b.W, which a following substep 1 may use in
+// place of its launch_prim.
 #define FV_DECLARE_STEP_VARIANT(ns)                                                        \
   namespace ns {                                                                           \
   cudaError_t launch_prim(const double* src, const StepBuffers& b, const fvd::Params& P,   \
                           cudaStream_t s);                                                 \
   cudaError_t launch_sweep(int axis, int stage, const StepBuffers& b, const fvd::Params& P, \
                            double dt, int segments, int num_sms, cudaStream_t s);          \
-  cudaError_t launch_reduce_dt(const double* U, const fvd::Params& P, DevCounters* ctr,     \
-                               cudaStream_t s);                                            \
+  cudaError_t launch_prim_dt(const double* U, const StepBuffers& b, const fvd::Params& P,  \
+                             cudaStream_t s);                                              \
   }
 FV_DECLARE_STEP_VARIANT(fv_fp64_exact)
 FV_DECLARE_STEP_VARIANT(fv_fp64_fma)
@@ -129,5 +133,8 @@ struct MeshView {
   int precision;
 };
 fv_status fv_internal_mesh(fv_mesh_t m, MeshView* out);
+// The caller wrote the mesh's U through a view: drops what the mesh derived
+// from the state (its primitives and CFL maximum for the next step).
+void fv_internal_state_written(fv_mesh_t m);
 // Run one full step of the mesh (as fv_step) / refill its ghosts.
 fv_status fv_internal_step(fv_mesh_t m, double dt);

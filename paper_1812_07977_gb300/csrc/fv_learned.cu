@@ -941,6 +941,7 @@ fv_status fv_step_learned(fv_mesh_t m, fv_net_t n, double dt) {
   if ((st = forward(n, v, g)) != FV_OK) return st;      // phi from U^n
   if ((st = fv_internal_step(m, dt)) != FV_OK) return st; // RK2 step
   k_apply_correction<<<grid_for(5 * g.n), 256, 0, v.stream>>>(v.U, v.P, n->o, n->scales, (float)dt);
+  fv_internal_state_written(m);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_fill_ghosts(v.U, v.P, v.stream);
   if (e != cudaSuccess) return cuda_fail(e, "applying the learned correction");

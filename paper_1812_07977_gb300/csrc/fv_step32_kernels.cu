@@ -41,6 +41,12 @@ constexpr int kHalo = PX * PY - TX * TY;    // 176 halo cells per plane
 constexpr int kXFaces = (TX + 1) * TY;      // 264
 constexpr int kYFaces = TX * (TY + 1);      // 288
 
+// First y face of thread tid.  The x faces beyond the first kThreads go to
+// warp 0; the y faces are assigned one warp later, so that their leftover
+// row goes to warp 1 and no warp evaluates more than two x / y faces plus
+// the z face per plane (the others wait for it at the plane's barrier).
+__device__ __forceinline__ int yface0(int tid) { return (tid + kThreads - 32) % kThreads; }
+
 struct Smem {
   float w[NF][PY][PX];
   float fx[NF][TY][TX + 1];
@@ -85,6 +91,34 @@ __device__ __forceinline__ void smem_store_flag(Smem& s, int row, int col, const
   s.w[4][row][col] = w.p;
 }
 
+// CFL signal speed of a cell's state in FP32 (bits of a non-negative float;
+// 0 for a non-physical cell, which is counted).  Explicit roundings (no
+// contraction): every kernel that computes the speed gets the same bits, so
+// the time-step pass, the fused stage 2 and batched runs agree on dt.
+__device__ __forceinline__ unsigned speed_bits(const double u[NF], const Params32& Q,
+                                               unsigned long long& bad) {
+  const Prim32 w = prim_from_state(u, Q);
+  if (!physical(w)) {
+    ++bad;
+    return 0u;
+  }
+  const float c2 = __fmul_rn(__fmul_rn(Q.gamma, w.p), rcp(w.r));
+  const float c = __fmul_rn(c2, rsqrtf(c2));
+  const float sp = __fadd_rn(__fadd_rn(__fmul_rn(__fadd_rn(fabsf(w.vx), c), Q.inv_d[0]),
+                                       __fmul_rn(__fadd_rn(fabsf(w.vy), c), Q.inv_d[1])),
+                             __fmul_rn(__fadd_rn(fabsf(w.vz), c), Q.inv_d[2]));
+  const unsigned b = __float_as_uint(sp);
+  return (sp > 0.0f && b < 0x7F800000u) ? b : 0u;
+}
+
+// Folds a thread's speed maximum (bits of a non-negative float) into a
+// grid-wide maximum held as the bits of the equal double.
+__device__ __forceinline__ void max_speed_to(unsigned long long* dst, unsigned smax) {
+  smax = __reduce_max_sync(0xffffffffu, smax);
+  if ((threadIdx.x & 31u) == 0u && smax)
+    atomicMax(dst, (unsigned long long)__double_as_longlong(f2d(__uint_as_float(smax))));
+}
+
 // Face flux between cells a1 and a2 given the four cells a0..a3 along the
 // face normal; falls back to first order if a face state is non-physical.
 template <int AXIS, bool MC>
@@ -106,13 +140,17 @@ __device__ __forceinline__ void face_flux(const Prim32& a0, const Prim32& a1, co
 // STAGE 1: U1 = U + dU.  STAGE 2: U = ((U + U1) + dU) / 2.  The input of the
 // substep (U for stage 1, U1 for stage 2) has its ghosts filled.  Counts of
 // face fallbacks and non-physical cells accumulate in the caller's counters.
-// MC: the limiter parameter is 2.
-template <int STAGE, bool MC>
+// MC: the limiter parameter is 2.  NEXT (stage 2): also the CFL speed of
+// each output cell (the next time step's), its maximum into smax_next and
+// its non-physical cells into bad_next.
+template <int STAGE, bool MC, bool NEXT>
 __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
                                              double* __restrict__ U1, const fvd::Params& P,
                                              const Params32& Q, float dt, int i0, int j0,
                                              int k0, int k1, unsigned& fallbacks_out,
-                                             unsigned long long& bad_out, unsigned& evaluated) {
+                                             unsigned long long& bad_out, unsigned& evaluated,
+                                             unsigned& smax_next,
+                                             unsigned long long& bad_next) {
   const double* __restrict__ src = STAGE == 1 ? U : U1;
   const int tid = threadIdx.x;
   const int ti = tid % TX, tj = tid / TX;
@@ -178,7 +216,7 @@ __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
     const int r = f / (TX + 1), fi = f % (TX + 1);
     if (i0 + fi <= P.nx && (fi < TX || i0 + fi == P.nx) && j0 + r < P.ny) counted |= 1u << pass;
   }
-  for (int f = tid, pass = 2; f < kYFaces; f += kThreads, ++pass) {
+  for (int f = yface0(tid), pass = 2; f < kYFaces; f += kThreads, ++pass) {
     const int fj = f / TX, c = f % TX;
     if (i0 + c < P.nx && j0 + fj <= P.ny && (fj < TY || j0 + fj == P.ny)) counted |= 1u << pass;
   }
@@ -272,7 +310,7 @@ __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
       fallbacks += fb & (counted >> pass);
     }
     // (d) y faces: face fj (between rows fj-1 and fj) of column c
-    for (int f = tid, pass = 2; f < kYFaces; f += kThreads, ++pass) {
+    for (int f = yface0(tid), pass = 2; f < kYFaces; f += kThreads, ++pass) {
       const int fj = f / TX, c = f % TX;
       const bool keep = s.same[fj][c + 2] & s.same[fj + 1][c + 2] & s.same[fj + 2][c + 2] &
                         s.same[fj + 3][c + 2];
@@ -294,6 +332,7 @@ __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
     __syncthreads();
     // (e) update of cell (i, j, k): FP32 divergence, FP64 RK combine
     if (owner) {
+      double un[NF];
 #pragma unroll
       for (int q = 0; q < NF; ++q) {
         const float acc = fmaf(fz_lo[q] - fz_hi[q], idz,
@@ -303,9 +342,11 @@ __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
         if (STAGE == 1) {
           U1[q * nf + g] = rk0[q] + du;
         } else {
-          U[q * nf + g] = dhalf((rk0[q] + rk1[q]) + du);
+          un[q] = dhalf((rk0[q] + rk1[q]) + du);
+          U[q * nf + g] = un[q];
         }
       }
+      if (NEXT && STAGE == 2) smax_next = max(smax_next, speed_bits(un, Q, bad_next));
     }
 #pragma unroll
     for (int q = 0; q < NF; ++q) fz_lo[q] = fz_hi[q];
@@ -323,14 +364,19 @@ __global__ void __launch_bounds__(kThreads, MINB)
 k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params32 Q, float dt,
           int kchunk, DevCounters* ctr) {
   __shared__ Smem s;
-  unsigned fallbacks = 0, evaluated = 0;
-  unsigned long long bad = 0;
+  unsigned fallbacks = 0, evaluated = 0, smax_next = 0;
+  unsigned long long bad = 0, bad_next = 0;
   const int k0 = blockIdx.z * kchunk;
-  stage32_tile<STAGE, MC>(s, U, U1, P, Q, dt, blockIdx.x * TX, blockIdx.y * TY, k0,
-                          min(k0 + kchunk, P.nz), fallbacks, bad, evaluated);
+  stage32_tile<STAGE, MC, STAGE == 2>(s, U, U1, P, Q, dt, blockIdx.x * TX, blockIdx.y * TY, k0,
+                                      min(k0 + kchunk, P.nz), fallbacks, bad, evaluated,
+                                      smax_next, bad_next);
   if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
   if (bad) atomicAdd(&ctr->np_step, bad);
   warp_count(&ctr->faces, evaluated);
+  if (STAGE == 2) {
+    max_speed_to(&ctr->smax_next, smax_next);
+    if (bad_next) atomicAdd(&ctr->np_dt, bad_next);
+  }
 }
 
 // ---------------------------------------------------------------- batches
@@ -343,8 +389,8 @@ k_stage32_batch(double* __restrict__ U, double* __restrict__ U1,
                 int kchunk, unsigned* __restrict__ next_item, DevCounters* ctr) {
   __shared__ Smem s;
   __shared__ int s_item;
-  unsigned fallbacks = 0, evaluated = 0;
-  unsigned long long bad = 0;
+  unsigned fallbacks = 0, evaluated = 0, unused_smax = 0;
+  unsigned long long bad = 0, unused_bad = 0;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_item = (int)atomicAdd(next_item, 1u);
@@ -354,8 +400,9 @@ k_stage32_batch(double* __restrict__ U, double* __restrict__ U1,
     const int4 w = items[it];       // mesh, tile x, tile y, chunk
     const BatchMesh& m = meshes[w.x];
     const int k0 = w.w * kchunk;
-    stage32_tile<STAGE, MC>(s, U + m.offset, U1 + m.offset, m.P, m.Q, (float)m.dt, w.y * TX,
-                            w.z * TY, k0, min(k0 + kchunk, m.P.nz), fallbacks, bad, evaluated);
+    stage32_tile<STAGE, MC, false>(s, U + m.offset, U1 + m.offset, m.P, m.Q, (float)m.dt,
+                                   w.y * TX, w.z * TY, k0, min(k0 + kchunk, m.P.nz), fallbacks,
+                                   bad, evaluated, unused_smax, unused_bad);
   }
   if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
   if (bad) atomicAdd(&ctr->np_step, bad);
@@ -372,20 +419,7 @@ __device__ __forceinline__ unsigned cell_speed_bits(const double* __restrict__ U
   const long long j = r / P.nx, i = r - j * P.nx;
   double u[NF];
   load_state(U, P.nfield, (k + 2) * P.sz + (j + 2) * P.sy + (i + 2), u);
-  const Prim32 w = prim_from_state(u, Q);
-  if (!physical(w)) {
-    ++bad;
-    return 0u;
-  }
-  // explicit roundings (no contraction): every kernel that computes the
-  // speed gets the same bits, so single-mesh and batched runs share a dt
-  const float c2 = __fmul_rn(__fmul_rn(Q.gamma, w.p), rcp(w.r));
-  const float c = __fmul_rn(c2, rsqrtf(c2));
-  const float sp = __fadd_rn(__fadd_rn(__fmul_rn(__fadd_rn(fabsf(w.vx), c), Q.inv_d[0]),
-                                       __fmul_rn(__fadd_rn(fabsf(w.vy), c), Q.inv_d[1])),
-                             __fmul_rn(__fadd_rn(fabsf(w.vz), c), Q.inv_d[2]));
-  const unsigned b = __float_as_uint(sp);
-  return (sp > 0.0f && b < 0x7F800000u) ? b : 0u;
+  return speed_bits(u, Q, bad);
 }
 
 // CFL signal speed per interior cell in FP32 from the FP64 state; the

@@ -4,7 +4,8 @@
 // rounded on its own, in the order of the method's definition) and
 // FV_NS=fv_fp64_fma with --fmad=true and the Newton-Raphson divide and
 // square root.  The CFL time step (ComputeTimeStep) is here too, so each
-// variant computes its own dt with its own arithmetic.
+// variant computes its own dt with its own arithmetic; its pass over the
+// state also gives the first substep its primitives.
 //
 // Structure of one substep of Algorithm 1 (its kernel sequence):
 //   k_prim            conserved -> primitive for every ghosted cell
@@ -265,50 +266,82 @@ k_sweep(const double* __restrict__ W, double* __restrict__ ACC, double* __restri
 constexpr int kDtThreads = 256;
 
 // ---------------------------------------------------------------- time step
-// s = ((|vx|+c)/dx + (|vy|+c)/dy) + (|vz|+c)/dz per interior cell; the
-// maximum over cells is exact in any order.  Non-negative doubles order
-// like their bit patterns, so the grid-wide maximum is an integer atomicMax.
-// A NaN s never wins, as in a plain `if (s > smax)` loop.
-// A cell equal bit for bit to the thread's previous cell has the same speed
-// (already in smax) and the same validity; when the whole warp has such
-// cells (uniform regions), it skips the arithmetic.
+// CFL signal speed of one cell (ComputeTimeStep):
+// s = ((|vx|+c)/dx + (|vy|+c)/dy) + (|vz|+c)/dz.
+__device__ __forceinline__ double cell_speed(const Prim& w, const Params& P) {
+#ifdef FV_NEWTON_DIVSQRT
+  const double c = sound_speed_nr(P.gamma * w.p, w.r);
+#else
+  const double c = sqrt(P.gamma * w.p / w.r);
+#endif
+  return ((fabs(w.vx) + c) * P.inv_d[0] + (fabs(w.vy) + c) * P.inv_d[1]) +
+         (fabs(w.vz) + c) * P.inv_d[2];
+}
+
+// Primitives of every ghosted cell (what k_prim gives the first substep)
+// and, over the interior cells, the maximum CFL speed and the non-physical
+// count, in one pass over the state.  The maximum is exact in any order:
+// non-negative doubles order like their bit patterns, so the grid-wide
+// maximum is an integer atomicMax, and a NaN speed never wins, as in a plain
+// `if (s > smax)` loop.  A cell equal bit for bit to the thread's previous
+// cell has its primitives, speed and validity; when the whole warp has such
+// cells (uniform regions), it skips the arithmetic.  Non-physical interior
+// cells count once, for the time step (a substep that uses these
+// primitives does not count them again).
 __global__ void __launch_bounds__(kDtThreads)
-k_reduce_dt(const double* __restrict__ U, Params P, DevCounters* ctr) {
-  const long long n = (long long)P.nx * P.ny * P.nz;
-  double smax = 0.0;
+k_prim_dt(const double* __restrict__ U, double* __restrict__ W, Params P, DevCounters* ctr) {
+  const long long nf = P.nfield;
+  const int X = P.nx + 4, Y = P.ny + 4;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  // (i, j, k) of cell c in the ghosted array, advanced by the stride's own
+  // (si, sj, sk) with carries
+  int k = (int)(c / P.sz);
+  int j = (int)((c - (long long)k * P.sz) / X);
+  int i = (int)(c - (long long)k * P.sz - (long long)j * X);
+  const int sk = (int)(stride / P.sz);
+  const int sj = (int)((stride - (long long)sk * P.sz) / X);
+  const int si = (int)(stride - (long long)sk * P.sz - (long long)sj * X);
+  double smax = 0.0, s = 0.0;
   unsigned long long bad = 0;
   double up[NF] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  bool have = false, bad_prev = false;
-  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < n;
-       m += (long long)gridDim.x * blockDim.x) {
-    const long long k = m / ((long long)P.nx * P.ny);
-    const long long r = m - k * ((long long)P.nx * P.ny);
-    const long long j = r / P.nx, i = r - j * P.nx;
-    const long long g = (k + 2) * P.sz + (j + 2) * P.sy + (i + 2);
+  Prim w = Prim{0.0, 0.0, 0.0, 0.0, 0.0};
+  bool have = false, bad_cell = false;
+  for (; c < nf; c += stride) {
     double u[NF];
     bool eq = have;
 #pragma unroll
     for (int q = 0; q < NF; ++q) {
-      u[q] = U[q * P.nfield + g];
+      u[q] = U[q * nf + c];
       eq = eq && bits(u[q]) == bits(up[q]);
       up[q] = u[q];
     }
     have = true;
-    if (__all_sync(__activemask(), eq)) {
-      bad += bad_prev;
-      continue;
+    if (!__all_sync(__activemask(), eq)) {
+      w = cons_to_prim(u, P);
+      bad_cell = !(is_pos(w.r) && is_pos(w.p));
+      s = cell_speed(w, P);
     }
-    const Prim w = cons_to_prim(u, P);
-    bad_prev = !(is_pos(w.r) && is_pos(w.p));
-    bad += bad_prev;
-#ifdef FV_NEWTON_DIVSQRT
-    const double c = sound_speed_nr(P.gamma * w.p, w.r);
-#else
-    const double c = sqrt(P.gamma * w.p / w.r);
-#endif
-    const double s = ((fabs(w.vx) + c) * P.inv_d[0] + (fabs(w.vy) + c) * P.inv_d[1]) +
-                     (fabs(w.vz) + c) * P.inv_d[2];
-    if (s > smax) smax = s;
+    W[c] = w.r;
+    W[nf + c] = w.vx;
+    W[2 * nf + c] = w.vy;
+    W[3 * nf + c] = w.vz;
+    W[4 * nf + c] = w.p;
+    if (i >= 2 && i < P.nx + 2 && j >= 2 && j < P.ny + 2 && k >= 2 && k < P.nz + 2) {
+      bad += bad_cell;
+      if (s > smax) smax = s;
+    }
+    i += si;
+    j += sj;
+    k += sk;
+    if (i >= X) {
+      i -= X;
+      ++j;
+    }
+    if (j >= Y) {
+      j -= Y;
+      ++k;
+    }
   }
   unsigned long long sb = (unsigned long long)__double_as_longlong(smax);
 #pragma unroll
@@ -334,12 +367,13 @@ k_reduce_dt(const double* __restrict__ U, Params P, DevCounters* ctr) {
 
 }  // namespace
 
-cudaError_t launch_reduce_dt(const double* U, const Params& P, DevCounters* ctr, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(&ctr->smax_bits, 0, sizeof(unsigned long long), s);
+cudaError_t launch_prim_dt(const double* U, const StepBuffers& b, const Params& P,
+                           cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(&b.ctr->smax_bits, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  long long blocks = ((long long)P.nx * P.ny * P.nz + kDtThreads - 1) / kDtThreads;
+  long long blocks = (P.nfield + kDtThreads - 1) / kDtThreads;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  k_reduce_dt<<<(unsigned)blocks, kDtThreads, 0, s>>>(U, P, ctr);
+  k_prim_dt<<<(unsigned)blocks, kDtThreads, 0, s>>>(U, b.W, P, b.ctr);
   return cudaGetLastError();
 }
 

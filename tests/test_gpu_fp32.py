@@ -143,6 +143,36 @@ def test_flux_reuse_is_exact_and_counts_fallbacks():
     assert fa[0] < fbc[0]          # the plane-to-plane reuse did skip faces
 
 
+@pytest.mark.parametrize("theta", [2.0, 1.5])
+def test_stage2_cfl_maximum_same_dt(theta):
+    """The second substep takes the CFL maximum of the state it writes;
+    fv_reduce_dt then uses it instead of its own pass.  A run that does and
+    one whose dt pass runs every step (fv_fill_ghosts in between drops the
+    maximum) agree bit for bit on every dt and on the state; so does the
+    first dt of a fresh mesh on the same state."""
+    n = (37, 22, 19)
+    runs = []
+    for refresh in (False, True):
+        m = _mesh32(n, theta=theta)
+        m.set_state(problems.riemann_oblique(*n))
+        dts = []
+        for _ in range(6):
+            dts.append(m.reduce_dt(0.4))
+            if refresh:
+                m.fill_ghosts()
+            m.step(dts[-1])
+        dts.append(m.reduce_dt(0.4))
+        runs.append((dts, m.get_state().cpu().numpy(), m.counters()))
+        m.close()
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1].view(np.uint64), runs[1][1].view(np.uint64))
+    assert runs[0][2] == runs[1][2]
+    m = _mesh32(n, theta=theta)
+    m.set_state(runs[0][1])
+    assert m.reduce_dt(0.4) == runs[0][0][-1]
+    m.close()
+
+
 def test_conservation_periodic():
     n = (20, 16, 24)
     U0 = problems.random_smooth_periodic(*n, seed=99)

@@ -361,6 +361,30 @@ def test_sweep_segments_bitwise_and_counted(segments):
     m.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp64_fma"])
+def test_primitives_from_the_dt_pass_same_bits(precision):
+    """fv_reduce_dt's pass leaves the state's primitives for the next
+    substep 1; a run that uses them and one that converts again (fv_fill_ghosts
+    in between drops them) give the same dt and state bits, and the same
+    counts."""
+    from paper_1812_07977_gb300.fv import Mesh
+    n = (37, 22, 19)
+    runs = []
+    for refresh in (False, True):
+        with Mesh(*n, precision=precision) as m:
+            m.set_state(torch.from_numpy(problems.riemann_oblique(*n)).cuda())
+            dts = []
+            for _ in range(5):
+                dts.append(m.reduce_dt(0.4))
+                if refresh:
+                    m.fill_ghosts()
+                m.step(dts[-1])
+            runs.append((dts, m.get_state().cpu().numpy(), m.counters()))
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1].view(np.uint64), runs[1][1].view(np.uint64))
+    assert runs[0][2] == runs[1][2]
+
+
 def test_host_buffers_match_device_buffers():
     n = (16, 12, 10)
     U0 = problems.riemann_oblique(*n)
