@@ -240,7 +240,10 @@ FV_API fv_status fv_batch_set_state(fv_batch_t b, int mesh, const double* U, int
 FV_API fv_status fv_batch_get_state(fv_batch_t b, int mesh, double* U, int on_device);
 
 /* One step of every mesh with its own dt = cfl / (its maximum signal
- * speed).  use_graph != 0: the whole step (CFL reductions, both substeps and
+ * speed).  The second substep takes each mesh's maximum of the state it
+ * writes, so the next step starts from it; a separate pass over the states
+ * runs only when they changed otherwise (fv_batch_set_state, the
+ * autotuner).  use_graph != 0: the step (per-mesh dt, both substeps and
  * ghost fills) is captured once into a CUDA graph and replayed (re-captured
  * when cfl or the tuning changes).  Asynchronous. */
 FV_API fv_status fv_batch_step(fv_batch_t b, double cfl, int use_graph);

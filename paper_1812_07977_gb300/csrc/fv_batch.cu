@@ -53,6 +53,7 @@ struct fv_batch_s {
   DevCounters* host_ctr = nullptr;
   int kchunk = 32;
   int occupancy = 2;
+  bool smax_current = false;         // meshes[].smax_bits hold the current states' maxima
   // CUDA graph of one whole step
   cudaGraphExec_t graph = nullptr;
   double graph_cfl = -1.0;
@@ -131,13 +132,29 @@ fv_status build_items(fv_batch_t b, int kchunk) {
   return FV_OK;
 }
 
-cudaError_t launch_step(fv_batch_t b, double cfl) {
+// One step from dt on: what the step graph holds.  The CFL maxima of the
+// states it starts from are in meshes[].smax_bits (the previous step's stage
+// 2, or launch_batch_max).
+cudaError_t launch_step_body(fv_batch_t b, double cfl) {
   cudaError_t e = fv_fp32::launch_batch_dt(b->dev, cfl, b->stream);
   for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage) {
     e = fv_fp32::launch_batch_stage(stage, b->dev, b->kchunk, b->occupancy, b->num_sms,
                                     b->stream);
     if (e == cudaSuccess) e = fv_fp32::launch_batch_ghosts(stage, b->dev, b->stream);
   }
+  return e;
+}
+
+// The maxima pass when the states changed since the last step.
+cudaError_t launch_max_if_stale(fv_batch_t b) {
+  if (b->smax_current) return cudaSuccess;
+  return fv_fp32::launch_batch_max(b->dev, b->stream);
+}
+
+cudaError_t launch_step(fv_batch_t b, double cfl) {
+  cudaError_t e = launch_max_if_stale(b);
+  if (e == cudaSuccess) e = launch_step_body(b, cfl);
+  b->smax_current = e == cudaSuccess;
   return e;
 }
 
@@ -170,6 +187,7 @@ fv_status fv_batch_create(const fv_mesh_desc* descs, int nmesh, void* cuda_strea
   b->desc.assign(descs, descs + nmesh);
   cudaError_t e = cudaGetDevice(&b->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e == cudaSuccess) e = fv_fp32::prepare_kernels();
   if (e != cudaSuccess) {
     delete b;
     return cuda_fail(e, "querying the device");
@@ -279,6 +297,7 @@ fv_status fv_batch_set_state(fv_batch_t b, int mesh, const double* U, int on_dev
   if (e == cudaSuccess) e = launch_scatter_interior(src, dst, P, b->stream);
   if (e == cudaSuccess) e = launch_fill_ghosts(dst, P, b->stream);
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(b->stream);
+  b->smax_current = false;
   if (e != cudaSuccess) return cuda_fail(e, "fv_batch_set_state");
   return FV_OK;
 }
@@ -320,7 +339,7 @@ fv_status fv_batch_step(fv_batch_t b, double cfl, int use_graph) {
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "beginning the step capture");
-    cudaError_t le = launch_step(b, cfl);
+    cudaError_t le = launch_step_body(b, cfl);
     e = cudaStreamEndCapture(b->stream, &graph);
     if (le != cudaSuccess || e != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
@@ -336,7 +355,9 @@ fv_status fv_batch_step(fv_batch_t b, double cfl, int use_graph) {
     b->graph_kchunk = b->kchunk;
     b->graph_occupancy = b->occupancy;
   }
-  e = cudaGraphLaunch(b->graph, b->stream);
+  e = launch_max_if_stale(b);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, b->stream);
+  b->smax_current = e == cudaSuccess;
   if (e != cudaSuccess) return cuda_fail(e, "launching the step graph");
   return FV_OK;
 }
@@ -421,6 +442,7 @@ fv_status fv_batch_autotune(fv_batch_t b, double cfl, int* kchunk_out, int* occu
   if (r == cudaSuccess)
     r = cudaMemcpyAsync(b->dev.ctr, &saved, sizeof saved, cudaMemcpyHostToDevice, b->stream);
   if (r == cudaSuccess) r = cudaStreamSynchronize(b->stream);
+  b->smax_current = false;
   if (e != cudaSuccess) return cuda_fail(e, "autotuning");
   if (r != cudaSuccess) return cuda_fail(r, "restoring the state after autotuning");
   if (st != FV_OK) return st;

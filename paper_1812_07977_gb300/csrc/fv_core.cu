@@ -319,6 +319,7 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   cudaError_t e = cudaGetDevice(&m->device);
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device);
+  if (e == cudaSuccess && desc->precision == FV_PREC_FP32_BULK) e = fv_fp32::prepare_kernels();
   if (e != cudaSuccess) {
     delete m;
     return cuda_fail(e, "cudaGetDevice");

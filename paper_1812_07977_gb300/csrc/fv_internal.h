@@ -85,15 +85,22 @@ struct BatchDevice {
 // fv_step32_kernels.cu: the FP32-bulk substep (one fused kernel; z chunks
 // of `kchunk` planes per CTA) and its CFL reduction.
 namespace fv_fp32 {
+// Raises the shared-memory limit of the fused substep kernels on the current
+// device (they take more than the default 48 KB); before their first launch.
+cudaError_t prepare_kernels();
 cudaError_t launch_stage(int stage, const StepBuffers& b, const fvd::Params& P, double dt,
                          int kchunk, double vacuum_ratio, int occupancy, cudaStream_t s);
 cudaError_t launch_reduce_dt(const double* U, const fvd::Params& P, double vacuum_ratio,
                              DevCounters* ctr, cudaStream_t s);
-// Batches: per-mesh CFL dt on the device (dt = cfl / max), the fused substep
-// over all meshes' work items (one persistent launch), and the ghost fill.
+// Batches: per-mesh CFL maxima of the current states (launch_batch_max), dt =
+// cfl / max per mesh with the maxima and work counters then cleared
+// (launch_batch_dt), the fused substep over all meshes' work items (one
+// persistent launch; stage 2 refills the maxima with those of its output),
+// and the ghost fill.
 constexpr int kBatchDtChunk = 2048;
 constexpr int kBatchGhostChunk = 256;
 constexpr int kTileX = 32, kTileY = 8;
+cudaError_t launch_batch_max(const BatchDevice& b, cudaStream_t s);
 cudaError_t launch_batch_dt(const BatchDevice& b, double cfl, cudaStream_t s);
 cudaError_t launch_batch_stage(int stage, const BatchDevice& b, int kchunk, int occupancy,
                                int num_sms, cudaStream_t s);

@@ -47,12 +47,41 @@ constexpr int kYFaces = TX * (TY + 1);      // 288
 // the z face per plane (the others wait for it at the plane's barrier).
 __device__ __forceinline__ int yface0(int tid) { return (tid + kThreads - 32) % kThreads; }
 
+#ifndef FV32_STAGE_DEPTH
+#define FV32_STAGE_DEPTH 1
+#endif
+// Iterations whose FP64 input is in flight ahead of the one being computed,
+// and the ring of staging slots (one per iteration in flight plus the one in
+// use).  Iteration k's slot holds the column cells of plane k+2 (the z
+// window) and the halo cells of plane k, each copied by the thread that uses
+// it, so a slot is reused without a barrier.
+constexpr int kStageDepth = FV32_STAGE_DEPTH;
+constexpr int kRing = kStageDepth + 1;
+
 struct Smem {
+  double col[kRing][NF][kThreads];
+  double halo[kRing][NF][kHalo];
   float w[NF][PY][PX];
   float fx[NF][TY][TX + 1];
   float fy[NF][TY + 1][TX];
   unsigned char same[PY][PX];   // cell equals (bit for bit) the cell one plane below
 };
+
+// Asynchronous 8-byte copy global -> shared (completes at cp_async_wait).
+__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// Waits until at most N of this thread's committed copy groups are pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 __device__ __forceinline__ void load_state(const double* __restrict__ U, long long nf,
                                            long long off, double u[NF]) {
@@ -225,23 +254,36 @@ __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
   if (k0 != 0 || !owner) fallbacks = 0;
   unsigned long long bad = 0;
 
-  // raw FP64 state of the next column plane (k+2) and halo cell (plane k),
-  // loaded one iteration ahead so their latency overlaps the face work
-  double next_col[NF], next_halo[NF];
-  load_state(src, nf, col + (long long)(k0 + 4) * P.sz, next_col);
-  if (tid < kHalo) load_state(src, nf, hcolo + (long long)(k0 + 2) * P.sz, next_halo);
+  // raw FP64 state of iteration t (column plane t+2, halo cell of plane t),
+  // copied kStageDepth iterations ahead into the staging ring so that its
+  // latency overlaps the face work; every iteration commits one group
+  auto stage_in = [&](int t) {
+    if (t < k1) {
+      const int slot = t % kRing;
+      const double* c = src + col + (long long)(t + 4) * P.sz;
+#pragma unroll
+      for (int q = 0; q < NF; ++q) cp_async8(&s.col[slot][q][tid], c + q * nf);
+      if (tid < kHalo) {
+        const double* h = src + hcolo + (long long)(t + 2) * P.sz;
+#pragma unroll
+        for (int q = 0; q < NF; ++q) cp_async8(&s.halo[slot][q][tid], h + q * nf);
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int t = 0; t < kStageDepth; ++t) stage_in(k0 + t);
 
   for (int k = k0; k < k1; ++k) {
     if (owner && !physical(w0)) ++bad;   // each interior cell once per substep
+    stage_in(k + kStageDepth);
+    cp_async_wait<kStageDepth>();        // this iteration's group has landed
+    const int slot = k % kRing;
     double cur_col[NF], cur_halo[NF];
 #pragma unroll
     for (int q = 0; q < NF; ++q) {
-      cur_col[q] = next_col[q];
-      cur_halo[q] = next_halo[q];
-    }
-    if (k + 1 < k1) {
-      load_state(src, nf, col + (long long)(k + 5) * P.sz, next_col);
-      if (tid < kHalo) load_state(src, nf, hcolo + (long long)(k + 3) * P.sz, next_halo);
+      cur_col[q] = s.col[slot][q][tid];
+      cur_halo[q] = tid < kHalo ? s.halo[slot][q][tid] : 0.0;
     }
     // operands of this plane's RK combine, loaded before the face work
     double rk0[NF], rk1[NF];
@@ -363,7 +405,8 @@ template <int STAGE, int MINB, bool MC>
 __global__ void __launch_bounds__(kThreads, MINB)
 k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params32 Q, float dt,
           int kchunk, DevCounters* ctr) {
-  __shared__ Smem s;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& s = *reinterpret_cast<Smem*>(smem_raw);
   unsigned fallbacks = 0, evaluated = 0, smax_next = 0;
   unsigned long long bad = 0, bad_next = 0;
   const int k0 = blockIdx.z * kchunk;
@@ -382,15 +425,18 @@ k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params
 // ---------------------------------------------------------------- batches
 // Persistent kernel over the tiles of many meshes: each CTA takes work items
 // (mesh, tile x, tile y, z chunk) from an atomic counter until none is left.
+// Stage 2 also folds the CFL maximum of each item's output cells into its
+// mesh's smax_bits (the next step's dt).
 template <int STAGE, int MINB, bool MC>
 __global__ void __launch_bounds__(kThreads, MINB)
-k_stage32_batch(double* __restrict__ U, double* __restrict__ U1,
-                const BatchMesh* __restrict__ meshes, const int4* __restrict__ items, int nitems,
-                int kchunk, unsigned* __restrict__ next_item, DevCounters* ctr) {
-  __shared__ Smem s;
+k_stage32_batch(double* __restrict__ U, double* __restrict__ U1, BatchMesh* __restrict__ meshes,
+                const int4* __restrict__ items, int nitems, int kchunk,
+                unsigned* __restrict__ next_item, DevCounters* ctr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& s = *reinterpret_cast<Smem*>(smem_raw);
   __shared__ int s_item;
-  unsigned fallbacks = 0, evaluated = 0, unused_smax = 0;
-  unsigned long long bad = 0, unused_bad = 0;
+  unsigned fallbacks = 0, evaluated = 0;
+  unsigned long long bad = 0, bad_next = 0;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_item = (int)atomicAdd(next_item, 1u);
@@ -398,14 +444,17 @@ k_stage32_batch(double* __restrict__ U, double* __restrict__ U1,
     const int it = s_item;
     if (it >= nitems) break;
     const int4 w = items[it];       // mesh, tile x, tile y, chunk
-    const BatchMesh& m = meshes[w.x];
+    BatchMesh& m = meshes[w.x];
     const int k0 = w.w * kchunk;
-    stage32_tile<STAGE, MC, false>(s, U + m.offset, U1 + m.offset, m.P, m.Q, (float)m.dt,
-                                   w.y * TX, w.z * TY, k0, min(k0 + kchunk, m.P.nz), fallbacks,
-                                   bad, evaluated, unused_smax, unused_bad);
+    unsigned smax_next = 0;
+    stage32_tile<STAGE, MC, STAGE == 2>(s, U + m.offset, U1 + m.offset, m.P, m.Q, (float)m.dt,
+                                        w.y * TX, w.z * TY, k0, min(k0 + kchunk, m.P.nz),
+                                        fallbacks, bad, evaluated, smax_next, bad_next);
+    if (STAGE == 2) max_speed_to(&m.smax_bits, smax_next);
   }
   if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
   if (bad) atomicAdd(&ctr->np_step, bad);
+  if (bad_next) atomicAdd(&ctr->np_dt, bad_next);
   warp_count(&ctr->faces, evaluated);
 }
 
@@ -521,31 +570,63 @@ Params32 make_params32(const fvd::Params& P, double vacuum_ratio) {
   return Q;
 }
 
+// Launches a substep kernel with one Smem of dynamic shared memory (more than
+// the default 48 KB; prepare_kernels raised the limit).
+template <typename K, typename... A>
+static cudaError_t launch_smem(K kernel, dim3 grid, cudaStream_t s, A... args) {
+  kernel<<<grid, kThreads, sizeof(Smem), s>>>(args...);
+  return cudaGetLastError();
+}
+
+template <typename K>
+static cudaError_t raise_smem(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(Smem));
+}
+
+template <int STAGE, int MINB>
+static cudaError_t raise_smem_all() {
+  cudaError_t e = raise_smem(k_stage32<STAGE, MINB, true>);
+  if (e == cudaSuccess) e = raise_smem(k_stage32<STAGE, MINB, false>);
+  if (e == cudaSuccess) e = raise_smem(k_stage32_batch<STAGE, MINB, true>);
+  if (e == cudaSuccess) e = raise_smem(k_stage32_batch<STAGE, MINB, false>);
+  return e;
+}
+
 cudaError_t launch_stage(int stage, const StepBuffers& b, const fvd::Params& P, double dt,
                          int kchunk, double vacuum_ratio, int occupancy, cudaStream_t s) {
   const Params32 Q = make_params32(P, vacuum_ratio);
   if (kchunk < 1) kchunk = 1;
   const dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + kchunk - 1) / kchunk);
   const float fdt = (float)dt;
+  cudaError_t e;
   // 3 CTAs per SM: 80 registers, a few spills; 2 CTAs per SM: up to 128
   if (Q.theta == 2.0f) {
     if (occupancy == 3) {
-      if (stage == 1) k_stage32<1, 3, true><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
-      else k_stage32<2, 3, true><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+      if (stage == 1) e = launch_smem(k_stage32<1, 3, true>, grid, s, b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+      else e = launch_smem(k_stage32<2, 3, true>, grid, s, b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
     } else {
-      if (stage == 1) k_stage32<1, 2, true><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
-      else k_stage32<2, 2, true><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+      if (stage == 1) e = launch_smem(k_stage32<1, 2, true>, grid, s, b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+      else e = launch_smem(k_stage32<2, 2, true>, grid, s, b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
     }
   } else {
     if (occupancy == 3) {
-      if (stage == 1) k_stage32<1, 3, false><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
-      else k_stage32<2, 3, false><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+      if (stage == 1) e = launch_smem(k_stage32<1, 3, false>, grid, s, b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+      else e = launch_smem(k_stage32<2, 3, false>, grid, s, b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
     } else {
-      if (stage == 1) k_stage32<1, 2, false><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
-      else k_stage32<2, 2, false><<<grid, kThreads, 0, s>>>(b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+      if (stage == 1) e = launch_smem(k_stage32<1, 2, false>, grid, s, b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
+      else e = launch_smem(k_stage32<2, 2, false>, grid, s, b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
     }
   }
-  return cudaGetLastError();
+  return e;
+}
+
+cudaError_t prepare_kernels() {
+  cudaError_t e = raise_smem_all<1, 2>();
+  if (e == cudaSuccess) e = raise_smem_all<2, 2>();
+  if (e == cudaSuccess) e = raise_smem_all<1, 3>();
+  if (e == cudaSuccess) e = raise_smem_all<2, 3>();
+  return e;
 }
 
 cudaError_t launch_reduce_dt(const double* U, const fvd::Params& P, double vacuum_ratio,
@@ -563,30 +644,35 @@ cudaError_t launch_reduce_dt(const double* U, const fvd::Params& P, double vacuu
 
 namespace fv_fp32 {
 
-cudaError_t launch_batch_dt(const BatchDevice& b, double cfl, cudaStream_t s) {
+cudaError_t launch_batch_max(const BatchDevice& b, cudaStream_t s) {
   k_batch_reset<<<1, 128, 0, s>>>(b.meshes, b.nmesh, b.next_item);
   if (b.ndt_blocks > 0) k_batch_dt<<<b.ndt_blocks, 256, 0, s>>>(b.U, b.meshes, b.dt_blocks, b.ctr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_dt(const BatchDevice& b, double cfl, cudaStream_t s) {
   k_batch_dt_finalize<<<1, 128, 0, s>>>(b.meshes, b.nmesh, cfl);
+  k_batch_reset<<<1, 128, 0, s>>>(b.meshes, b.nmesh, b.next_item);
   return cudaGetLastError();
 }
 
 template <bool MC>
-static void batch_stage(int stage, const BatchDevice& b, int kchunk, int occupancy, int grid,
-                        unsigned* counter, cudaStream_t s) {
+static cudaError_t batch_stage(int stage, const BatchDevice& b, int kchunk, int occupancy,
+                               int grid, unsigned* counter, cudaStream_t s) {
   if (occupancy == 3) {
     if (stage == 1)
-      k_stage32_batch<1, 3, MC><<<grid, kThreads, 0, s>>>(b.U, b.U1, b.meshes, b.items,
-                                                           b.nitems, kchunk, counter, b.ctr);
+      return launch_smem(k_stage32_batch<1, 3, MC>, grid, s, b.U, b.U1, b.meshes, b.items,
+                         b.nitems, kchunk, counter, b.ctr);
     else
-      k_stage32_batch<2, 3, MC><<<grid, kThreads, 0, s>>>(b.U, b.U1, b.meshes, b.items,
-                                                           b.nitems, kchunk, counter, b.ctr);
+      return launch_smem(k_stage32_batch<2, 3, MC>, grid, s, b.U, b.U1, b.meshes, b.items,
+                         b.nitems, kchunk, counter, b.ctr);
   } else {
     if (stage == 1)
-      k_stage32_batch<1, 2, MC><<<grid, kThreads, 0, s>>>(b.U, b.U1, b.meshes, b.items,
-                                                           b.nitems, kchunk, counter, b.ctr);
+      return launch_smem(k_stage32_batch<1, 2, MC>, grid, s, b.U, b.U1, b.meshes, b.items,
+                         b.nitems, kchunk, counter, b.ctr);
     else
-      k_stage32_batch<2, 2, MC><<<grid, kThreads, 0, s>>>(b.U, b.U1, b.meshes, b.items,
-                                                           b.nitems, kchunk, counter, b.ctr);
+      return launch_smem(k_stage32_batch<2, 2, MC>, grid, s, b.U, b.U1, b.meshes, b.items,
+                         b.nitems, kchunk, counter, b.ctr);
   }
 }
 
@@ -596,9 +682,8 @@ cudaError_t launch_batch_stage(int stage, const BatchDevice& b, int kchunk, int 
                                int num_sms, cudaStream_t s) {
   const int grid = num_sms * (occupancy == 3 ? 3 : 2);
   unsigned* counter = b.next_item + (stage == 1 ? 0 : 1);
-  if (b.all_mc) batch_stage<true>(stage, b, kchunk, occupancy, grid, counter, s);
-  else batch_stage<false>(stage, b, kchunk, occupancy, grid, counter, s);
-  return cudaGetLastError();
+  return b.all_mc ? batch_stage<true>(stage, b, kchunk, occupancy, grid, counter, s)
+                  : batch_stage<false>(stage, b, kchunk, occupancy, grid, counter, s);
 }
 
 cudaError_t launch_batch_ghosts(int stage, const BatchDevice& b, cudaStream_t s) {

@@ -87,6 +87,26 @@ def test_batch_dt_per_mesh_matches_oracle():
         assert abs(dts[m] - dto) <= 1e-6 * dto, (m, dts[m], dto)
 
 
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_dt_follows_set_state(use_graph):
+    """The second substep leaves each mesh's CFL maximum for the next step;
+    a state set in between replaces it: the step after set_state uses the dt
+    of the new state (here the initial one, so the first step's dt)."""
+    from paper_1812_07977_gb300.fv import Batch
+    spec = _small_batch(count=5, seed=7)
+    with Batch([s["shape"] for s in spec]) as b:
+        for m, s in enumerate(spec):
+            b.set_state(m, s["U0"])
+        b.step(0.4, use_graph=use_graph)
+        first = b.dts()
+        for _ in range(3):
+            b.step(0.4, use_graph=use_graph)
+        assert not np.array_equal(b.dts(), first)
+        b.set_state(2, spec[2]["U0"])
+        b.step(0.4, use_graph=use_graph)
+        assert b.dts()[2] == first[2]
+
+
 def test_batch_mesh_against_fp64_oracle():
     from paper_1812_07977_gb300.fv import Batch
     spec = _small_batch(count=4, seed=9)
