@@ -278,6 +278,40 @@ __device__ __forceinline__ double cell_speed(const Prim& w, const Params& P) {
          (fabs(w.vz) + c) * P.inv_d[2];
 }
 
+#ifndef FV_DT_FILTER
+#define FV_DT_FILTER 1
+#endif
+
+// x as a float rounded toward zero (|result| <= |x|, relative error below
+// 2^-23), on the integer pipe; `ok` is cleared unless x is +-0 or
+// 2^-100 <= |x| < 2^101.
+__device__ __forceinline__ float trunc_f32(double x, bool& ok) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  if (((hi << 1) | lo) == 0u) return 0.0f;
+  ok = ok && e - (1023u - 100u) <= 200u;
+  const unsigned f = ((e - 896u) << 23) | ((hi & 0x000FFFFFu) << 3) | (lo >> 29);
+  return __uint_as_float(f | (hi & 0x80000000u));
+}
+
+// An upper bound of cell_speed(w) from FP32 arithmetic: inputs truncated
+// (relative error < 2^-23 each) and about ten FP32 operations (< 2^-23 each)
+// give s32 within 2^-19 of the exact speed, and s32 (1 + 2^-14) is above
+// the exact speed and above the FP64 cell_speed (within 2 ulps of it).
+// +inf when rho or p is not positive or an operand is outside the range of
+// trunc_f32 (the FP64 speed is then always computed).
+__device__ __forceinline__ float speed_bound(const Prim& w, float g32, const float i32[3]) {
+  bool ok = true;
+  const float r = trunc_f32(w.r, ok), p = trunc_f32(w.p, ok);
+  const float vx = trunc_f32(w.vx, ok), vy = trunc_f32(w.vy, ok), vz = trunc_f32(w.vz, ok);
+  if (!(ok && r > 0.0f && p > 0.0f)) return __int_as_float(0x7F800000);
+  const float c = __fsqrt_rn(__fdiv_rn(__fmul_rn(g32, p), r));
+  const float sp = __fadd_rn(__fadd_rn(__fmul_rn(__fadd_rn(fabsf(vx), c), i32[0]),
+                                       __fmul_rn(__fadd_rn(fabsf(vy), c), i32[1])),
+                             __fmul_rn(__fadd_rn(fabsf(vz), c), i32[2]));
+  return __fmul_ru(sp, 1.0f + 0x1p-14f);
+}
+
 // Primitives of every ghosted cell (what k_prim gives the first substep)
 // and, over the interior cells, the maximum CFL speed and the non-physical
 // count, in one pass over the state.  The maximum is exact in any order:
@@ -287,7 +321,11 @@ __device__ __forceinline__ double cell_speed(const Prim& w, const Params& P) {
 // cell has its primitives, speed and validity; when the whole warp has such
 // cells (uniform regions), it skips the arithmetic.  Non-physical interior
 // cells count once, for the time step (a substep that uses these
-// primitives does not count them again).
+// primitives does not count them again).  A cell whose FP32 speed bound is
+// below the thread's running maximum cannot raise it: when no lane of the
+// warp needs it, the FP64 speed is not computed (the maximum is unchanged,
+// so the result is the same bits), and 0 stands in for it, so that a later
+// equal cell changes nothing either.
 __global__ void __launch_bounds__(kDtThreads)
 k_prim_dt(const double* __restrict__ U, double* __restrict__ W, Params P, DevCounters* ctr) {
   const long long nf = P.nfield;
@@ -303,10 +341,14 @@ k_prim_dt(const double* __restrict__ U, double* __restrict__ W, Params P, DevCou
   const int sj = (int)((stride - (long long)sk * P.sz) / X);
   const int si = (int)(stride - (long long)sk * P.sz - (long long)sj * X);
   double smax = 0.0, s = 0.0;
+  float smax_f = 0.0f;   // smax rounded toward zero
   unsigned long long bad = 0;
   double up[NF] = {0.0, 0.0, 0.0, 0.0, 0.0};
   Prim w = Prim{0.0, 0.0, 0.0, 0.0, 0.0};
   bool have = false, bad_cell = false;
+  const float g32 = __double2float_ru(P.gamma);
+  const float i32[3] = {__double2float_ru(P.inv_d[0]), __double2float_ru(P.inv_d[1]),
+                        __double2float_ru(P.inv_d[2])};
   for (; c < nf; c += stride) {
     double u[NF];
     bool eq = have;
@@ -320,7 +362,10 @@ k_prim_dt(const double* __restrict__ U, double* __restrict__ W, Params P, DevCou
     if (!__all_sync(__activemask(), eq)) {
       w = cons_to_prim(u, P);
       bad_cell = !(is_pos(w.r) && is_pos(w.p));
-      s = cell_speed(w, P);
+      // smax_f <= smax, so bound < smax_f means the speed is below smax
+      const bool need = !FV_DT_FILTER || !(speed_bound(w, g32, i32) < smax_f);
+      if (__any_sync(__activemask(), need)) s = cell_speed(w, P);
+      else s = 0.0;  // below smax: equal cells that follow change nothing
     }
     W[c] = w.r;
     W[nf + c] = w.vx;
@@ -329,7 +374,10 @@ k_prim_dt(const double* __restrict__ U, double* __restrict__ W, Params P, DevCou
     W[4 * nf + c] = w.p;
     if (i >= 2 && i < P.nx + 2 && j >= 2 && j < P.ny + 2 && k >= 2 && k < P.nz + 2) {
       bad += bad_cell;
-      if (s > smax) smax = s;
+      if (s > smax) {
+        smax = s;
+        smax_f = __double2float_rz(smax);
+      }
     }
     i += si;
     j += sj;

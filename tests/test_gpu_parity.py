@@ -138,6 +138,57 @@ def test_periodic_random_bitwise_and_conserved_sums():
     m.close()
 
 
+def _wide_range_states(nx, ny, nz, seed):
+    """Physical states whose speeds span many orders of magnitude: rho and p
+    log-uniform over 1e-30 .. 1e30 in a slab of four columns (partly
+    outside the FP32 bound's operand range; at rest there, with a 1e-45 y
+    velocity in two of them, and p / rho within 1e-2 .. 1e2), 1e-3 .. 1e3
+    with velocities up to 10 elsewhere; a fast cell where it is visited
+    last, or first; and a uniform state perturbed by 1e-13 (near ties)."""
+    rng = np.random.default_rng(seed)
+    shape = (nz, ny, nx)
+    rho = 10.0 ** rng.uniform(-3, 3, shape)
+    p = 10.0 ** rng.uniform(-3, 3, shape)
+    v = rng.uniform(-10, 10, (3,) + shape)
+    rho[:, :, :4] = 10.0 ** rng.uniform(-30, 30, (nz, ny, 4))
+    p[:, :, :4] = rho[:, :, :4] * 10.0 ** rng.uniform(-2, 2, (nz, ny, 4))
+    v[..., :4] = 0.0            # at rest where rho, p span 1e-30 .. 1e30
+    v[1, ..., 2:4] = 1e-45
+    out = []
+    for where in (-1, 0):
+        r2, p2, v2 = rho.copy(), p.copy(), v.copy()
+        r2.reshape(-1)[where] = 1e-3
+        p2.reshape(-1)[where] = 1e3
+        v2[0].reshape(-1)[where] = 50.0
+        out.append(problems.conserved_from_primitive(r2, v2[0], v2[1], v2[2], p2))
+    # nearly tied speeds: a uniform state perturbed by 1e-13 relative
+    e = 1.0 + 1e-13 * rng.uniform(-1, 1, (5,) + shape)
+    out.append(problems.conserved_from_primitive(e[0], 0.3 * e[1], -0.2 * e[2], 0.1 * e[3], e[4]))
+    return out
+
+
+def test_reduce_dt_wide_range_bitwise():
+    """The time-step pass skips the FP64 speed of cells whose FP32 bound
+    cannot raise the running maximum: on states where many cells are skipped
+    and the bound's edge cases occur, dt stays the oracle's bits (exact
+    build) and within a few ulps (FMA build).  Each thread visits several
+    cells at this size."""
+    from paper_1812_07977_gb300.fv import Mesh
+    n = (128, 120, 96)
+    for seed, U0 in enumerate(_wide_range_states(*n, seed=3)):
+        om = oracle.mesh(*n, ly=2.0)
+        dto, _, bad = oracle.reduce_dt(om, oracle.ghosted_from_interior(om, U0), 0.4)
+        assert bad == 0
+        for prec in ("fp64", "fp64_fma"):
+            with Mesh(*n, ly=2.0, precision=prec) as m:
+                m.set_state(U0)
+                dt = m.reduce_dt(0.4)
+            if prec == "fp64":
+                assert dt == dto, (seed, dt, dto)
+            else:
+                assert abs(dt - dto) <= 1e-14 * dto, (seed, dt, dto)
+
+
 def test_fma_dt_within_a_few_ulps():
     """The FMA build's CFL time step (Newton-Raphson sound speed, contracted
     sums) against the oracle's, on random and Riemann states."""
