@@ -283,7 +283,7 @@ def run_batched(args, world, dev, rank):
     b = Batch([s["shape"] for s in spec], stream=stream)
     for m, s in enumerate(spec):
         b.set_state(m, torch.from_numpy(s["U0"]).to(dev))
-    kc, occ, tune_ms = b.autotune(CFL)
+    kc, occ, tile_y, tune_ms = b.autotune(CFL)
     for _ in range(args.warmup):
         b.step(CFL, use_graph=True)
     for m, s in enumerate(spec):
@@ -304,7 +304,8 @@ def run_batched(args, world, dev, rank):
     return {"value": world * cells * args.batch_steps / el, "unit": "zone-updates/s",
             "ms_per_step": 1e3 * el / args.batch_steps, "steps": args.batch_steps,
             "meshes": nmesh, "cells": cells, "work_items": items,
-            "autotuned": {"kchunk": kc, "ctas_per_sm": occ, "ms_per_step": tune_ms},
+            "autotuned": {"kchunk": kc, "tile": f"32x{tile_y}", "occupancy": occ,
+                          "ms_per_step": tune_ms},
             "timing": "CUDA events on the batch's stream around the graph launches",
             "nonphysical": bad}
 

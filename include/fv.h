@@ -251,15 +251,20 @@ FV_API fv_status fv_batch_step(fv_batch_t b, double cfl, int use_graph);
 /* The dt each mesh used in the last step (nmesh doubles).  Synchronising. */
 FV_API fv_status fv_batch_get_dt(fv_batch_t b, double* dt);
 
-/* Launch configuration: z planes per work item and CTAs per SM (2 or 3). */
-FV_API fv_status fv_batch_set_tuning(fv_batch_t b, int kchunk, int occupancy);
+/* Launch configuration: z planes per work item (kchunk in [1, 4096]), the
+ * work item's tile of 32 x tile_y columns (tile_y 4, 8 or 16: CTAs of 128,
+ * 256 or 512 threads) and occupancy 2 (16 warps per SM, up to 128
+ * registers) or, for tile_y 8 only, 3 (80 registers).  Every configuration
+ * gives the same bits.  Errors: INVALID_ARG. */
+FV_API fv_status fv_batch_set_tuning(fv_batch_t b, int kchunk, int occupancy, int tile_y);
 
-/* Autotuner: times one step for each z chunk in {8, 16, 32, 64} and each
- * occupancy in {2, 3} on the batch's current state, keeps the fastest and
- * reports it.  The state and counters are restored afterwards (a snapshot
- * buffer of one state is allocated on first use).  Synchronising. */
+/* Autotuner: times three steps for each z chunk in {8, 16, 32, 64} and each
+ * (tile_y, occupancy) in {(4, 2), (8, 2), (8, 3), (16, 2)} on the batch's
+ * current state, keeps the fastest and reports it (any output pointer may be
+ * NULL).  The state and counters are restored afterwards (a snapshot buffer
+ * of one state is allocated on first use).  Synchronising. */
 FV_API fv_status fv_batch_autotune(fv_batch_t b, double cfl, int* kchunk, int* occupancy,
-                                   double* ms_per_step);
+                                   int* tile_y, double* ms_per_step);
 
 FV_API fv_status fv_batch_get_counters(fv_batch_t b, long long* nonphysical_cells,
                                        long long* fallback_faces);
@@ -351,8 +356,12 @@ FV_API fv_status fv_conserved_sums_noalloc(const double* U, int nx, int ny, int 
  *  FV_TUNE_VACUUM_RATIO  FP32-bulk: recover the pressure in FP64 where the
  *                        kinetic energy exceeds this fraction of E (default
  *                        0.99; a value > 1 turns the recovery off)
- *  FV_TUNE_OCCUPANCY     CTAs per SM the fused FP32-bulk kernel is built for:
- *                        2 (up to 128 registers, default) or 3 (80 registers)
+ *  FV_TUNE_OCCUPANCY     occupancy the fused FP32-bulk kernel is built for:
+ *                        2 (16 warps per SM, up to 128 registers, default)
+ *                        or 3 (24 warps, 80 registers; tile height 8 only)
+ *  FV_TUNE_TILE_Y        tile height of the fused FP32-bulk kernel: 4, 8
+ *                        (default) or 16 (tiles of 32 x 4 / 8 / 16 columns,
+ *                        CTAs of 128 / 256 / 512 threads); the same bits
  *  FV_TUNE_SWEEP_SEGMENTS  FP64 paths: pieces each grid line of a sweep is
  *                        cut into, to run more, shorter work items (integer
  *                        in [0, 4096], capped at the line's length; 0, the
@@ -365,7 +374,8 @@ typedef enum {
   FV_TUNE_KCHUNK = 0,
   FV_TUNE_VACUUM_RATIO = 1,
   FV_TUNE_OCCUPANCY = 2,
-  FV_TUNE_SWEEP_SEGMENTS = 3
+  FV_TUNE_SWEEP_SEGMENTS = 3,
+  FV_TUNE_TILE_Y = 4
 } fv_tuning_key;
 FV_API fv_status fv_set_tuning(fv_mesh_t m, int key, double value);
 

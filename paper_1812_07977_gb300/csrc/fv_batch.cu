@@ -53,11 +53,12 @@ struct fv_batch_s {
   DevCounters* host_ctr = nullptr;
   int kchunk = 32;
   int occupancy = 2;
+  int tile_y = 8;                    // tile height of the fused kernel (4, 8 or 16)
   bool smax_current = false;         // meshes[].smax_bits hold the current states' maxima
   // CUDA graph of one whole step
   cudaGraphExec_t graph = nullptr;
   double graph_cfl = -1.0;
-  int graph_kchunk = -1, graph_occupancy = -1;
+  int graph_kchunk = -1, graph_occupancy = -1, graph_tile_y = -1;
 };
 
 namespace {
@@ -98,9 +99,10 @@ void free_batch(fv_batch_s* b) {
   delete b;
 }
 
-// Fused-kernel work items for a z chunk: every (mesh, tile x, tile y, chunk),
-// largest meshes first so the tail of the persistent launch is short.
-fv_status build_items(fv_batch_t b, int kchunk) {
+// Fused-kernel work items for a z chunk and tile height: every (mesh, tile x,
+// tile y, chunk), largest meshes first so the tail of the persistent launch
+// is short.
+fv_status build_items(fv_batch_t b, int kchunk, int tile_y) {
   if (b->graph) {  // the captured step refers to the item table being replaced
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
@@ -115,7 +117,7 @@ fv_status build_items(fv_batch_t b, int kchunk) {
   for (int m : order) {
     const fvd::Params& P = b->host_meshes[m].P;
     const int tx = (P.nx + fv_fp32::kTileX - 1) / fv_fp32::kTileX;
-    const int ty = (P.ny + fv_fp32::kTileY - 1) / fv_fp32::kTileY;
+    const int ty = (P.ny + tile_y - 1) / tile_y;
     const int tz = (P.nz + kchunk - 1) / kchunk;
     for (int z = 0; z < tz; ++z)
       for (int y = 0; y < ty; ++y)
@@ -129,6 +131,7 @@ fv_status build_items(fv_batch_t b, int kchunk) {
   if (e != cudaSuccess) return cuda_fail(e, "uploading work items");
   b->dev.nitems = (int)items.size();
   b->kchunk = kchunk;
+  b->tile_y = tile_y;
   return FV_OK;
 }
 
@@ -138,7 +141,8 @@ fv_status build_items(fv_batch_t b, int kchunk) {
 cudaError_t launch_step_body(fv_batch_t b, double cfl) {
   cudaError_t e = fv_fp32::launch_batch_dt(b->dev, cfl, b->stream);
   for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage) {
-    e = fv_fp32::launch_batch_stage(stage, b->dev, b->kchunk, b->occupancy, b->num_sms,
+    e = fv_fp32::launch_batch_stage(stage, b->dev, b->kchunk, b->occupancy, b->tile_y,
+                                    b->num_sms,
                                     b->stream);
     if (e == cudaSuccess) e = fv_fp32::launch_batch_ghosts(stage, b->dev, b->stream);
   }
@@ -254,7 +258,7 @@ fv_status fv_batch_create(const fv_mesh_desc* descs, int nmesh, void* cuda_strea
     free_batch(b);
     return cuda_fail(e, "initialising batch storage");
   }
-  fv_status st = build_items(b, 32);
+  fv_status st = build_items(b, 32, 8);
   if (st != FV_OK) {
     free_batch(b);
     return st;
@@ -331,7 +335,7 @@ fv_status fv_batch_step(fv_batch_t b, double cfl, int use_graph) {
     return FV_OK;
   }
   if (!b->graph || b->graph_cfl != cfl || b->graph_kchunk != b->kchunk ||
-      b->graph_occupancy != b->occupancy) {
+      b->graph_occupancy != b->occupancy || b->graph_tile_y != b->tile_y) {
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;
@@ -354,6 +358,7 @@ fv_status fv_batch_step(fv_batch_t b, double cfl, int use_graph) {
     b->graph_cfl = cfl;
     b->graph_kchunk = b->kchunk;
     b->graph_occupancy = b->occupancy;
+    b->graph_tile_y = b->tile_y;
   }
   e = launch_max_if_stale(b);
   if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, b->stream);
@@ -376,21 +381,25 @@ fv_status fv_batch_get_dt(fv_batch_t b, double* dt) {
   return FV_OK;
 }
 
-fv_status fv_batch_set_tuning(fv_batch_t b, int kchunk, int occupancy) {
+fv_status fv_batch_set_tuning(fv_batch_t b, int kchunk, int occupancy, int tile_y) {
   fv_status st = check(b);
   if (st != FV_OK) return st;
-  if (kchunk < 1 || kchunk > 4096 || (occupancy != 2 && occupancy != 3))
-    return fail(FV_ERR_INVALID_ARG, "kchunk %d must be in [1, 4096] and occupancy 2 or 3",
-                kchunk, occupancy);
+  if (kchunk < 1 || kchunk > 4096 || !fv_fp32::valid_config(tile_y, occupancy))
+    return fail(FV_ERR_INVALID_ARG,
+                "kchunk %d must be in [1, 4096], tile_y (%d) 4, 8 or 16 and occupancy (%d) 2, "
+                "or 3 with tile_y 8",
+                kchunk, tile_y, occupancy);
   DeviceGuard g(b->device);
   cudaStreamSynchronize(b->stream);
-  if (kchunk != b->kchunk && (st = build_items(b, kchunk)) != FV_OK) return st;
+  if ((kchunk != b->kchunk || tile_y != b->tile_y) &&
+      (st = build_items(b, kchunk, tile_y)) != FV_OK)
+    return st;
   b->occupancy = occupancy;
   return FV_OK;
 }
 
 fv_status fv_batch_autotune(fv_batch_t b, double cfl, int* kchunk_out, int* occupancy_out,
-                            double* ms_per_step_out) {
+                            int* tile_y_out, double* ms_per_step_out) {
   fv_status st = check(b);
   if (st != FV_OK) return st;
   if (!(cfl > 0.0)) return fail(FV_ERR_INVALID_ARG, "cfl must be > 0");
@@ -410,12 +419,13 @@ fv_status fv_batch_autotune(fv_batch_t b, double cfl, int* kchunk_out, int* occu
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   const int kcs[] = {8, 16, 32, 64};
-  const int occs[] = {2, 3};
+  const int cfgs[4][2] = {{4, 2}, {8, 2}, {8, 3}, {16, 2}};   // tile height, occupancy
   double best = 1e300;
-  int best_kc = b->kchunk, best_occ = b->occupancy;
+  int best_kc = b->kchunk, best_occ = b->occupancy, best_ty = b->tile_y;
   for (int kc : kcs) {
-    if ((st = build_items(b, kc)) != FV_OK) break;
-    for (int occ : occs) {
+    for (const auto& cfg : cfgs) {
+      if ((st = build_items(b, kc, cfg[0])) != FV_OK) break;
+      const int occ = cfg[1];
       b->occupancy = occ;
       e = launch_step(b, cfl);  // warm-up
       cudaEventRecord(e0, b->stream);
@@ -429,13 +439,14 @@ fv_status fv_batch_autotune(fv_batch_t b, double cfl, int* kchunk_out, int* occu
         best = ms / 3.0;
         best_kc = kc;
         best_occ = occ;
+        best_ty = cfg[0];
       }
     }
-    if (e != cudaSuccess) break;
+    if (e != cudaSuccess || st != FV_OK) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (st == FV_OK && e == cudaSuccess) st = build_items(b, best_kc);
+  if (st == FV_OK && e == cudaSuccess) st = build_items(b, best_kc, best_ty);
   b->occupancy = best_occ;
   // restore the state (ghosts included) and the counters
   cudaError_t r = cudaMemcpyAsync(b->dev.U, b->backup, sb, cudaMemcpyDeviceToDevice, b->stream);
@@ -448,6 +459,7 @@ fv_status fv_batch_autotune(fv_batch_t b, double cfl, int* kchunk_out, int* occu
   if (st != FV_OK) return st;
   if (kchunk_out) *kchunk_out = best_kc;
   if (occupancy_out) *occupancy_out = best_occ;
+  if (tile_y_out) *tile_y_out = best_ty;
   if (ms_per_step_out) *ms_per_step_out = best;
   return FV_OK;
 }

@@ -60,6 +60,7 @@ struct fv_mesh_s {
   int kchunk;               // z planes per CTA of the fused FP32-bulk kernel
   double vacuum_ratio;      // FP32-bulk FP64 pressure-recovery threshold
   int occupancy;            // CTAs per SM the fused kernel is compiled for (2 or 3)
+  int tile_y;               // tile height of the fused kernel (4, 8 or 16)
   int segments;             // pieces per grid line of the FP64 sweeps (0: automatic)
   bool w_current;           // FP64: W holds the primitives of U (from the dt pass)
   bool smax_current;        // FP32-bulk: ctr->smax_next is the CFL maximum of U
@@ -255,7 +256,7 @@ cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
     if (e == cudaSuccess)
       e = timed(m, FV_KERNEL_FUSED, 1, [&] {
         return fv_fp32::launch_stage(stage, m->buf, m->P, dt, m->kchunk, m->vacuum_ratio,
-                                     m->occupancy, m->stream);
+                                     m->occupancy, m->tile_y, m->stream);
       });
     if (e != cudaSuccess) return e;
     double* dst = stage == 1 ? m->buf.U1 : m->buf.U;
@@ -311,6 +312,7 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   m->kchunk = desc->nz >= 64 ? 32 : desc->nz;
   m->vacuum_ratio = 0.99;
   m->occupancy = 2;
+  m->tile_y = 8;
   m->segments = 0;
   m->w_current = false;
   m->smax_current = false;
@@ -587,11 +589,21 @@ fv_status fv_set_tuning(fv_mesh_t m, int key, double value) {
     return FV_OK;
   }
   if (key == FV_TUNE_OCCUPANCY) {
-    if (value != 2.0 && value != 3.0) {
-      set_error("FV_TUNE_OCCUPANCY must be 2 or 3 (got %g)", value);
+    if ((value != 2.0 && value != 3.0) || !fv_fp32::valid_config(m->tile_y, (int)value)) {
+      set_error("FV_TUNE_OCCUPANCY must be 2, or 3 with tile height 8 (got %g, tile height %d)",
+                value, m->tile_y);
       return FV_ERR_INVALID_ARG;
     }
     m->occupancy = (int)value;
+    return FV_OK;
+  }
+  if (key == FV_TUNE_TILE_Y) {
+    if ((value != 4.0 && value != 8.0 && value != 16.0) ||
+        !fv_fp32::valid_config((int)value, m->occupancy)) {
+      set_error("FV_TUNE_TILE_Y must be 4, 8 or 16, and 8 at occupancy 3 (got %g)", value);
+      return FV_ERR_INVALID_ARG;
+    }
+    m->tile_y = (int)value;
     return FV_OK;
   }
   if (key == FV_TUNE_SWEEP_SEGMENTS) {

@@ -88,8 +88,13 @@ namespace fv_fp32 {
 // Raises the shared-memory limit of the fused substep kernels on the current
 // device (they take more than the default 48 KB); before their first launch.
 cudaError_t prepare_kernels();
+// The fused substep is built for tiles of 32 x tile_y columns, tile_y in
+// {4, 8, 16}, at occupancy 2 (16 warps per SM, 128 registers), and for
+// 32 x 8 tiles also at occupancy 3 (80 registers).
+bool valid_config(int tile_y, int occupancy);
 cudaError_t launch_stage(int stage, const StepBuffers& b, const fvd::Params& P, double dt,
-                         int kchunk, double vacuum_ratio, int occupancy, cudaStream_t s);
+                         int kchunk, double vacuum_ratio, int occupancy, int tile_y,
+                         cudaStream_t s);
 cudaError_t launch_reduce_dt(const double* U, const fvd::Params& P, double vacuum_ratio,
                              DevCounters* ctr, cudaStream_t s);
 // Batches: per-mesh CFL maxima of the current states (launch_batch_max), dt =
@@ -99,11 +104,11 @@ cudaError_t launch_reduce_dt(const double* U, const fvd::Params& P, double vacuu
 // and the ghost fill.
 constexpr int kBatchDtChunk = 2048;
 constexpr int kBatchGhostChunk = 256;
-constexpr int kTileX = 32, kTileY = 8;
+constexpr int kTileX = 32;
 cudaError_t launch_batch_max(const BatchDevice& b, cudaStream_t s);
 cudaError_t launch_batch_dt(const BatchDevice& b, double cfl, cudaStream_t s);
 cudaError_t launch_batch_stage(int stage, const BatchDevice& b, int kchunk, int occupancy,
-                               int num_sms, cudaStream_t s);
+                               int tile_y, int num_sms, cudaStream_t s);
 cudaError_t launch_batch_ghosts(int stage, const BatchDevice& b, cudaStream_t s);
 fvd32::Params32 make_params32(const fvd::Params& P, double vacuum_ratio);
 }

@@ -32,20 +32,51 @@ using namespace fvd32;
 namespace fv_fp32 {
 namespace {
 
-constexpr int TX = 32;
-constexpr int TY = 8;
-constexpr int kThreads = TX * TY;
-constexpr int PX = TX + 4;                  // plane buffer with a two-cell halo
-constexpr int PY = TY + 4;
-constexpr int kHalo = PX * PY - TX * TY;    // 176 halo cells per plane
-constexpr int kXFaces = (TX + 1) * TY;      // 264
-constexpr int kYFaces = TX * (TY + 1);      // 288
+constexpr int TX = 32;   // tile width: one warp per tile row
+
+// A tile of TX x TY columns (TY = 4, 8 or 16: 128, 256 or 512 threads, one
+// per column) with its plane buffer (two-cell halo), halo cells and faces.
+template <int TY_>
+struct Shape {
+  static constexpr int TY = TY_;
+  static constexpr int kThreads = TX * TY;
+  static constexpr int PX = TX + 4;
+  static constexpr int PY = TY + 4;
+  static constexpr int kHalo = PX * PY - TX * TY;        // 160, 176, 208
+  static constexpr int kHaloPer = (kHalo + kThreads - 1) / kThreads;  // 2, 1, 1
+  static constexpr int kXFaces = (TX + 1) * TY;
+  static constexpr int kYFaces = TX * (TY + 1);
+  static_assert(kXFaces <= 2 * kThreads && kYFaces <= 2 * kThreads, "two face passes");
+};
 
 // First y face of thread tid.  The x faces beyond the first kThreads go to
 // warp 0; the y faces are assigned one warp later, so that their leftover
 // row goes to warp 1 and no warp evaluates more than two x / y faces plus
 // the z face per plane (the others wait for it at the plane's barrier).
-__device__ __forceinline__ int yface0(int tid) { return (tid + kThreads - 32) % kThreads; }
+template <class S>
+__device__ __forceinline__ int yface0(int tid) {
+  return (tid + S::kThreads - 32) % S::kThreads;
+}
+
+// Halo cell h of a tile (0 <= h < kHalo): the two rows below the tile, the
+// two above, then two columns on each side of every tile row; (row, col)
+// relative to the tile's first cell.
+template <class S>
+__device__ __forceinline__ void halo_cell(int h, int& row, int& col) {
+  constexpr int PX = S::PX;
+  if (h < 2 * PX) {
+    row = h / PX - 2;
+    col = h % PX - 2;
+  } else if (h < 4 * PX) {
+    row = S::TY + (h - 2 * PX) / PX;
+    col = (h - 2 * PX) % PX - 2;
+  } else {
+    const int u = h - 4 * PX;
+    row = u / 4;
+    const int c = u % 4;
+    col = c < 2 ? c - 2 : TX + c - 2;
+  }
+}
 
 #ifndef FV32_STAGE_DEPTH
 #define FV32_STAGE_DEPTH 1
@@ -58,13 +89,14 @@ __device__ __forceinline__ int yface0(int tid) { return (tid + kThreads - 32) % 
 constexpr int kStageDepth = FV32_STAGE_DEPTH;
 constexpr int kRing = kStageDepth + 1;
 
+template <class S>
 struct Smem {
-  double col[kRing][NF][kThreads];
-  double halo[kRing][NF][kHalo];
-  float w[NF][PY][PX];
-  float fx[NF][TY][TX + 1];
-  float fy[NF][TY + 1][TX];
-  unsigned char same[PY][PX];   // cell equals (bit for bit) the cell one plane below
+  double col[kRing][NF][S::kThreads];
+  double halo[kRing][NF][S::kHalo];
+  float w[NF][S::PY][S::PX];
+  float fx[NF][S::TY][TX + 1];
+  float fy[NF][S::TY + 1][TX];
+  unsigned char same[S::PY][S::PX];   // cell equals (bit for bit) the cell one plane below
 };
 
 // Asynchronous 8-byte copy global -> shared (completes at cp_async_wait).
@@ -96,7 +128,8 @@ __device__ __forceinline__ Prim32 load_prim(const double* __restrict__ U, long l
   return prim_from_state(u, Q);
 }
 
-__device__ __forceinline__ Prim32 smem_prim(const Smem& s, int row, int col) {
+template <class SM>
+__device__ __forceinline__ Prim32 smem_prim(const SM& s, int row, int col) {
   return Prim32{s.w[0][row][col], s.w[1][row][col], s.w[2][row][col], s.w[3][row][col],
                 s.w[4][row][col]};
 }
@@ -110,7 +143,8 @@ __device__ __forceinline__ bool same32(const Prim32& a, const Prim32& b) {
 
 // Stores the plane's primitives of one cell and whether they equal the
 // previous plane's in that slot (`valid`: the slot holds the previous plane).
-__device__ __forceinline__ void smem_store_flag(Smem& s, int row, int col, const Prim32& w,
+template <class SM>
+__device__ __forceinline__ void smem_store_flag(SM& s, int row, int col, const Prim32& w,
                                                 bool valid) {
   s.same[row][col] = valid && same32(smem_prim(s, row, col), w);
   s.w[0][row][col] = w.r;
@@ -172,8 +206,8 @@ __device__ __forceinline__ void face_flux(const Prim32& a0, const Prim32& a1, co
 // MC: the limiter parameter is 2.  NEXT (stage 2): also the CFL speed of
 // each output cell (the next time step's), its maximum into smax_next and
 // its non-physical cells into bad_next.
-template <int STAGE, bool MC, bool NEXT>
-__device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
+template <class S, int STAGE, bool MC, bool NEXT>
+__device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
                                              double* __restrict__ U1, const fvd::Params& P,
                                              const Params32& Q, float dt, int i0, int j0,
                                              int k0, int k1, unsigned& fallbacks_out,
@@ -189,24 +223,18 @@ __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
   const int gi = min(i0 + ti, P.nx + 1), gj = min(j0 + tj, P.ny + 1);
   const bool owner = (i0 + ti < P.nx) && (j0 + tj < P.ny);
   const long long col = (long long)(gj + 2) * P.sy + (gi + 2);
-  // the halo cell this thread loads each plane (threads 0..175)
-  int hrow = 0, hcol = 0;
-  if (tid < kHalo) {
-    if (tid < 2 * PX) {
-      hrow = tid / PX - 2;
-      hcol = tid % PX - 2;
-    } else if (tid < 4 * PX) {
-      hrow = TY + (tid - 2 * PX) / PX;
-      hcol = (tid - 2 * PX) % PX - 2;
-    } else {
-      const int u = tid - 4 * PX;
-      hrow = u / 4;
-      const int c = u % 4;
-      hcol = c < 2 ? c - 2 : TX + c - 2;
-    }
+  constexpr int kThreads = S::kThreads, kHalo = S::kHalo, kHaloPer = S::kHaloPer;
+  constexpr int TY = S::TY;
+  // the halo cells this thread loads each plane (h = tid + e * kThreads)
+  int hrow[kHaloPer], hcol[kHaloPer];
+  long long hcolo[kHaloPer];
+#pragma unroll
+  for (int e = 0; e < kHaloPer; ++e) {
+    hrow[e] = hcol[e] = 0;
+    if (tid + e * kThreads < kHalo) halo_cell<S>(tid + e * kThreads, hrow[e], hcol[e]);
+    const int hgi = min(i0 + hcol[e], P.nx + 1), hgj = min(j0 + hrow[e], P.ny + 1);
+    hcolo[e] = (long long)(hgj + 2) * P.sy + (hgi + 2);
   }
-  const int hgi = min(i0 + hcol, P.nx + 1), hgj = min(j0 + hrow, P.ny + 1);
-  const long long hcolo = (long long)(hgj + 2) * P.sy + (hgi + 2);
 
   unsigned fallbacks = 0;
   const float idx = Q.inv_d[0], idy = Q.inv_d[1], idz = Q.inv_d[2];
@@ -241,11 +269,11 @@ __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
   // which of those faces this tile counts: each face of the mesh is counted
   // by one tile (face TX of a tile is face 0 of the next)
   unsigned counted = 0;
-  for (int f = tid, pass = 0; f < kXFaces; f += kThreads, ++pass) {
+  for (int f = tid, pass = 0; f < S::kXFaces; f += kThreads, ++pass) {
     const int r = f / (TX + 1), fi = f % (TX + 1);
     if (i0 + fi <= P.nx && (fi < TX || i0 + fi == P.nx) && j0 + r < P.ny) counted |= 1u << pass;
   }
-  for (int f = yface0(tid), pass = 2; f < kYFaces; f += kThreads, ++pass) {
+  for (int f = yface0<S>(tid), pass = 2; f < S::kYFaces; f += kThreads, ++pass) {
     const int fj = f / TX, c = f % TX;
     if (i0 + c < P.nx && j0 + fj <= P.ny && (fj < TY || j0 + fj == P.ny)) counted |= 1u << pass;
   }
@@ -263,10 +291,14 @@ __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
       const double* c = src + col + (long long)(t + 4) * P.sz;
 #pragma unroll
       for (int q = 0; q < NF; ++q) cp_async8(&s.col[slot][q][tid], c + q * nf);
-      if (tid < kHalo) {
-        const double* h = src + hcolo + (long long)(t + 2) * P.sz;
 #pragma unroll
-        for (int q = 0; q < NF; ++q) cp_async8(&s.halo[slot][q][tid], h + q * nf);
+      for (int e = 0; e < kHaloPer; ++e) {
+        const int h = tid + e * kThreads;
+        if (h < kHalo) {
+          const double* hp = src + hcolo[e] + (long long)(t + 2) * P.sz;
+#pragma unroll
+          for (int q = 0; q < NF; ++q) cp_async8(&s.halo[slot][q][h], hp + q * nf);
+        }
       }
     }
     cp_async_commit();
@@ -279,12 +311,9 @@ __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
     stage_in(k + kStageDepth);
     cp_async_wait<kStageDepth>();        // this iteration's group has landed
     const int slot = k % kRing;
-    double cur_col[NF], cur_halo[NF];
+    double cur_col[NF];
 #pragma unroll
-    for (int q = 0; q < NF; ++q) {
-      cur_col[q] = s.col[slot][q][tid];
-      cur_halo[q] = tid < kHalo ? s.halo[slot][q][tid] : 0.0;
-    }
+    for (int q = 0; q < NF; ++q) cur_col[q] = s.col[slot][q][tid];
     // operands of this plane's RK combine, loaded before the face work
     double rk0[NF], rk1[NF];
     const long long g = col + (long long)(k + 2) * P.sz;
@@ -327,12 +356,21 @@ __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
     // to the previous plane's in its slot (never on a chunk's first plane,
     // where the slot holds another tile's data)
     smem_store_flag(s, tj + 2, ti + 2, w0, k > k0);
-    if (tid < kHalo) smem_store_flag(s, hrow + 2, hcol + 2, prim_from_state(cur_halo, Q), k > k0);
+#pragma unroll
+    for (int e = 0; e < kHaloPer; ++e) {
+      const int h = tid + e * kThreads;
+      if (h < kHalo) {
+        double uh[NF];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) uh[q] = s.halo[slot][q][h];
+        smem_store_flag(s, hrow[e] + 2, hcol[e] + 2, prim_from_state(uh, Q), k > k0);
+      }
+    }
     __syncthreads();
     // (c) x faces: face fi (between columns fi-1 and fi) of row r.  A face
     // whose four cells all equal the previous plane's has that plane's
     // inputs, so its flux (still in s.fx) and fallback stand.
-    for (int f = tid, pass = 0; f < kXFaces; f += kThreads, ++pass) {
+    for (int f = tid, pass = 0; f < S::kXFaces; f += kThreads, ++pass) {
       const int r = f / (TX + 1), fi = f % (TX + 1);
       const bool keep = s.same[r + 2][fi] & s.same[r + 2][fi + 1] & s.same[r + 2][fi + 2] &
                         s.same[r + 2][fi + 3];
@@ -352,7 +390,7 @@ __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
       fallbacks += fb & (counted >> pass);
     }
     // (d) y faces: face fj (between rows fj-1 and fj) of column c
-    for (int f = yface0(tid), pass = 2; f < kYFaces; f += kThreads, ++pass) {
+    for (int f = yface0<S>(tid), pass = 2; f < S::kYFaces; f += kThreads, ++pass) {
       const int fj = f / TX, c = f % TX;
       const bool keep = s.same[fj][c + 2] & s.same[fj + 1][c + 2] & s.same[fj + 2][c + 2] &
                         s.same[fj + 3][c + 2];
@@ -401,18 +439,19 @@ __device__ __forceinline__ void stage32_tile(Smem& s, double* __restrict__ U,
   bad_out += bad;
 }
 
-template <int STAGE, int MINB, bool MC>
-__global__ void __launch_bounds__(kThreads, MINB)
+template <int STAGE, int TY, int MINB, bool MC>
+__global__ void __launch_bounds__(TX * TY, MINB)
 k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params32 Q, float dt,
           int kchunk, DevCounters* ctr) {
+  using S = Shape<TY>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem& s = *reinterpret_cast<Smem*>(smem_raw);
+  Smem<S>& s = *reinterpret_cast<Smem<S>*>(smem_raw);
   unsigned fallbacks = 0, evaluated = 0, smax_next = 0;
   unsigned long long bad = 0, bad_next = 0;
   const int k0 = blockIdx.z * kchunk;
-  stage32_tile<STAGE, MC, STAGE == 2>(s, U, U1, P, Q, dt, blockIdx.x * TX, blockIdx.y * TY, k0,
-                                      min(k0 + kchunk, P.nz), fallbacks, bad, evaluated,
-                                      smax_next, bad_next);
+  stage32_tile<S, STAGE, MC, STAGE == 2>(s, U, U1, P, Q, dt, blockIdx.x * TX, blockIdx.y * TY,
+                                         k0, min(k0 + kchunk, P.nz), fallbacks, bad, evaluated,
+                                         smax_next, bad_next);
   if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
   if (bad) atomicAdd(&ctr->np_step, bad);
   warp_count(&ctr->faces, evaluated);
@@ -427,13 +466,14 @@ k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params
 // (mesh, tile x, tile y, z chunk) from an atomic counter until none is left.
 // Stage 2 also folds the CFL maximum of each item's output cells into its
 // mesh's smax_bits (the next step's dt).
-template <int STAGE, int MINB, bool MC>
-__global__ void __launch_bounds__(kThreads, MINB)
+template <int STAGE, int TY, int MINB, bool MC>
+__global__ void __launch_bounds__(TX * TY, MINB)
 k_stage32_batch(double* __restrict__ U, double* __restrict__ U1, BatchMesh* __restrict__ meshes,
                 const int4* __restrict__ items, int nitems, int kchunk,
                 unsigned* __restrict__ next_item, DevCounters* ctr) {
+  using S = Shape<TY>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem& s = *reinterpret_cast<Smem*>(smem_raw);
+  Smem<S>& s = *reinterpret_cast<Smem<S>*>(smem_raw);
   __shared__ int s_item;
   unsigned fallbacks = 0, evaluated = 0;
   unsigned long long bad = 0, bad_next = 0;
@@ -447,9 +487,10 @@ k_stage32_batch(double* __restrict__ U, double* __restrict__ U1, BatchMesh* __re
     BatchMesh& m = meshes[w.x];
     const int k0 = w.w * kchunk;
     unsigned smax_next = 0;
-    stage32_tile<STAGE, MC, STAGE == 2>(s, U + m.offset, U1 + m.offset, m.P, m.Q, (float)m.dt,
-                                        w.y * TX, w.z * TY, k0, min(k0 + kchunk, m.P.nz),
-                                        fallbacks, bad, evaluated, smax_next, bad_next);
+    stage32_tile<S, STAGE, MC, STAGE == 2>(s, U + m.offset, U1 + m.offset, m.P, m.Q,
+                                           (float)m.dt, w.y * TX, w.z * TY, k0,
+                                           min(k0 + kchunk, m.P.nz), fallbacks, bad, evaluated,
+                                           smax_next, bad_next);
     if (STAGE == 2) max_speed_to(&m.smax_bits, smax_next);
   }
   if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
@@ -570,62 +611,99 @@ Params32 make_params32(const fvd::Params& P, double vacuum_ratio) {
   return Q;
 }
 
-// Launches a substep kernel with one Smem of dynamic shared memory (more than
-// the default 48 KB; prepare_kernels raised the limit).
-template <typename K, typename... A>
-static cudaError_t launch_smem(K kernel, dim3 grid, cudaStream_t s, A... args) {
-  kernel<<<grid, kThreads, sizeof(Smem), s>>>(args...);
-  return cudaGetLastError();
+// Kernel configurations: tile height TY and CTAs per SM (MINB).  Occupancy 2
+// is 16 warps per SM at up to 128 registers for every tile height; occupancy
+// 3 (24 warps, 80 registers) exists for the 32 x 8 tile.
+__host__ __device__ constexpr int minb_of(int tile_y, int occupancy) {
+  return occupancy == 2 ? 16 / tile_y : occupancy == 3 && tile_y == 8 ? 3 : 0;
 }
 
-template <typename K>
-static cudaError_t raise_smem(K kernel) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sizeof(Smem));
+// Calls fn.template run<STAGE, TY, MINB, MC>() for a configuration, or
+// returns cudaErrorInvalidValue for one that is not built.
+template <class Fn>
+static cudaError_t dispatch(int stage, int tile_y, int occupancy, bool mc, Fn& fn) {
+#define FV32_CASE(TYV, MB)                                                                  \
+  if (tile_y == TYV && minb_of(tile_y, occupancy) == MB) {                                  \
+    if (mc)                                                                                 \
+      return stage == 1 ? fn.template run<1, TYV, MB, true>() : fn.template run<2, TYV, MB, true>(); \
+    return stage == 1 ? fn.template run<1, TYV, MB, false>()                                \
+                      : fn.template run<2, TYV, MB, false>();                               \
+  }
+  FV32_CASE(4, 4)
+  FV32_CASE(8, 2)
+  FV32_CASE(8, 3)
+  FV32_CASE(16, 1)
+#undef FV32_CASE
+  return cudaErrorInvalidValue;
 }
 
-template <int STAGE, int MINB>
-static cudaError_t raise_smem_all() {
-  cudaError_t e = raise_smem(k_stage32<STAGE, MINB, true>);
-  if (e == cudaSuccess) e = raise_smem(k_stage32<STAGE, MINB, false>);
-  if (e == cudaSuccess) e = raise_smem(k_stage32_batch<STAGE, MINB, true>);
-  if (e == cudaSuccess) e = raise_smem(k_stage32_batch<STAGE, MINB, false>);
-  return e;
+struct LaunchMesh {
+  const StepBuffers& b;
+  const fvd::Params& P;
+  Params32 Q;
+  float dt;
+  int kchunk;
+  cudaStream_t s;
+  template <int STAGE, int TY, int MINB, bool MC>
+  cudaError_t run() {
+    using S = Shape<TY>;
+    const dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + kchunk - 1) / kchunk);
+    k_stage32<STAGE, TY, MINB, MC><<<grid, S::kThreads, sizeof(Smem<S>), s>>>(
+        b.U, b.U1, P, Q, dt, kchunk, b.ctr);
+    return cudaGetLastError();
+  }
+};
+
+struct LaunchBatch {
+  const BatchDevice& b;
+  int kchunk;
+  int grid_per_sm_unit;  // SMs
+  unsigned* counter;
+  cudaStream_t s;
+  template <int STAGE, int TY, int MINB, bool MC>
+  cudaError_t run() {
+    using S = Shape<TY>;
+    k_stage32_batch<STAGE, TY, MINB, MC><<<grid_per_sm_unit * MINB, S::kThreads,
+                                           sizeof(Smem<S>), s>>>(
+        b.U, b.U1, b.meshes, b.items, b.nitems, kchunk, counter, b.ctr);
+    return cudaGetLastError();
+  }
+};
+
+// Raises the dynamic shared-memory limit of both kernels of a configuration
+// (the plane buffers and staging ring take more than the default 48 KB).
+struct RaiseSmem {
+  template <int STAGE, int TY, int MINB, bool MC>
+  cudaError_t run() {
+    const int bytes = (int)sizeof(Smem<Shape<TY>>);
+    cudaError_t e = cudaFuncSetAttribute(k_stage32<STAGE, TY, MINB, MC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_stage32_batch<STAGE, TY, MINB, MC>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+  }
+};
+
+bool valid_config(int tile_y, int occupancy) {
+  return (tile_y == 4 || tile_y == 8 || tile_y == 16) && minb_of(tile_y, occupancy) > 0;
 }
 
 cudaError_t launch_stage(int stage, const StepBuffers& b, const fvd::Params& P, double dt,
-                         int kchunk, double vacuum_ratio, int occupancy, cudaStream_t s) {
-  const Params32 Q = make_params32(P, vacuum_ratio);
-  if (kchunk < 1) kchunk = 1;
-  const dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + kchunk - 1) / kchunk);
-  const float fdt = (float)dt;
-  cudaError_t e;
-  // 3 CTAs per SM: 80 registers, a few spills; 2 CTAs per SM: up to 128
-  if (Q.theta == 2.0f) {
-    if (occupancy == 3) {
-      if (stage == 1) e = launch_smem(k_stage32<1, 3, true>, grid, s, b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
-      else e = launch_smem(k_stage32<2, 3, true>, grid, s, b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
-    } else {
-      if (stage == 1) e = launch_smem(k_stage32<1, 2, true>, grid, s, b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
-      else e = launch_smem(k_stage32<2, 2, true>, grid, s, b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
-    }
-  } else {
-    if (occupancy == 3) {
-      if (stage == 1) e = launch_smem(k_stage32<1, 3, false>, grid, s, b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
-      else e = launch_smem(k_stage32<2, 3, false>, grid, s, b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
-    } else {
-      if (stage == 1) e = launch_smem(k_stage32<1, 2, false>, grid, s, b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
-      else e = launch_smem(k_stage32<2, 2, false>, grid, s, b.U, b.U1, P, Q, fdt, kchunk, b.ctr);
-    }
-  }
-  return e;
+                         int kchunk, double vacuum_ratio, int occupancy, int tile_y,
+                         cudaStream_t s) {
+  LaunchMesh fn{b, P, make_params32(P, vacuum_ratio), (float)dt, kchunk < 1 ? 1 : kchunk, s};
+  return dispatch(stage, tile_y, occupancy, fn.Q.theta == 2.0f, fn);
 }
 
 cudaError_t prepare_kernels() {
-  cudaError_t e = raise_smem_all<1, 2>();
-  if (e == cudaSuccess) e = raise_smem_all<2, 2>();
-  if (e == cudaSuccess) e = raise_smem_all<1, 3>();
-  if (e == cudaSuccess) e = raise_smem_all<2, 3>();
+  RaiseSmem fn;
+  const int cfg[4][2] = {{4, 2}, {8, 2}, {8, 3}, {16, 2}};
+  cudaError_t e = cudaSuccess;
+  for (int c = 0; c < 4 && e == cudaSuccess; ++c)
+    for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage)
+      for (int mc = 0; mc < 2 && e == cudaSuccess; ++mc)
+        e = dispatch(stage, cfg[c][0], cfg[c][1], mc != 0, fn);
   return e;
 }
 
@@ -656,34 +734,12 @@ cudaError_t launch_batch_dt(const BatchDevice& b, double cfl, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <bool MC>
-static cudaError_t batch_stage(int stage, const BatchDevice& b, int kchunk, int occupancy,
-                               int grid, unsigned* counter, cudaStream_t s) {
-  if (occupancy == 3) {
-    if (stage == 1)
-      return launch_smem(k_stage32_batch<1, 3, MC>, grid, s, b.U, b.U1, b.meshes, b.items,
-                         b.nitems, kchunk, counter, b.ctr);
-    else
-      return launch_smem(k_stage32_batch<2, 3, MC>, grid, s, b.U, b.U1, b.meshes, b.items,
-                         b.nitems, kchunk, counter, b.ctr);
-  } else {
-    if (stage == 1)
-      return launch_smem(k_stage32_batch<1, 2, MC>, grid, s, b.U, b.U1, b.meshes, b.items,
-                         b.nitems, kchunk, counter, b.ctr);
-    else
-      return launch_smem(k_stage32_batch<2, 2, MC>, grid, s, b.U, b.U1, b.meshes, b.items,
-                         b.nitems, kchunk, counter, b.ctr);
-  }
-}
-
 // The MC form when every mesh of the batch has limiter parameter 2, else the
 // general form for all (same results as each mesh's single-mesh kernel).
 cudaError_t launch_batch_stage(int stage, const BatchDevice& b, int kchunk, int occupancy,
-                               int num_sms, cudaStream_t s) {
-  const int grid = num_sms * (occupancy == 3 ? 3 : 2);
-  unsigned* counter = b.next_item + (stage == 1 ? 0 : 1);
-  return b.all_mc ? batch_stage<true>(stage, b, kchunk, occupancy, grid, counter, s)
-                  : batch_stage<false>(stage, b, kchunk, occupancy, grid, counter, s);
+                               int tile_y, int num_sms, cudaStream_t s) {
+  LaunchBatch fn{b, kchunk, num_sms, b.next_item + (stage == 1 ? 0 : 1), s};
+  return dispatch(stage, tile_y, occupancy, b.all_mc, fn);
 }
 
 cudaError_t launch_batch_ghosts(int stage, const BatchDevice& b, cudaStream_t s) {

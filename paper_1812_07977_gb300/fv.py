@@ -91,8 +91,9 @@ def load_library(path: str | None = None):
         "fv_batch_get_state": ([vp, i, vp, i], i),
         "fv_batch_step": ([vp, d, i], i),
         "fv_batch_get_dt": ([vp, dp], i),
-        "fv_batch_set_tuning": ([vp, i, i], i),
-        "fv_batch_autotune": ([vp, d, ctypes.POINTER(i), ctypes.POINTER(i), dp], i),
+        "fv_batch_set_tuning": ([vp, i, i, i], i),
+        "fv_batch_autotune": ([vp, d, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                               dp], i),
         "fv_batch_get_counters": ([vp, ctypes.POINTER(ctypes.c_longlong),
                                    ctypes.POINTER(ctypes.c_longlong)], i),
         "fv_batch_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong),
@@ -265,7 +266,8 @@ class Mesh:
         return a.value, b.value
 
     def set_tuning(self, key: str, value):
-        keys = {"kchunk": 0, "vacuum_ratio": 1, "occupancy": 2, "sweep_segments": 3}
+        keys = {"kchunk": 0, "vacuum_ratio": 1, "occupancy": 2, "sweep_segments": 3,
+                "tile_y": 4}
         _check(self._lib.fv_set_tuning(self._h, keys[key], float(value)), "fv_set_tuning")
 
     def profile(self, on: bool = True):
@@ -391,16 +393,17 @@ class Batch:
         _check(self._lib.fv_batch_get_dt(self._h, out), "fv_batch_get_dt")
         return np.array(out[:])
 
-    def set_tuning(self, kchunk, occupancy):
-        _check(self._lib.fv_batch_set_tuning(self._h, int(kchunk), int(occupancy)),
+    def set_tuning(self, kchunk, occupancy=2, tile_y=8):
+        _check(self._lib.fv_batch_set_tuning(self._h, int(kchunk), int(occupancy), int(tile_y)),
                "fv_batch_set_tuning")
 
     def autotune(self, cfl=0.4):
-        kc, occ, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        """(kchunk, occupancy, tile_y, ms per step) of the fastest configuration."""
+        kc, occ, ty, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         _check(self._lib.fv_batch_autotune(self._h, float(cfl), ctypes.byref(kc),
-                                           ctypes.byref(occ), ctypes.byref(ms)),
+                                           ctypes.byref(occ), ctypes.byref(ty), ctypes.byref(ms)),
                "fv_batch_autotune")
-        return kc.value, occ.value, ms.value
+        return kc.value, occ.value, ty.value, ms.value
 
     def counters(self):
         a, b = ctypes.c_longlong(), ctypes.c_longlong()

@@ -58,13 +58,14 @@ def test_batch_equals_single_meshes_bitwise(use_graph):
             assert np.array_equal(got, ref[m]), m
 
 
-@pytest.mark.parametrize("kchunk,occ", [(8, 2), (5, 3), (64, 2)])
-def test_batch_result_independent_of_tuning(kchunk, occ):
+@pytest.mark.parametrize("kchunk,occ,tile_y", [(8, 2, 8), (5, 3, 8), (64, 2, 8), (7, 2, 4),
+                                                (16, 2, 16), (3, 2, 16)])
+def test_batch_result_independent_of_tuning(kchunk, occ, tile_y):
     from paper_1812_07977_gb300.fv import Batch
     spec = _small_batch(count=5, seed=11)
     ref = _single_runs(spec, 3)
     with Batch([s["shape"] for s in spec]) as b:
-        b.set_tuning(kchunk, occ)
+        b.set_tuning(kchunk, occ, tile_y)
         for m, s in enumerate(spec):
             b.set_state(m, s["U0"])
         for _ in range(3):
@@ -134,8 +135,9 @@ def test_autotune_restores_state_and_picks_a_candidate():
     with Batch([s["shape"] for s in spec]) as b:
         for m, s in enumerate(spec):
             b.set_state(m, s["U0"])
-        kc, occ, ms = b.autotune(0.4)
-        assert kc in (8, 16, 32, 64) and occ in (2, 3) and ms > 0
+        kc, occ, ty, ms = b.autotune(0.4)
+        assert kc in (8, 16, 32, 64) and (ty, occ) in ((4, 2), (8, 2), (8, 3), (16, 2))
+        assert ms > 0
         for m, s in enumerate(spec):
             assert np.array_equal(b.get_state(m).cpu().numpy(), s["U0"])
         assert b.counters() == (0, 0)
@@ -169,5 +171,9 @@ def test_batch_rejects_bad_arguments():
             b.set_tuning(0, 2)
         with pytest.raises(FvError):
             b.set_tuning(8, 4)
+        with pytest.raises(FvError):
+            b.set_tuning(8, 2, 12)
+        with pytest.raises(FvError):
+            b.set_tuning(8, 3, 16)
         with pytest.raises(FvError):
             b.step(-1.0)

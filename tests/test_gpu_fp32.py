@@ -173,6 +173,29 @@ def test_stage2_cfl_maximum_same_dt(theta):
     m.close()
 
 
+@pytest.mark.parametrize("tile_y", [4, 16])
+def test_tile_shapes_same_bits(tile_y):
+    """The fused kernel built for 32 x 4 and 32 x 16 tiles (128 / 512
+    threads; the 32 x 4 tile has more halo cells than threads) gives the
+    32 x 8 tile's bits, dt and counts, on a ragged mesh with z chunks."""
+    n = (45, 38, 33)
+    out = []
+    for ty in (8, tile_y):
+        m = _mesh32(n)
+        m.set_tuning("tile_y", ty)
+        m.set_tuning("kchunk", 7)
+        m.set_state(problems.riemann_oblique(*n))
+        dts = []
+        for _ in range(4):
+            dts.append(m.reduce_dt(0.4))
+            m.step(dts[-1])
+        out.append((dts, m.get_state().cpu().numpy(), m.counters()))
+        m.close()
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1].view(np.uint64), out[1][1].view(np.uint64))
+    assert out[0][2] == out[1][2]
+
+
 def test_conservation_periodic():
     n = (20, 16, 24)
     U0 = problems.random_smooth_periodic(*n, seed=99)
