@@ -2,23 +2,26 @@
 //
 // One kernel per substep does all of Algorithm 1's substep kernels
 // (ComputeDifferences, ComputeReconstruction, RiemannSolverInput,
-// ComputeFluxes, ComputeUpdate and the RK combine) for a tile of 32 x 8
-// columns marching along z over a chunk of planes, so each substep reads
-// its input state once (plus the tile's two-cell halo) and writes its output
-// once: 120-200 B of FP64 state traffic per zone-update instead of the
-// ~1 KB of the FP64 path's separate sweeps.
+// ComputeFluxes, ComputeUpdate and the RK combine) for a tile of 32 x TY
+// columns (TY = 4, 8 or 16) marching along z over a chunk of planes, so each
+// substep reads its input state once (plus the tile's two-cell halo) and
+// writes its output once: 120-200 B of FP64 state traffic per zone-update
+// instead of the ~1 KB of the FP64 path's separate sweeps.
 //
-// Per plane k, each thread owns one column (i, j) of the tile:
+// Per plane k, each thread owns one column (i, j) of the tile; the FP64
+// input of the next plane is staged into shared memory by cp.async while
+// the current one is computed:
 //   z  : a register window along its column (primitives of planes k..k+2,
 //        the z differences and half slopes of planes k, k+1, and the z
 //        flux of face k-1/2 carried from the previous plane) gives the z
 //        flux of face k+1/2 -- every z flux computed once;
 //   x,y: the plane's primitives (tile plus two-cell halo) go to shared
-//        memory; the 33 x 8 x-faces and 32 x 9 y-faces are computed once
-//        each (slopes of both neighbours recomputed per face) into shared
-//        memory;
+//        memory; the 33 x TY x-faces and 32 x (TY+1) y-faces are computed
+//        once each (slopes of both neighbours recomputed per face) into
+//        shared memory;
 //   update: dU = dt * (-(Fx(i+1/2)-Fx(i-1/2))/dx - (..)/dy - (..)/dz) in FP32,
-//        then the RK combine in FP64 on the FP64 state.
+//        then the RK combine in FP64 on the FP64 state; stage 2 also takes
+//        the CFL speed of the cell it writes (the next step's time step).
 // Flux reuse (bit for bit what evaluating gives): a z face whose column has
 // five equal cells around it takes the previous z flux; an x or y face whose
 // four cells all equal those one plane below keeps that plane's flux (each
