@@ -196,6 +196,31 @@ def test_tile_shapes_same_bits(tile_y):
     assert out[0][2] == out[1][2]
 
 
+@pytest.mark.parametrize("n,bc", [((45, 38, 33), (OUT, OUT, OUT)), ((45, 38, 33), (PER, PER, PER)),
+                                  ((3, 1, 2), (OUT, PER, OUT)), ((2, 5, 1), (PER, OUT, PER)),
+                                  ((1, 1, 1), (OUT, OUT, OUT)), ((1, 2, 3), (PER, PER, PER))])
+def test_ghosts_filled_after_each_substep(n, bc):
+    """After each substep the ghost cells of its output hold their source
+    cells: the ghosted state is unchanged by another ghost fill (outflow,
+    periodic and axes of 1-3 cells)."""
+    m = _mesh32(n, bc=bc)
+    U0 = (problems.random_smooth_periodic(*n, seed=4) if PER in bc
+          else problems.riemann_oblique(*n))
+    m.set_state(U0)
+    for _ in range(2):
+        m.step(m.reduce_dt(0.4))
+    a = m.get_ghosted_state().cpu().numpy()
+    m.fill_ghosts()
+    b = m.get_ghosted_state().cpu().numpy()
+    assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+    m.substep(1, 1e-4)                 # the stage-1 output (U1) as well
+    a = m.get_ghosted_state().cpu().numpy()
+    m.fill_ghosts()
+    b = m.get_ghosted_state().cpu().numpy()
+    assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+    m.close()
+
+
 def test_conservation_periodic():
     n = (20, 16, 24)
     U0 = problems.random_smooth_periodic(*n, seed=99)
