@@ -299,6 +299,16 @@ class Mesh:
             n += 1
         return t, n, dts
 
+    # short names: set(U), dt(cfl), step(dt), get()
+    def set(self, U):
+        self.set_state(U)
+
+    def get(self, out=None):
+        return self.get_state(out)
+
+    def dt(self, cfl: float) -> float:
+        return self.reduce_dt(cfl)
+
 
 def conserved_sums_noalloc(U, lx=1.0, ly=1.0, lz=1.0, stream=None):
     """Conservation sums of a caller-held (5, nz, ny, nx) float64 CUDA tensor

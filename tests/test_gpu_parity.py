@@ -436,6 +436,30 @@ def test_primitives_from_the_dt_pass_same_bits(precision):
     assert runs[0][2] == runs[1][2]
 
 
+def test_driver_loop_with_short_names():
+    """Algorithm 1's loop through the wrapper's short names (set, dt, step,
+    get) with dt clamped to the end time, against the oracle's loop: the same
+    dts and state bits."""
+    from paper_1812_07977_gb300.fv import Mesh
+    n = (20, 6, 5)
+    U0 = problems.riemann_planar(*n)
+    om = oracle.mesh(*n)
+    Uo = oracle.ghosted_from_interior(om, U0)
+    T = 0.05
+    with Mesh(*n) as m:
+        m.set(U0)
+        t = 0.0
+        while t < T:
+            dt = min(m.dt(0.4), T - t)
+            dto = min(oracle.reduce_dt(om, Uo, 0.4)[0], T - t)
+            assert dt == dto
+            m.step(dt)
+            oracle.step(om, Uo, dto)
+            t += dt
+        got = m.get().cpu().numpy()
+    assert np.array_equal(got, oracle.interior(Uo))
+
+
 def test_host_buffers_match_device_buffers():
     n = (16, 12, 10)
     U0 = problems.riemann_oblique(*n)
