@@ -179,6 +179,7 @@ void free_mesh(fv_mesh_s* m) {
   cudaFree(m->buf.U);
   cudaFree(m->buf.U1);
   cudaFree(m->buf.W);
+  cudaFree(m->buf.keep);
   cudaFree(m->buf.ACC);
   cudaFree(m->buf.ctr);
   cudaFree(m->sums_work);
@@ -270,8 +271,11 @@ cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
   // the dt pass since the state last changed left U's primitives in W
   if (!(stage == 1 && m->w_current)) {
     e = timed(m, FV_KERNEL_PRIM, 1, [&] {
-      return fma ? fv_fp64_fma::launch_prim(src, m->buf, m->P, m->stream)
-                 : fv_fp64_exact::launch_prim(src, m->buf, m->P, m->stream);
+      // substep 2: W holds U's primitives, and the cells substep 1 copied
+      // unchanged keep them
+      const bool keep = stage == 2;
+      return fma ? fv_fp64_fma::launch_prim(src, m->buf, m->P, keep, m->stream)
+                 : fv_fp64_exact::launch_prim(src, m->buf, m->P, keep, m->stream);
     });
   }
   m->w_current = false;
@@ -334,6 +338,8 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   if ((e = cudaMalloc(&m->buf.U, sb)) != cudaSuccess ||
       (e = cudaMalloc(&m->buf.U1, sb)) != cudaSuccess ||
       (desc->precision != FV_PREC_FP32_BULK && (e = cudaMalloc(&m->buf.W, sb)) != cudaSuccess) ||
+      (desc->precision != FV_PREC_FP32_BULK &&
+       (e = cudaMalloc(&m->buf.keep, m->dense_doubles / fvd::NF)) != cudaSuccess) ||
       (e = cudaMalloc(&m->buf.ACC, db)) != cudaSuccess ||
       (e = cudaMalloc(&m->buf.ctr, sizeof(DevCounters))) != cudaSuccess ||
       (e = cudaMalloc(&m->sums_work, wb)) != cudaSuccess ||

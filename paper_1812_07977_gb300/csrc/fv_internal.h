@@ -32,6 +32,7 @@ struct StepBuffers {
   double* U1;     // first RK stage, ghosted, 5 fields
   double* W;      // primitives of the stage's input state, ghosted, 5 fields
   double* ACC;    // flux-divergence accumulator, dense interior, 5 fields
+  unsigned char* keep;  // per interior cell: substep 1 copied U to U1 unchanged (dense)
   DevCounters* ctr;
 };
 
@@ -41,13 +42,15 @@ struct StepBuffers {
 // axis 0, 1, 2; the z sweep (axis 2) applies the RK combine of `stage`.
 // `segments`: pieces each grid line of a sweep is cut into (0: chosen from
 // the mesh size and `num_sms`, the device's multiprocessor count).
+// launch_prim with keep (substep 2): W holds U's primitives and b.keep the
+// cells substep 1 left unchanged; only the other cells are converted.
 // launch_prim_dt: the CFL maximum of U into ctr->smax_bits and, in the same
 // pass, U's primitives into b.W, which a following substep 1 may use in
 // place of its launch_prim.
 #define FV_DECLARE_STEP_VARIANT(ns)                                                        \
   namespace ns {                                                                           \
   cudaError_t launch_prim(const double* src, const StepBuffers& b, const fvd::Params& P,   \
-                          cudaStream_t s);                                                 \
+                          bool keep, cudaStream_t s);                                      \
   cudaError_t launch_sweep(int axis, int stage, const StepBuffers& b, const fvd::Params& P, \
                            double dt, int segments, int num_sms, cudaStream_t s);          \
   cudaError_t launch_prim_dt(const double* U, const StepBuffers& b, const fvd::Params& P,  \

@@ -39,36 +39,67 @@ constexpr int kSweepMinBlocks = 8;   // 16 warps per SM: at most 128 registers
 
 // A cell equal bit for bit to the thread's previous cell has its primitives;
 // when the whole warp has such cells (uniform regions), it reuses them.
+// KEEP (substep 2): W holds the primitives of U, and keep[] marks the
+// interior cells whose substep 1 copied U to U1 unchanged; such a cell, and
+// every ghost cell filled from it, already has its primitives in W and is
+// neither read nor written.
+template <bool KEEP>
 __global__ void __launch_bounds__(kPrimThreads)
-k_prim(const double* __restrict__ U, double* __restrict__ W, Params P, DevCounters* ctr) {
+k_prim(const double* __restrict__ U, double* __restrict__ W, Params P,
+       const unsigned char* __restrict__ keep, DevCounters* ctr) {
   const long long nf = P.nfield;
+  const int X = P.nx + 4, Y = P.ny + 4;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  // (i, j, k) of cell c in the ghosted array, advanced by increments
+  int k = (int)(c / P.sz);
+  int j = (int)((c - (long long)k * P.sz) / X);
+  int i = (int)(c - (long long)k * P.sz - (long long)j * X);
+  const int sk = (int)(stride / P.sz);
+  const int sj = (int)((stride - (long long)sk * P.sz) / X);
+  const int si = (int)(stride - (long long)sk * P.sz - (long long)sj * X);
   double up[NF] = {0.0, 0.0, 0.0, 0.0, 0.0};
   Prim w = Prim{0.0, 0.0, 0.0, 0.0, 0.0};
   bool have = false;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nf;
-       c += (long long)gridDim.x * blockDim.x) {
+  for (; c < nf; c += stride) {
+    bool skip = false;
+    if (KEEP) {
+      const int ci = ghost_source(i - 2, P.nx, P.bc[0]);
+      const int cj = ghost_source(j - 2, P.ny, P.bc[1]);
+      const int ck = ghost_source(k - 2, P.nz, P.bc[2]);
+      skip = keep[((long long)ck * P.ny + cj) * P.nx + ci] != 0;
+    }
     double u[NF];
     bool eq = have;
 #pragma unroll
     for (int q = 0; q < NF; ++q) {
-      u[q] = U[q * nf + c];
+      u[q] = skip ? up[q] : U[q * nf + c];
       eq = eq && bits(u[q]) == bits(up[q]);
       up[q] = u[q];
     }
-    have = true;
+    eq = eq || skip;
+    have = have || !skip;
     if (!__all_sync(__activemask(), eq)) w = cons_to_prim(u, P);
-    W[c] = w.r;
-    W[nf + c] = w.vx;
-    W[2 * nf + c] = w.vy;
-    W[3 * nf + c] = w.vz;
-    W[4 * nf + c] = w.p;
-    if (!(is_pos(w.r) && is_pos(w.p))) {
-      long long k = c / P.sz;
-      long long rem = c - k * P.sz;
-      long long j = rem / P.sy;
-      long long i = rem - j * P.sy;
-      if (i >= 2 && i < P.nx + 2 && j >= 2 && j < P.ny + 2 && k >= 2 && k < P.nz + 2)
+    if (!skip) {
+      W[c] = w.r;
+      W[nf + c] = w.vx;
+      W[2 * nf + c] = w.vy;
+      W[3 * nf + c] = w.vz;
+      W[4 * nf + c] = w.p;
+      if (!(is_pos(w.r) && is_pos(w.p)) && i >= 2 && i < P.nx + 2 && j >= 2 &&
+          j < P.ny + 2 && k >= 2 && k < P.nz + 2)
         atomicAdd(&ctr->np_step, 1ULL);
+    }
+    i += si;
+    j += sj;
+    k += sk;
+    if (i >= X) {
+      i -= X;
+      ++j;
+    }
+    if (j >= Y) {
+      j -= Y;
+      ++k;
     }
   }
 }
@@ -124,7 +155,8 @@ __device__ __forceinline__ void rk_combine(double* __restrict__ U, double* __res
 template <int AXIS, int STAGE, int TK>
 __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks)
 k_sweep(const double* __restrict__ W, double* __restrict__ ACC, double* __restrict__ U,
-        double* __restrict__ U1, Params P, double dt, int seg, DevCounters* ctr) {
+        double* __restrict__ U1, Params P, double dt, int seg, unsigned char* __restrict__ keep,
+        DevCounters* ctr) {
   const int n_line = AXIS == 0 ? P.nx : AXIS == 1 ? P.ny : P.nz;
   const int na = AXIS == 0 ? P.ny : P.nx;
   const int nb = AXIS == 2 ? P.ny : P.nz;
@@ -227,15 +259,18 @@ k_sweep(const double* __restrict__ W, double* __restrict__ ACC, double* __restri
             neg_zero = neg_zero && is_neg_zero(acc[q]);
           }
           const long long gc0 = g0 + (long long)(f - 1) * gs;
+          // (stage 1 marks the copied cells for the primitives of substep 2)
           if (__all_sync(__activemask(), neg_zero)) {
 #pragma unroll
             for (int q = 0; q < NF; ++q) {
               if (STAGE == 1) U1[q * nf + gc0] = U[q * nf + gc0];
               else U[q * nf + gc0] = half(U[q * nf + gc0] + U1[q * nf + gc0]);
             }
+            if (STAGE == 1) keep[dc] = 1;
           } else {
 #pragma unroll
             for (int q = 0; q < NF; ++q) rk_combine<STAGE>(U, U1, q * nf + gc0, dt * acc[q]);
+            if (STAGE == 1) keep[dc] = 0;
           }
         }
       } else {
@@ -251,6 +286,7 @@ k_sweep(const double* __restrict__ W, double* __restrict__ ACC, double* __restri
             rk_combine<STAGE>(U, U1, q * nf + g0 + (long long)(f - 1) * gs, dt * acc);
           }
         }
+        if (AXIS == 2 && STAGE == 1) keep[dc] = 0;
       }
     }
 #pragma unroll
@@ -425,11 +461,14 @@ cudaError_t launch_prim_dt(const double* U, const StepBuffers& b, const Params& 
   return cudaGetLastError();
 }
 
-cudaError_t launch_prim(const double* src, const StepBuffers& b, const Params& P,
+cudaError_t launch_prim(const double* src, const StepBuffers& b, const Params& P, bool keep,
                         cudaStream_t s) {
   long long blocks = (P.nfield + kPrimThreads - 1) / kPrimThreads;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_prim<<<(unsigned)blocks, kPrimThreads, 0, s>>>(src, b.W, P, b.ctr);
+  if (keep)
+    k_prim<true><<<(unsigned)blocks, kPrimThreads, 0, s>>>(src, b.W, P, b.keep, b.ctr);
+  else
+    k_prim<false><<<(unsigned)blocks, kPrimThreads, 0, s>>>(src, b.W, P, nullptr, b.ctr);
   return cudaGetLastError();
 }
 
@@ -459,13 +498,13 @@ static cudaError_t sweep_tk(int axis, int stage, const StepBuffers& b, const Par
   const dim3 g((unsigned)((lines + kSweepThreads - 1) / kSweepThreads),
                (unsigned)((n + seg - 1) / seg));
   if (axis == 0)
-    k_sweep<0, 0, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, seg, b.ctr);
+    k_sweep<0, 0, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, seg, b.keep, b.ctr);
   else if (axis == 1)
-    k_sweep<1, 0, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, seg, b.ctr);
+    k_sweep<1, 0, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, seg, b.keep, b.ctr);
   else if (stage == 1)
-    k_sweep<2, 1, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, seg, b.ctr);
+    k_sweep<2, 1, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, seg, b.keep, b.ctr);
   else
-    k_sweep<2, 2, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, seg, b.ctr);
+    k_sweep<2, 2, TK><<<g, kSweepThreads, 0, s>>>(b.W, b.ACC, b.U, b.U1, P, dt, seg, b.keep, b.ctr);
   return cudaGetLastError();
 }
 
