@@ -59,9 +59,10 @@ FLOPS_DT = 23            # per interior cell
 # writes U^{n+1} (120 B).
 BYTES_PER_ZONE_UPDATE = 200
 # DRAM bytes (read + write) per sweep launch, mean of the x, y and z sweeps of
-# the FP64-FMA build at 256^3 (lines in 10 segments) from one ncu capture
+# the FP64-FMA build at 256^3 (lines in 10 segments, stage-1 z sweep with its
+# unchanged-cell flags) from one ncu capture
 # (profiles/k_sweep_fp64_fma_oblique256.md); None for builds not captured.
-SWEEP_TRAFFIC = {"fp64_fma": 2.22e9}
+SWEEP_TRAFFIC = {"fp64_fma": 2.23e9}
 # The same for the fused FP32-bulk substep kernel (mean of stage 1 and 2, 32 x 8
 # tiles, staging ring, stage 2 with the next step's CFL maximum;
 # profiles/k_stage32_fp32_oblique256.md).
