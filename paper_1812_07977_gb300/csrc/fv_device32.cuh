@@ -80,7 +80,7 @@ __device__ __forceinline__ double f2d(float f) {
 }
 
 // Approximate reciprocal (one MUFU.RCP, within 2 ulp): the FP32-bulk
-// arithmetic is judged by its error against FP64, not bit for bit.
+// arithmetic is held to an error bound against FP64, not bit for bit.
 __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
 
 struct Prim32 { float r, vx, vy, vz, p; };

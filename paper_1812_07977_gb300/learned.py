@@ -10,7 +10,7 @@ correction dU matches r.  Evaluation runs the coarse solver with and without
 the correction on a held-out perturbation amplitude, on the same time steps
 as a fine reference run, and reports the L1 density error of each: the plain
 solver is both the fallback (a corrected step that produces a non-physical
-cell is redone without the correction) and the judge of the gain.
+cell is redone without the correction) and the arbiter of the gain.
 
 Tensor reshaping and averaging here are data preparation on the GPU (torch);
 the solver steps and every network pass run in the library's kernels.
@@ -178,7 +178,7 @@ def train(net: Net, data, epochs: int, lr: float, gamma: float = 1.4, seed: int 
           denoise: bool = False):
     """Adam over the samples for `epochs` epochs.  With a validation
     reference run `val`, the parameters of the epoch with the lowest mean
-    validation rollout error are kept (model selection by the judge).
+    validation rollout error are kept (model selection against the plain solver).
 
     With `noise` > 0 each sample's input is perturbed by Gaussian noise of
     `noise` times each conserved field's standard deviation while the target
@@ -248,7 +248,7 @@ def run(fine_n=256, factor=4, train_amps=(0.01, 0.04, 0.07, 0.1), val_amp=0.085,
     """The whole workflow: data from fine runs, training with model selection
     on a validation amplitude, evaluation on a held-out test amplitude.  If no
     epoch's correction beats the plain solver on the validation run, the
-    judge keeps the plain solver (use_learned False).  Returns a summary."""
+    plain solver is kept (use_learned False).  Returns a summary."""
     t0 = time.perf_counter()
     data, fine_steps = generate(fine_n, factor, train_amps, samples, every=every, rollout=rollout)
     val = reference_run(fine_n, factor, val_amp, val_steps)

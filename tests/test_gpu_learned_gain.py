@@ -2,7 +2,7 @@
 shear layers, block-averaged 4x, train the network on the GPU with the
 library's own kernels; on a held-out perturbation amplitude the corrected
 coarse (16^3) run must follow the averaged fine run much more closely than
-the plain coarse run (the judge of the gain), with no fallback needed."""
+the plain coarse run (the arbiter of the gain), with no fallback needed."""
 import numpy as np
 import pytest
 
@@ -37,7 +37,7 @@ def test_trained_correction_gains_at_the_configured_workload():
     mesh, 32-step rollouts.  Without noise injection the corrected run
     drifts past the plain one over 32 steps; with training-input noise of
     half a standard deviation the correction must cut the mean L1 density
-    error at least 3x on the held-out amplitude and be kept by the judge."""
+    error at least 3x on the held-out amplitude and be kept over the plain solver."""
     from paper_1812_07977_gb300 import learned
     r = learned.run(fine_n=256, factor=4, train_amps=(0.01, 0.04, 0.07, 0.1), val_amp=0.085,
                     test_amp=0.055, samples=16, every=2, epochs=16, lr=1e-3, eval_steps=32,
