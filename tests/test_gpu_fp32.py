@@ -1,5 +1,5 @@
 """FP32-bulk path (FV_PREC_FP32_BULK): FP32 reconstruction and fluxes on an
-FP64 state.  It is not bitwise, so it is held to its error against the FP64
+FP64 state.  It is not bitwise, so it is checked by its error against the FP64
 oracle on the same seeded inputs, per field, and by the invariants that stay
 exact in any precision: uniform states, zero transverse momentum of a planar
 problem, identical lines of a planar problem, round-off conservation.
