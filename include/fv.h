@@ -184,8 +184,8 @@ FV_API fv_status fv_get_counters(fv_mesh_t m, long long* nonphysical_cells,
  * the flux, of the face before it; the FP64 sweeps then reuse that flux
  * (same bits as evaluating it).  They also evaluate the first face of every
  * line segment after the first twice (FV_TUNE_SWEEP_SEGMENTS), so for states
- * without equal neighbours evaluated = defined + 2 x (extra segments x lines)
- * per step.  The fused
+ * without equal neighbours each step evaluates the defined faces plus, for
+ * each axis, (segments - 1) x (lines along it) faces per substep.  The fused
  * FP32-bulk kernel reuses z fluxes the same way and x / y fluxes whose four
  * cells equal those one plane below; it evaluates the faces on tile and
  * z-chunk edges in both neighbouring tiles, so for states without equal
