@@ -117,27 +117,35 @@ class ClockSampler:
         time.sleep(0.3)
         self.proc.terminate()
         self.proc.wait()
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) == 8:
-                rows.append(parts)
+        with open(self.path) as f:
+            lines = f.readlines()
         os.unlink(self.path)
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = set()
-        sm, smax = [], None
-        for r in rows:
-            try:
-                sm.append(float(r[0]))
-                smax = float(r[1])
-            except ValueError:
-                continue
-            for k, name in enumerate(names):
-                if r[4 + k].lower() == "active":
-                    reasons.add(name)
-        loaded = [s for s in sm if smax and s > 0.5 * smax] or sm
-        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": smax,
-                "samples": len(sm), "reasons": sorted(reasons)}
+        return summarize_clocks(lines)
+
+
+def summarize_clocks(lines):
+    """Median SM clock under load (samples above half the maximum), the
+    maximum clock and the throttle reasons seen Active, from nvidia-smi's
+    `ClockSampler.FIELDS` rows (csv, no header, no units)."""
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = set()
+    sm, smax = [], None
+    for line in lines:
+        r = [p.strip() for p in line.split(",")]
+        if len(r) != 8:
+            continue
+        try:
+            clock, top = float(r[0]), float(r[1])
+        except ValueError:
+            continue
+        sm.append(clock)
+        smax = top
+        for k, name in enumerate(names):
+            if r[4 + k].lower() == "active":
+                reasons.add(name)
+    loaded = [s for s in sm if smax and s > 0.5 * smax] or sm
+    return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": smax,
+            "samples": len(sm), "reasons": sorted(reasons)}
 
 
 def _dist():
