@@ -67,25 +67,25 @@ typedef enum { FV_BC_OUTFLOW = 0, FV_BC_PERIODIC = 1 } fv_bc;
  *  FV_PREC_FP64      FP64, every operation rounded separately in the order
  *                    of the method's definition (no fused multiply-add):
  *                    bitwise reproducible against a plain IEEE FP64 code.
+ *  FV_PREC_FP32_BULK FP64 state, FP32 bulk arithmetic: reconstruction, wave
+ *                    speeds, HLL fluxes and the flux divergence in FP32 (one
+ *                    fused kernel per substep); the RK combine adds the FP32
+ *                    update to the FP64 state in FP64; the pressure of cells
+ *                    whose kinetic energy exceeds 99% of E is recovered in
+ *                    FP64; the CFL time step is FP64 (FP32 speeds serve only
+ *                    as upper bounds that skip cells which cannot raise the
+ *                    maximum); conservation sums as FV_PREC_FP64.
  *  FV_PREC_FP64_FMA  FP64 with fused multiply-add contraction, and each
  *                    divide and square root (sound speeds, HLL weights, 1/rho)
  *                    as an FP32 seed refined by two Newton-Raphson steps in
  *                    FP64: the same method, a few ulp per operation away from
  *                    FV_PREC_FP64 (held to 1e-12 relative of each field).
- *  Both FP64 forms evaluate a face's flux once and reuse it, bit for bit, for
- *  the next face of a grid line when the cells around both are equal (see
- *  fv_get_face_counts).
+ *  The values 0 and 1 are those of the boundary's original two-value enum;
+ *  the FMA build was added after them.  Both FP64 forms evaluate a face's
+ *  flux once and reuse it, bit for bit, for the next face of a grid line
+ *  when the cells around both are equal (see fv_get_face_counts).
  */
-/*  FV_PREC_FP32_BULK FP64 state, FP32 bulk arithmetic: reconstruction, wave
- *                    speeds, HLL fluxes and the flux divergence in FP32 (one
- *                    fused kernel per substep); the RK combine adds the FP32
- *                    update to the FP64 state in FP64; the pressure of cells
- *                    whose kinetic energy exceeds 99% of E is recovered in
- *                    FP64; the CFL maximum is exact and dt = cfl / max is
- *                    formed in FP64 (per-cell signal speeds in FP32);
- *                    conservation sums as FV_PREC_FP64.
- */
-typedef enum { FV_PREC_FP64 = 0, FV_PREC_FP64_FMA = 1, FV_PREC_FP32_BULK = 2 } fv_precision;
+typedef enum { FV_PREC_FP64 = 0, FV_PREC_FP32_BULK = 1, FV_PREC_FP64_FMA = 2 } fv_precision;
 
 typedef struct {
   int nx, ny, nz;       /* interior cells per axis, each >= 1 */
@@ -324,6 +324,32 @@ FV_API fv_status fv_net_train_step(fv_net_t n, fv_mesh_t m, const double* residu
  * U += dU(phi) on the interior and a ghost fill.  Asynchronous. */
 FV_API fv_status fv_step_learned(fv_mesh_t m, fv_net_t n, double dt);
 
+/* The network's intermediate values from its last forward pass
+ * (fv_net_forward, fv_net_train_step, fv_step_learned) or, for the
+ * gradients, its last training step, for inspection and testing.  Cells are
+ * numbered c = (k*ny + j)*nx + i over the mesh the pass ran on.
+ *  FV_NET_BUF_FEATURES  x = (W - in_mean)/in_scale: BF16 [c][8] (5 channels,
+ *                       3 zero pads)
+ *  FV_NET_BUF_H1, _H2   tanh outputs of layers 1 and 2: BF16 [c][32]
+ *  FV_NET_BUF_OUT       network output o (phi = out_scale o): FP32 [5][c]
+ *  FV_NET_BUF_GRAD_OUT  dL/do: FP32 [5][c]
+ *  FV_NET_BUF_GRAD_A2, _A1  dL/d(pre-activation) of layers 2 and 1 (after
+ *                       the tanh backward): FP32 [c][32]
+ * `dst` is a device pointer on the network's device with room for exactly
+ * `bytes` bytes, which must equal the buffer's size.  Synchronising.
+ * Errors: INVALID_ARG (unknown buffer, size mismatch, NULL dst, no pass has
+ * produced it yet), CUDA. */
+typedef enum {
+  FV_NET_BUF_FEATURES = 0,
+  FV_NET_BUF_H1 = 1,
+  FV_NET_BUF_H2 = 2,
+  FV_NET_BUF_OUT = 3,
+  FV_NET_BUF_GRAD_OUT = 4,
+  FV_NET_BUF_GRAD_A2 = 5,
+  FV_NET_BUF_GRAD_A1 = 6
+} fv_net_buffer;
+FV_API fv_status fv_net_get_buffer(fv_net_t n, int which, void* dst, size_t bytes);
+
 /* Conservation sums of a caller-held state, allocating nothing.
  *
  * The paper has no counterpart: this entry point exists for callers that
@@ -348,7 +374,12 @@ FV_API fv_status fv_step_learned(fv_mesh_t m, fv_net_t n, double dt);
  * other host threads) race and must be serialised by the caller.  The first
  * call on each device looks up the array's device address (with that device
  * current) and caches it; make that first call before any stream capture.
- * Errors: INVALID_ARG (NULL pointer, size out of range), CUDA. */
+ * The cached address belongs to the device's context: after a
+ * cudaDeviceReset of that device it is stale, so do not call this entry
+ * point again in that process after such a reset.
+ * Errors: INVALID_ARG (NULL pointer, size out of range), CUDA (also when a
+ * CUDA error from an earlier, unrelated call is still pending: it is
+ * reported, not cleared, and nothing is launched). */
 FV_API fv_status fv_conserved_sums_noalloc(const double* U, int nx, int ny, int nz,
                                            double lx, double ly, double lz,
                                            void* cuda_stream, double out[5]);

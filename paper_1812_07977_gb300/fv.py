@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfvgb.so")
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_BAD_HANDLE = range(7)
 BC = {"outflow": 0, "periodic": 1}
-PRECISION = {"fp64": 0, "fp64_fma": 1, "fp32_bulk": 2}
+PRECISION = {"fp64": 0, "fp32_bulk": 1, "fp64_fma": 2}
 
 # Every entry point declared in include/fv.h.
 ABI_SYMBOLS = (
@@ -32,7 +32,7 @@ ABI_SYMBOLS = (
     "fv_batch_get_counters", "fv_batch_info",
     "fv_net_param_count", "fv_net_create", "fv_net_destroy", "fv_net_set_params",
     "fv_net_get_params", "fv_net_set_scales", "fv_net_forward", "fv_net_train_step",
-    "fv_step_learned",
+    "fv_step_learned", "fv_net_get_buffer",
 )
 KERNEL_CLASSES = ("prim", "sweep_x", "sweep_y", "sweep_z", "fused", "ghost", "dt", "other")
 
@@ -107,6 +107,7 @@ def load_library(path: str | None = None):
         "fv_net_forward": ([vp, vp, vp], i),
         "fv_net_train_step": ([vp, vp, vp, d, d, dp], i),
         "fv_step_learned": ([vp, vp, d], i),
+        "fv_net_get_buffer": ([vp, i, vp, ctypes.c_size_t], i),
         "fv_status_string": ([i], ctypes.c_char_p),
         "fv_last_error": ([], ctypes.c_char_p),
     }
@@ -499,3 +500,25 @@ class Net:
 
     def step(self, mesh, dt):
         _check(self._lib.fv_step_learned(mesh.handle, self._h, float(dt)), "fv_step_learned")
+
+    # buffer name: (enum value, torch dtype name, channel-last pitch or None)
+    BUFFERS = {"features": (0, "bfloat16", 8), "h1": (1, "bfloat16", 32),
+               "h2": (2, "bfloat16", 32), "out": (3, "float32", None),
+               "grad_out": (4, "float32", None), "grad_a2": (5, "float32", 32),
+               "grad_a1": (6, "float32", 32)}
+
+    def buffer(self, name, mesh):
+        """An intermediate buffer of the last pass on `mesh`
+        (fv_net_get_buffer), as a CUDA tensor of shape (C, nz, ny, nx):
+        channel-last buffers are returned transposed to channel-first."""
+        torch = _torch()
+        which, dtype, pitch = self.BUFFERS[name]
+        _, nz, ny, nx = mesh.shape
+        shape = (nz * ny * nx, pitch) if pitch else (5, nz, ny, nx)
+        out = torch.empty(shape, dtype=getattr(torch, dtype), device=f"cuda:{mesh.device}")
+        _check(self._lib.fv_net_get_buffer(self._h, which, ctypes.c_void_p(out.data_ptr()),
+                                           out.numel() * out.element_size()),
+               "fv_net_get_buffer")
+        if pitch:
+            out = out.t().reshape(pitch, nz, ny, nx)
+        return out

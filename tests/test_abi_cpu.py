@@ -88,3 +88,32 @@ def test_calls_on_bad_handles(lib):
     assert lib.fv_destroy_mesh(bogus) == fv.ERR_BAD_HANDLE
     assert lib.fv_destroy_mesh(None) == fv.OK
     assert "not live" in lib.fv_last_error().decode()
+
+
+def _enum_values(name):
+    text = open(os.path.join(ROOT, "include", "fv.h")).read()
+    body = re.search(r"typedef enum\s*\{([^}]*)\}\s*" + name + r"\s*;", text, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    return {k: int(v) for k, v in re.findall(r"(\w+)\s*=\s*(\d+)", body)}
+
+
+def test_precision_enum_keeps_the_boundary_values():
+    """FV_PREC_FP64 = 0 and FV_PREC_FP32_BULK = 1 as the boundary first fixed
+    them; later arithmetic variants take new values, and the binding's names
+    map onto the header's numbers."""
+    v = _enum_values("fv_precision")
+    assert v["FV_PREC_FP64"] == 0 and v["FV_PREC_FP32_BULK"] == 1
+    assert v["FV_PREC_FP64_FMA"] == 2
+    assert len(set(v.values())) == len(v)
+    for name, num in fv.PRECISION.items():
+        assert v["FV_PREC_" + name.upper()] == num
+
+
+def test_status_and_bc_enum_values():
+    s = _enum_values("fv_status")
+    assert [s[k] for k in ("FV_OK", "FV_ERR_INVALID_ARG", "FV_ERR_OOM", "FV_ERR_CUDA",
+                           "FV_ERR_NONPHYSICAL", "FV_ERR_TIMEOUT",
+                           "FV_ERR_BAD_HANDLE")] == list(range(7))
+    b = _enum_values("fv_bc")
+    assert b == {"FV_BC_OUTFLOW": 0, "FV_BC_PERIODIC": 1}
+    assert fv.BC == {"outflow": 0, "periodic": 1}
