@@ -2,6 +2,8 @@
 // interior <-> ghosted copies of set/get state.  Built without FMA
 // contraction.  (The FP64 time step, ComputeTimeStep, is compiled with the
 // step kernels, in both of their arithmetic variants.)
+#include <atomic>
+
 #include "fv_device.cuh"
 #include "fv_internal.h"
 
@@ -10,12 +12,13 @@ using namespace fvd;
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kMaxBlocks = 152 * 8;
+constexpr int kBlocksPerSm = 8;   // 2048 threads: a full SM of 256-thread blocks
 
 inline unsigned grid_for(long long n) {
   long long b = (n + kThreads - 1) / kThreads;
   if (b < 1) b = 1;
-  return (unsigned)(b < kMaxBlocks ? b : kMaxBlocks);
+  const long long most = (long long)kBlocksPerSm * fv_sm_count();
+  return (unsigned)(b < most ? b : most);
 }
 
 // ---------------------------------------------------------------- ghosts
@@ -169,4 +172,20 @@ cudaError_t launch_pairwise_sums(const double* U, const Params& P, double* work,
     count = next;
   }
   return cudaGetLastError();
+}
+
+int fv_sm_count() {
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> cache[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+  if (dev < kMaxDevices) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+    return 1;
+  if (dev < kMaxDevices) cache[dev].store(n, std::memory_order_relaxed);
+  return n;
 }

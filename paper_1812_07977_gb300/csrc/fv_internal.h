@@ -117,6 +117,9 @@ fvd32::Params32 make_params32(const fvd::Params& P, double vacuum_ratio);
 }
 
 // fv_aux.cu (always built without contraction)
+// Multiprocessors of the current device (queried once per device and cached;
+// 1 if the query fails), for sizing grid-stride launches.
+int fv_sm_count();
 cudaError_t launch_fill_ghosts(double* U, const fvd::Params& P, cudaStream_t s);
 cudaError_t launch_scatter_interior(const double* dense, double* U, const fvd::Params& P,
                                     cudaStream_t s);

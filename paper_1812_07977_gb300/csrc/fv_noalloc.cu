@@ -135,6 +135,15 @@ extern "C" fv_status fv_conserved_sums_noalloc(const double* U, int nx, int ny, 
   fv_status st = scratch_address(&scratch);
   if (st != FV_OK) return fail(st);
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  // An error left pending by some earlier, unrelated call is reported as
+  // such (and left for its owner), not as a failure of these launches.
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    snprintf(g_noalloc_error, sizeof g_noalloc_error,
+             "a CUDA error was pending before the no-allocation sums started: %s",
+             cudaGetErrorString(e));
+    return fail(FV_ERR_CUDA);
+  }
   double* level1 = scratch;
   double* level2 = scratch + 5 * kLevel1;
   double* result = scratch + 5 * kLevel1 + 5 * kLevel2;
@@ -143,18 +152,19 @@ extern "C" fv_status fv_conserved_sums_noalloc(const double* U, int nx, int ny, 
   long long count = (next_pow2(n) + kChunk - 1) / kChunk;
   k_noalloc_pass<<<dim3((unsigned)count, 5), kThreads, 0, s>>>(
       U, n, n, count == 1 ? result : level1, count == 1 ? 1 : kLevel1);
+  e = cudaGetLastError();   // this launch's own error
   double* a = level1;
   long long stride = kLevel1;
-  while (count > 1) {
+  while (count > 1 && e == cudaSuccess) {
     const long long next = (count + kChunk - 1) / kChunk;
     double* dst = next == 1 ? result : level2;
     k_noalloc_pass<<<dim3((unsigned)next, 5), kThreads, 0, s>>>(a, count, stride, dst,
                                                                  next == 1 ? 1 : kLevel2);
+    e = cudaGetLastError();
     a = level2;
     stride = kLevel2;
     count = next;
   }
-  cudaError_t e = cudaGetLastError();
   double host[5];
   if (e == cudaSuccess) e = cudaMemcpyAsync(host, result, sizeof host, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
