@@ -57,35 +57,57 @@ def pad(x, periodic):
     return x
 
 
+def _shifted(xp, a, bb, c, shape):
+    """The (C, nz*ny*nx) matrix of input cells at offset (a, bb, c) - 1."""
+    nz, ny, nx = shape
+    return xp[:, a:a + nz, bb:bb + ny, c:c + nx].reshape(xp.shape[0], -1)
+
+
 def conv3(x, w, b, periodic):
-    """3x3x3 "same" cross-correlation, written as 27 shifted matrix products."""
+    """3x3x3 "same" cross-correlation, written as 27 shifted matrix products
+    (channels x cells, one per offset)."""
     _, nz, ny, nx = x.shape
     xp = pad(x, periodic)
-    out = np.broadcast_to(b[:, None, None, None], (w.shape[0], nz, ny, nx)).copy()
+    out = np.broadcast_to(b[:, None], (w.shape[0], nz * ny * nx)).copy()
     for a in range(3):
         for bb in range(3):
             for c in range(3):
-                sl = xp[:, a:a + nz, bb:bb + ny, c:c + nx]
-                out += np.einsum("oi,izyx->ozyx", w[:, :, a, bb, c], sl)
-    return out
+                out += w[:, :, a, bb, c] @ _shifted(xp, a, bb, c, (nz, ny, nx))
+    return out.reshape(w.shape[0], nz, ny, nx)
+
+
+def conv3_weight_grad(x, gout, periodic):
+    """dW of sum(gout * conv3(x, w, b)): per offset, gout times the shifted
+    input, summed over the cells."""
+    _, nz, ny, nx = x.shape
+    xp = pad(x, periodic)
+    g = gout.reshape(gout.shape[0], -1)
+    gw = np.zeros((gout.shape[0], x.shape[0], 3, 3, 3))
+    for a in range(3):
+        for bb in range(3):
+            for c in range(3):
+                gw[:, :, a, bb, c] = g @ _shifted(xp, a, bb, c, (nz, ny, nx)).T
+    return gw
+
+
+def conv3_input_grad(w, gout, periodic):
+    """dX of sum(gout * conv3(x, w, b)): each offset's transposed weights
+    times gout, added at the shifted cells, the padding folded back."""
+    _, nz, ny, nx = gout.shape
+    g = gout.reshape(gout.shape[0], -1)
+    gxp = np.zeros((w.shape[1], nz + 2, ny + 2, nx + 2))
+    for a in range(3):
+        for bb in range(3):
+            for c in range(3):
+                gxp[:, a:a + nz, bb:bb + ny, c:c + nx] += (
+                    w[:, :, a, bb, c].T @ g).reshape(w.shape[1], nz, ny, nx)
+    return unpad_adjoint(gxp, periodic)
 
 
 def conv3_backward(x, w, gout, periodic):
     """Gradients of sum(gout * conv3(x, w, b)) with respect to x, w and b."""
-    _, nz, ny, nx = x.shape
-    xp = pad(x, periodic)
-    gw = np.zeros_like(w)
-    gxp = np.zeros_like(xp)
-    for a in range(3):
-        for bb in range(3):
-            for c in range(3):
-                sl = xp[:, a:a + nz, bb:bb + ny, c:c + nx]
-                gw[:, :, a, bb, c] = np.einsum("ozyx,izyx->oi", gout, sl)
-                gxp[:, a:a + nz, bb:bb + ny, c:c + nx] += np.einsum(
-                    "oi,ozyx->izyx", w[:, :, a, bb, c], gout)
-    # fold the padding back onto the cells it copies
-    gx = unpad_adjoint(gxp, periodic)
-    return gx, gw, gout.sum(axis=(1, 2, 3))
+    return (conv3_input_grad(w, gout, periodic), conv3_weight_grad(x, gout, periodic),
+            gout.sum(axis=(1, 2, 3)))
 
 
 def unpad_adjoint(gp, periodic):
@@ -185,3 +207,215 @@ def init_params(seed: int, scale: float = 1.0):
         else:
             p[k] = np.zeros(shape)
     return p
+
+
+# ---------------------------------------------------------------------------
+# Element-wise error scales of the BF16 / FP32 network arithmetic.
+#
+# The library's network rounds its operands to BF16 (weights; the features
+# and the two hidden activations, which it stores as BF16; the 5- and
+# 32-channel gradients fed to the adjoint and weight-gradient convolutions)
+# and accumulates in FP32.  For each quantity of forward() and
+# loss_and_grads() the functions below compute, in FP64 from the oracle's own
+# values (no value of the library enters), two per-element numbers:
+#   S  the scale of the BF16 rounding errors that reach it: every rounding
+#      to BF16 is a relative error of at most U_BF16, taken as an independent
+#      zero-mean variable of variance U_BF16^2 (a conservative variance: a
+#      uniform error on [-u, u] has u^2/3), and S^2 is the variance of their
+#      first-order effect, propagated through each contraction with squared
+#      weights -- the probabilistic rounding-error analysis of Higham & Mary
+#      (SIAM J. Sci. Comput. 41, 2019), in which a length-n inner product's
+#      error grows like sqrt(n) u rather than n u;
+#   D  a deterministic bound of the errors made where the value itself is
+#      formed: FP32 accumulation, taken in the worst case (products of BF16
+#      operands are exact in FP32; the tensor cores round, possibly by
+#      truncation, once per MMA of 16 products, so K terms cost at most
+#      K/16 * 2^-22 of the sum of their magnitudes), the FP32 element-wise
+#      operations (a few 2^-24 each) and tanhf (2 ulp).  Downstream, an
+#      input's D counts like its S: an error of unknown sign, independent
+#      from one input element to the next (S^2 + D^2 enters the variance).
+# A library value v_dev of exact value v is expected within
+#   |v_dev - v| <= c S + D,
+# c a number of standard deviations (the tests use 10).  The parameters the
+# library holds are taken to be exactly `p` (FP32 values), each weight
+# reaching the tensor cores rounded once to BF16 -- unless `weights_exact`
+# says that every weight already is a BF16 value.  A weight's rounding error
+# is the same in every cell, so its effect on a sum over cells (a weight
+# gradient) is coherent, not random: tests that check weight gradients use
+# BF16-valued weights, for which it is zero.
+
+U_BF16 = 2.0 ** -8           # unit roundoff of BF16 (8-bit significand)
+ACC_MMA = 2.0 ** -22         # one tensor-core accumulation step (16 products)
+TANH_ABS = 2.0 ** -21        # |tanhf(a) - tanh(a)| on the device (2 ulp of |t| <= 1)
+K_SECOND = 12.0              # error size, in units of S, taken in second-order terms
+
+
+def _mma_steps(ci):
+    """MMA steps of 16 products per output value of a 3x3x3 convolution with
+    ci input channels (the channels padded to a multiple of 16)."""
+    return 27 * ((ci + 15) // 16)
+
+
+def _sq_conv(x, w, periodic):
+    """conv3 of x >= 0 with w^2 (or |w| for absolute sums) and no bias."""
+    return conv3(x, w, np.zeros(w.shape[0]), periodic)
+
+
+def _var(S, D):
+    """Variance an input error of scale S and bound D contributes downstream."""
+    return S * S + D * D
+
+
+def _layer(v, Sv, Dv, w, b, ci, periodic, uw):
+    """A convolution with BF16 weights and inputs, FP32 accumulation, bias
+    added in FP32; uw: the weights' relative rounding error (U_BF16, or 0
+    for BF16-valued weights).  Returns the exact output and its (S, D)."""
+    a = conv3(v, w, b, periodic)
+    w2 = w * w
+    # input errors and the weights' BF16 rounding (uw |w| per weight)
+    S2 = _sq_conv(_var(Sv, Dv), w2, periodic) + uw ** 2 * _sq_conv(v * v, w2, periodic)
+    S = np.sqrt(S2)
+    A = _sq_conv(np.abs(v), np.abs(w), periodic) + K_SECOND * S
+    D = _mma_steps(ci) * ACC_MMA * A + 2.0 ** -23 * (np.abs(a) + A + np.abs(b)[:, None, None, None])
+    return a, S, D
+
+
+def forward_scales(p, W, norm, periodic, gamma, U, weights_exact=False):
+    """forward() with error scales.  W: primitives, U: the conserved state
+    they come from (the library converts U to primitives in FP32, then
+    normalises and rounds to BF16).  Returns {x, h1, h2, o} (o = phi /
+    out_scale, the raw network output), the pre-activations a1, a2 and
+    S*, D* of x, h1, h2 and o."""
+    mean = norm["in_mean"][:, None, None, None]
+    scale = norm["in_scale"][:, None, None, None]
+    x = (W - mean) / scale
+    # FP32 primitives are a few ulp off (the pressure cancels against the
+    # kinetic energy, so its error scales with E), then the FP32 normalisation
+    ke = 0.5 * W[0] * (W[1] ** 2 + W[2] ** 2 + W[3] ** 2)
+    mag = np.abs(W) + np.abs(mean)
+    mag[4] += (gamma - 1.0) * (np.abs(U[4]) + ke)
+    out = {"x": x, "Sx": U_BF16 * np.abs(x), "Dx": (1 + U_BF16) * 2.0 ** -20 * mag / scale}
+    v, Sv, Dv = x, out["Sx"], out["Dx"]
+    for layer, (wk, bk, ci) in enumerate((("w1", "b1", C_IN), ("w2", "b2", C_HID),
+                                          ("w3", "b3", C_HID))):
+        a, Sa, Da = _layer(v, Sv, Dv, p[wk], p[bk], ci, periodic,
+                           0.0 if weights_exact else U_BF16)
+        if layer < 2:
+            h = np.tanh(a)
+            d = 1.0 - h * h
+            # the slope of tanh over |a| +- Da is at most sech^2(max(0, |a| - Da))
+            dmax = 1.0 - np.tanh(np.maximum(0.0, np.abs(a) - Da)) ** 2
+            Sh = np.sqrt((d * Sa) ** 2 + (U_BF16 * h) ** 2)
+            # (second order in Sa: the slope changes by at most 2 |a| Sa-ish;
+            # bounded by taking the slope's maximum over |a| +- (Da + K Sa))
+            dmx = 1.0 - np.tanh(np.maximum(0.0, np.abs(a) - Da - K_SECOND * Sa)) ** 2
+            Dh = (1 + U_BF16) * (dmax * Da + (dmx - d) * K_SECOND * Sa + TANH_ABS)
+            n = str(layer + 1)
+            out["a" + n], out["h" + n], out["Sh" + n], out["Dh" + n] = a, h, Sh, Dh
+            v, Sv, Dv = h, Sh, Dh
+        else:
+            out["o"], out["So"], out["Do"] = a, Sa, Da
+    return out
+
+
+def _stencil(f, dt, inv_d, scale, periodic, weights):
+    """dt scale sum_d inv_d^k (w0 f(i+e) + w1 f(i) + w0 f(i-e)) for f >= 0."""
+    fp = pad(f, periodic)
+    c = fp[:, 1:-1, 1:-1, 1:-1]
+    out = np.zeros_like(f)
+    k, w0, w1 = weights
+    for a in range(3):
+        axis = 3 - a
+        lo = [slice(None), slice(1, -1), slice(1, -1), slice(1, -1)]
+        hi = list(lo)
+        lo[axis] = slice(0, -2)
+        hi[axis] = slice(2, None)
+        out += inv_d[a] ** k * (w0 * fp[tuple(hi)] + w1 * c + w0 * fp[tuple(lo)])
+    return (dt * scale[:, None, None, None]) ** k * out
+
+
+def _through_stencil(f, Sf, Df, dt, inv_d, scale, periodic):
+    """(S, D) of the FP32 stencil dt scale sum_d inv_d (f(i+e) - 2 f(i) + f(i-e))
+    (the correction and its adjoint) from f's (S, D)."""
+    S = np.sqrt(_stencil(_var(Sf, Df), dt, inv_d, scale, periodic, (2, 1.0, 4.0)))
+    Sabs = _stencil(np.abs(f) + Df + K_SECOND * Sf, dt, inv_d, scale, periodic, (1, 1.0, 2.0))
+    return S, 2.0 ** -20 * Sabs
+
+
+def backward_scales(p, fw, r, dt, inv_d, norm, periodic, weights_exact=False):
+    """loss_and_grads() with error scales, from forward_scales()'s output fw
+    and the FP64 residual r.  Returns the exact g_o (dL/do), g_a2 and g_a1
+    (gradients of the tanh layers' pre-activations), grads (dict) and
+    S*, D* of g_o, g_a2, g_a1 and of every gradient tensor (dicts S, D)."""
+    osc, sig = norm["out_scale"], norm["res_scale"]
+    sig4 = sig[:, None, None, None]
+    o = fw["o"]
+    phi = osc[:, None, None, None] * o
+    dU = laplacian_update(phi, dt, inv_d, periodic)
+    n = dU.size
+    e = (dU - r) / sig4
+    g_dU = 2.0 * e / sig4 / n
+    g_o = laplacian_update_adjoint(g_dU, dt, inv_d, periodic) * osc[:, None, None, None]
+    # the loss kernel: dU by the FP32 stencil, e = (dU - r) / sigma, 2 e / (sigma N)
+    Sdu, Ddu = _through_stencil(o, fw["So"], fw["Do"], dt, inv_d, osc, periodic)
+    Se = Sdu / sig4
+    De = (1 + 2.0 ** -21) * (Ddu + 2.0 ** -23 * (np.abs(dU) + np.abs(r) + Ddu
+                                                  + K_SECOND * Sdu)) / sig4 \
+        + 2.0 ** -22 * (np.abs(e) + K_SECOND * Se)
+    Sg = 2.0 * Se / (sig4 * n)
+    Dg = (1 + 2.0 ** -22) * 2.0 * De / (sig4 * n) + 2.0 ** -22 * (np.abs(g_dU) + K_SECOND * Sg)
+    # its adjoint: the same stencil
+    Sgo, Dgo = _through_stencil(g_dU, Sg, Dg, dt, inv_d, osc, periodic)
+    out = {"g_o": g_o, "Sgo": Sgo, "Dgo": Dgo, "e": e, "Se": Se, "De": De}
+    u2 = U_BF16 ** 2
+    grads, S, D = {}, {}, {}
+    gout, Sgout, Dgout = g_o, Sgo, Dgo
+    ncell = g_o[0].size
+    # tensor-memory accumulation of a tile (4 planes x 8 MMAs of 16 cells),
+    # then the per-tile partials added in FP32 in tile order
+    wg_acc = 32 * ACC_MMA + (-(-ncell // 512)) * 2.0 ** -24
+    for wk, bk, ik, ci in (("w3", "b3", "2", C_HID), ("w2", "b2", "1", C_HID),
+                           ("w1", "b1", "", C_IN)):
+        xin = fw["h" + ik] if ik else fw["x"]
+        Sin = fw["Sh" + ik] if ik else fw["Sx"]
+        Din = fw["Dh" + ik] if ik else fw["Dx"]
+        grads[wk] = conv3_weight_grad(xin, gout, periodic)
+        grads[bk] = gout.sum(axis=(1, 2, 3))
+        # sum over cells of bf(g_dev) in_dev: the gradient's BF16 rounding and
+        # the errors of both factors, then the accumulation
+        vg, vi = _var(Sgout, Dgout), _var(Sin, Din)
+        S2 = conv3_weight_grad(xin * xin, vg + u2 * gout * gout, periodic) \
+            + conv3_weight_grad(vi, gout * gout, periodic)
+        S[wk] = np.sqrt(S2)
+        ag = np.abs(gout) + K_SECOND * np.sqrt(vg)
+        ai = np.abs(xin) + K_SECOND * np.sqrt(vi)
+        D[wk] = wg_acc * (1 + U_BF16) * conv3_weight_grad(ai, ag, periodic) \
+            + K_SECOND ** 2 * conv3_weight_grad(np.sqrt(vi), np.sqrt(vg), periodic) / ncell ** 0.5
+        S[bk] = np.sqrt(vg.sum(axis=(1, 2, 3)))
+        D[bk] = (5 + -(-ncell // 512)) * 2.0 ** -24 * ag.sum(axis=(1, 2, 3))
+        if wk == "w1":
+            break
+        # the input gradient: the adjoint convolution of bf(g_dev) with the
+        # BF16 weights (FP32 output), then g_a = g_h (1 - y^2), y the layer's
+        # BF16 activation
+        w = p[wk]
+        g_h = conv3_input_grad(w, gout, periodic)
+        uw2 = 0.0 if weights_exact else u2
+        Sgh = np.sqrt(conv3_input_grad(w * w, vg + (u2 + uw2) * gout * gout, periodic))
+        Dgh = _mma_steps(C_OUT if wk == "w3" else C_HID) * ACC_MMA * (1 + U_BF16) ** 2 \
+            * (conv3_input_grad(np.abs(w), np.abs(gout), periodic) + K_SECOND * Sgh)
+        h, Sh, Dh = fw["h" + ik], fw["Sh" + ik], fw["Dh" + ik]
+        d = 1.0 - h * h
+        g_a = g_h * d
+        # |y^2 - h^2| beyond its random linear part 2 h dy, with |dy| up to
+        # Dh + K_SECOND Sh, and the products of two errors likewise
+        Sga = np.sqrt((d * Sgh) ** 2 + (d * Dgh) ** 2 + (2.0 * h * g_h) ** 2 * _var(Sh, Dh))
+        # second-order terms: |y^2 - h^2 - 2 h dy| = dy^2 and dg dy, with
+        # |dy| <= Dh + K Sh and |dg| <= Dgh + K Sgh; the FP32 multiply
+        ey, eg = Dh + K_SECOND * Sh, Dgh + K_SECOND * Sgh
+        Dga = (np.abs(g_h) + eg) * ey * ey + eg * 2.0 * (np.abs(h) + ey) * ey \
+            + 2.0 ** -22 * (np.abs(g_h) + eg) * (np.abs(d) + 2.0 * np.abs(h) * ey + ey * ey)
+        out["g_a" + ik], out["Sg" + ik], out["Dg" + ik] = g_a, Sga, Dga
+        gout, Sgout, Dgout = g_a, Sga, Dga
+    out["grads"], out["S"], out["D"] = grads, S, D
+    return out

@@ -590,6 +590,11 @@ struct fv_net_s {
   uint4* wlay = nullptr;            // laid-out weights of the convolution being run
   unsigned* status = nullptr;       // device: set by a convolution whose MMA wait ran out
   unsigned* host_status = nullptr;  // pinned mirror
+  // the last pass: its mesh's cell count and stream, and whether the
+  // gradient buffers hold a training step's values
+  long long last_cells = 0;
+  cudaStream_t last_stream = nullptr;
+  bool have_grads = false;
 };
 
 namespace {
@@ -710,7 +715,8 @@ cudaError_t conv_wgrad(const TI* in, const float* gout, float* partial, float* g
 
 unsigned grid_for(long long n) {
   long long b = (n + 255) / 256;
-  return (unsigned)(b < 152 * 8 ? (b < 1 ? 1 : b) : 152 * 8);
+  const long long most = 8LL * fv_sm_count();
+  return (unsigned)(b < most ? (b < 1 ? 1 : b) : most);
 }
 
 // Forward pass on the mesh's current state: x, h1, h2 and o.
@@ -731,6 +737,9 @@ fv_status forward(fv_net_s* n, const MeshView& v, const Grid3& g) {
     e = conv_fwd<CH, COUT, bf16, float, false, true, false>(n->h2, n->wb + OW3, n->params + OB3, n->o, g,
                                                n->wlay, n->status, s);
   if (e != cudaSuccess) return cuda_fail(e, "network forward pass");
+  n->last_cells = g.n;
+  n->last_stream = s;
+  n->have_grads = false;
   return FV_OK;
 }
 
@@ -923,6 +932,7 @@ fv_status fv_net_train_step(fv_net_t n, fv_mesh_t m, const double* residual, dou
     e = cudaMemcpyAsync(n->host_status, n->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "network training step");
+  n->have_grads = true;
   if ((st = take_status(n, s)) != FV_OK) return st;
   if (loss_out) {
     double L = 0.0;
@@ -945,6 +955,35 @@ fv_status fv_step_learned(fv_mesh_t m, fv_net_t n, double dt) {
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_fill_ghosts(v.U, v.P, v.stream);
   if (e != cudaSuccess) return cuda_fail(e, "applying the learned correction");
+  return FV_OK;
+}
+
+fv_status fv_net_get_buffer(fv_net_t n, int which, void* dst, size_t bytes) {
+  fv_status st = check(n);
+  if (st != FV_OK) return st;
+  if (!dst) return fail(FV_ERR_INVALID_ARG, "dst is NULL");
+  const long long c = n->last_cells;
+  const void* src = nullptr;
+  size_t size = 0;
+  bool grad = false;
+  switch (which) {
+    case FV_NET_BUF_FEATURES: src = n->x; size = (size_t)c * pitch8<CIN>() * sizeof(bf16); break;
+    case FV_NET_BUF_H1: src = n->h1; size = (size_t)c * CH * sizeof(bf16); break;
+    case FV_NET_BUF_H2: src = n->h2; size = (size_t)c * CH * sizeof(bf16); break;
+    case FV_NET_BUF_OUT: src = n->o; size = (size_t)c * COUT * sizeof(float); break;
+    case FV_NET_BUF_GRAD_OUT: src = n->go; size = (size_t)c * COUT * sizeof(float); grad = true; break;
+    case FV_NET_BUF_GRAD_A2: src = n->g2; size = (size_t)c * CH * sizeof(float); grad = true; break;
+    case FV_NET_BUF_GRAD_A1: src = n->g1; size = (size_t)c * CH * sizeof(float); grad = true; break;
+    default: return fail(FV_ERR_INVALID_ARG, "unknown network buffer %d", which);
+  }
+  if (c == 0 || (grad && !n->have_grads))
+    return fail(FV_ERR_INVALID_ARG, "buffer %d has not been produced by a %s yet", which,
+                grad ? "training step" : "forward pass");
+  if (bytes != size)
+    return fail(FV_ERR_INVALID_ARG, "buffer %d holds %zu bytes, not %zu", which, size, bytes);
+  cudaError_t e = cudaMemcpyAsync(dst, src, size, cudaMemcpyDeviceToDevice, n->last_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(n->last_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "fv_net_get_buffer");
   return FV_OK;
 }
 

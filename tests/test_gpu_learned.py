@@ -1,11 +1,14 @@
 """Learned flux correction on the GPU (fv_net_*, fv_step_learned) against the
 FP64 numpy oracle (oracle/learned.py) on the same parameters and states.
 
-The GPU network runs in BF16 (weights and activations; 8-bit mantissa)
-with FP32 accumulation, so it is compared with relative tolerances derived
-from BF16 rounding (2^-9 per value, compounded over three layers): the
-network output within 2% of its scale, the loss within 2%, each parameter
-tensor's gradient within 5% (relative L2) and aligned (cosine > 0.995)."""
+The GPU network runs in BF16 (weights and activations; 8-bit significand)
+with FP32 accumulation.  On this small, ragged mesh (every tensor-core tile
+partly outside it) the network output is checked element by element against
+the oracle's error scales (16 S + D, oracle.learned.forward_scales), and the
+loss and each parameter tensor's gradient against gates about three times
+the measured BF16-level error (relative L2 below 1%, cosine above 0.9999);
+the element-wise gradient checks at the full-tile 64^3 mesh are in
+test_gpu_learned_elementwise.py."""
 import numpy as np
 import pytest
 
@@ -60,12 +63,14 @@ def _inv_d(shape):
 def test_forward_matches_oracle():
     U0, p, mesh, net = _setup()
     o = net.forward(mesh).cpu().numpy().astype(np.float64)
-    phi, _ = L.forward(p, _prims(U0), NORM, PER)
-    ref = phi / NORM["out_scale"][:, None, None, None]
-    err = np.abs(o - ref).max() / np.abs(ref).max()
+    p32 = {k: np.asarray(v, np.float32).astype(np.float64) for k, v in p.items()}
+    fw = L.forward_scales(p32, _prims(U0), NORM, PER, 1.4, U0)
+    ref = fw["o"]
+    err = np.abs(o - ref)
+    ratio = (err / (16.0 * fw["So"] + fw["Do"])).max()
     rel2 = np.linalg.norm(o - ref) / np.linalg.norm(ref)
-    print("forward: max err", err, "rel L2", rel2)
-    assert err < 2e-2 and rel2 < 1e-2
+    print("forward: max err / (16 S + D)", ratio, "rel L2", rel2)
+    assert ratio <= 1.0 and rel2 < 1e-2
     mesh.close()
     net.close()
 
@@ -92,7 +97,7 @@ def test_loss_and_gradients_match_oracle():
         rel = np.linalg.norm(a - b) / np.linalg.norm(b)
         cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
         print(k, "rel L2", rel, "cos", cos)
-        assert rel < 5e-2 and cos > 0.995, k
+        assert rel < 1e-2 and cos > 0.9999, k
     mesh.close()
     net.close()
 
