@@ -225,6 +225,50 @@ __device__ __forceinline__ Prim cons_to_prim(const double u[NF], const Params& P
   return w;
 }
 
+// ---------------------------------------------------------------- time step
+// CFL signal speed of one cell (ComputeTimeStep):
+// s = ((|vx|+c)/dx + (|vy|+c)/dy) + (|vz|+c)/dz with c = sqrt((gamma p)/rho):
+// IEEE operations in this order, or the Newton forms in the FMA build.
+__device__ __forceinline__ double cell_speed(const Prim& w, const Params& P) {
+#ifdef FV_NEWTON_DIVSQRT
+  const double c = sound_speed_nr(P.gamma * w.p, w.r);
+#else
+  const double c = sqrt(P.gamma * w.p / w.r);
+#endif
+  return ((fabs(w.vx) + c) * P.inv_d[0] + (fabs(w.vy) + c) * P.inv_d[1]) +
+         (fabs(w.vz) + c) * P.inv_d[2];
+}
+
+// x as a float rounded toward zero (|result| <= |x|, relative error below
+// 2^-23), on the integer pipe; `ok` is cleared unless x is +-0 or
+// 2^-100 <= |x| < 2^101.
+__device__ __forceinline__ float trunc_f32(double x, bool& ok) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  if (((hi << 1) | lo) == 0u) return 0.0f;
+  ok = ok && e - (1023u - 100u) <= 200u;
+  const unsigned f = ((e - 896u) << 23) | ((hi & 0x000FFFFFu) << 3) | (lo >> 29);
+  return __uint_as_float(f | (hi & 0x80000000u));
+}
+
+// An upper bound of cell_speed(w) from FP32 arithmetic: inputs truncated
+// (relative error < 2^-23 each) and about ten FP32 operations (< 2^-23 each)
+// give s32 within 2^-19 of the exact speed, and s32 (1 + 2^-14) is above
+// the exact speed and above the FP64 cell_speed (within 2 ulps of it).
+// +inf when rho or p is not positive or an operand is outside the range of
+// trunc_f32 (the FP64 speed is then always computed).
+__device__ __forceinline__ float speed_bound(const Prim& w, float g32, const float i32[3]) {
+  bool ok = true;
+  const float r = trunc_f32(w.r, ok), p = trunc_f32(w.p, ok);
+  const float vx = trunc_f32(w.vx, ok), vy = trunc_f32(w.vy, ok), vz = trunc_f32(w.vz, ok);
+  if (!(ok && r > 0.0f && p > 0.0f)) return __int_as_float(0x7F800000);
+  const float c = __fsqrt_rn(__fdiv_rn(__fmul_rn(g32, p), r));
+  const float sp = __fadd_rn(__fadd_rn(__fmul_rn(__fadd_rn(fabsf(vx), c), i32[0]),
+                                       __fmul_rn(__fadd_rn(fabsf(vy), c), i32[1])),
+                             __fmul_rn(__fadd_rn(fabsf(vz), c), i32[2]));
+  return __fmul_ru(sp, 1.0f + 0x1p-14f);
+}
+
 // One side of a face: conserved state, normal flux, sound speed.
 template <int AXIS>
 struct Side {

@@ -27,6 +27,9 @@
 // four cells all equal those one plane below keeps that plane's flux (each
 // plane's primitives are stored with a per-cell "equal to the plane below"
 // flag).  Both are decided per warp.
+#include <cmath>
+#include <limits>
+
 #include "fv_device32.cuh"
 #include "fv_internal.h"
 
@@ -157,32 +160,16 @@ __device__ __forceinline__ void smem_store_flag(SM& s, int row, int col, const P
   s.w[4][row][col] = w.p;
 }
 
-// CFL signal speed of a cell's state in FP32 (bits of a non-negative float;
-// 0 for a non-physical cell, which is counted).  Explicit roundings (no
-// contraction): every kernel that computes the speed gets the same bits, so
-// the time-step pass, the fused stage 2 and batched runs agree on dt.
-__device__ __forceinline__ unsigned speed_bits(const double u[NF], const Params32& Q,
-                                               unsigned long long& bad) {
-  const Prim32 w = prim_from_state(u, Q);
-  if (!physical(w)) {
-    ++bad;
-    return 0u;
+// Folds a thread's CFL speed maximum (a double >= 0, ordered like its bits)
+// into a grid-wide maximum held as the bits of a double.  All 32 lanes call.
+__device__ __forceinline__ void max_speed_to(unsigned long long* dst, double smax) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(smax);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, b, o);
+    b = v > b ? v : b;
   }
-  const float c2 = __fmul_rn(__fmul_rn(Q.gamma, w.p), rcp(w.r));
-  const float c = __fmul_rn(c2, rsqrtf(c2));
-  const float sp = __fadd_rn(__fadd_rn(__fmul_rn(__fadd_rn(fabsf(w.vx), c), Q.inv_d[0]),
-                                       __fmul_rn(__fadd_rn(fabsf(w.vy), c), Q.inv_d[1])),
-                             __fmul_rn(__fadd_rn(fabsf(w.vz), c), Q.inv_d[2]));
-  const unsigned b = __float_as_uint(sp);
-  return (sp > 0.0f && b < 0x7F800000u) ? b : 0u;
-}
-
-// Folds a thread's speed maximum (bits of a non-negative float) into a
-// grid-wide maximum held as the bits of the equal double.
-__device__ __forceinline__ void max_speed_to(unsigned long long* dst, unsigned smax) {
-  smax = __reduce_max_sync(0xffffffffu, smax);
-  if ((threadIdx.x & 31u) == 0u && smax)
-    atomicMax(dst, (unsigned long long)__double_as_longlong(f2d(__uint_as_float(smax))));
+  if ((threadIdx.x & 31u) == 0u && b) atomicMax(dst, b);
 }
 
 // Face flux between cells a1 and a2 given the four cells a0..a3 along the
@@ -206,16 +193,17 @@ __device__ __forceinline__ void face_flux(const Prim32& a0, const Prim32& a1, co
 // STAGE 1: U1 = U + dU.  STAGE 2: U = ((U + U1) + dU) / 2.  The input of the
 // substep (U for stage 1, U1 for stage 2) has its ghosts filled.  Counts of
 // face fallbacks and non-physical cells accumulate in the caller's counters.
-// MC: the limiter parameter is 2.  NEXT (stage 2): also the CFL speed of
-// each output cell (the next time step's), its maximum into smax_next and
-// its non-physical cells into bad_next.
+// MC: the limiter parameter is 2.  NEXT (stage 2): also the FP64 CFL speed
+// of each output cell (the next time step's), its maximum into smax_next
+// (with smax_next_f <= smax_next as a float) and its non-physical cells
+// into bad_next.
 template <class S, int STAGE, bool MC, bool NEXT>
 __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
                                              double* __restrict__ U1, const fvd::Params& P,
                                              const Params32& Q, float dt, int i0, int j0,
                                              int k0, int k1, unsigned& fallbacks_out,
                                              unsigned long long& bad_out, unsigned& evaluated,
-                                             unsigned& smax_next,
+                                             double& smax_next, float& smax_next_f,
                                              unsigned long long& bad_next) {
   const double* __restrict__ src = STAGE == 1 ? U : U1;
   const int tid = threadIdx.x;
@@ -429,7 +417,7 @@ __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
           U[q * nf + g] = un[q];
         }
       }
-      if (NEXT && STAGE == 2) smax_next = max(smax_next, speed_bits(un, Q, bad_next));
+      if (NEXT && STAGE == 2) fold_speed(un, P, Q, smax_next, smax_next_f, bad_next);
     }
 #pragma unroll
     for (int q = 0; q < NF; ++q) fz_lo[q] = fz_hi[q];
@@ -449,12 +437,14 @@ k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params
   using S = Shape<TY>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<S>& s = *reinterpret_cast<Smem<S>*>(smem_raw);
-  unsigned fallbacks = 0, evaluated = 0, smax_next = 0;
+  unsigned fallbacks = 0, evaluated = 0;
   unsigned long long bad = 0, bad_next = 0;
+  double smax_next = 0.0;
+  float smax_next_f = 0.0f;
   const int k0 = blockIdx.z * kchunk;
   stage32_tile<S, STAGE, MC, STAGE == 2>(s, U, U1, P, Q, dt, blockIdx.x * TX, blockIdx.y * TY,
                                          k0, min(k0 + kchunk, P.nz), fallbacks, bad, evaluated,
-                                         smax_next, bad_next);
+                                         smax_next, smax_next_f, bad_next);
   if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
   if (bad) atomicAdd(&ctr->np_step, bad);
   warp_count(&ctr->faces, evaluated);
@@ -489,11 +479,12 @@ k_stage32_batch(double* __restrict__ U, double* __restrict__ U1, BatchMesh* __re
     const int4 w = items[it];       // mesh, tile x, tile y, chunk
     BatchMesh& m = meshes[w.x];
     const int k0 = w.w * kchunk;
-    unsigned smax_next = 0;
+    double smax_next = 0.0;
+    float smax_next_f = 0.0f;
     stage32_tile<S, STAGE, MC, STAGE == 2>(s, U + m.offset, U1 + m.offset, m.P, m.Q,
                                            (float)m.dt, w.y * TX, w.z * TY, k0,
                                            min(k0 + kchunk, m.P.nz), fallbacks, bad, evaluated,
-                                           smax_next, bad_next);
+                                           smax_next, smax_next_f, bad_next);
     if (STAGE == 2) max_speed_to(&m.smax_bits, smax_next);
   }
   if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
@@ -502,46 +493,59 @@ k_stage32_batch(double* __restrict__ U, double* __restrict__ U1, BatchMesh* __re
   warp_count(&ctr->faces, evaluated);
 }
 
-// CFL signal speed of interior cell m of a mesh in FP32 (bits of a
-// non-negative float; 0 for a non-physical cell, which is counted).
-__device__ __forceinline__ unsigned cell_speed_bits(const double* __restrict__ U,
-                                                    const fvd::Params& P, const Params32& Q,
-                                                    long long m, unsigned long long& bad) {
+// Folds the FP64 CFL speed of interior cell m of a mesh into a running
+// maximum (fold_speed).
+__device__ __forceinline__ void fold_cell(const double* __restrict__ U, const fvd::Params& P,
+                                          const Params32& Q, long long m, double& smax,
+                                          float& smax_f, unsigned long long& bad) {
   const long long k = m / ((long long)P.nx * P.ny);
   const long long r = m - k * ((long long)P.nx * P.ny);
   const long long j = r / P.nx, i = r - j * P.nx;
   double u[NF];
   load_state(U, P.nfield, (k + 2) * P.sz + (j + 2) * P.sy + (i + 2), u);
-  return speed_bits(u, Q, bad);
+  fold_speed(u, P, Q, smax, smax_f, bad);
 }
 
-// CFL signal speed per interior cell in FP32 from the FP64 state; the
-// maximum is taken exactly (non-negative floats order like their bits) and
-// handed over as the bits of the equal double; dt = cfl / max is formed in
-// FP64 on the host.
+// Block maximum of the threads' speeds (doubles >= 0), folded into *dst;
+// blocks of 256 threads.
+__device__ __forceinline__ void block_max_to(unsigned long long* dst, double smax) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(smax);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, b, o);
+    b = v > b ? v : b;
+  }
+  __shared__ unsigned long long wmax[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) wmax[wid] = b;
+  __syncthreads();
+  if (wid == 0) {
+    b = lane < 8 ? wmax[lane] : 0ULL;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, b, o);
+      b = v > b ? v : b;
+    }
+    if (lane == 0 && b) atomicMax(dst, b);
+  }
+}
+
+// The CFL time step's maximum over the interior cells with FP64 speeds (the
+// FP64 method's IEEE operations); FP32 bounds skip the cells that cannot
+// raise a thread's running maximum.  Exact in any order (non-negative
+// doubles order like their bits); dt = cfl / max is formed in FP64 on the
+// host.
 __global__ void __launch_bounds__(256)
 k_reduce_dt32(const double* __restrict__ U, fvd::Params P, Params32 Q, DevCounters* ctr) {
   const long long n = (long long)P.nx * P.ny * P.nz;
-  unsigned smax = 0;
+  double smax = 0.0;
+  float smax_f = 0.0f;
   unsigned long long bad = 0;
   for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < n;
        m += (long long)gridDim.x * blockDim.x)
-    smax = max(smax, cell_speed_bits(U, P, Q, m, bad));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-  __shared__ unsigned wmax[8];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) wmax[wid] = smax;
+    fold_cell(U, P, Q, m, smax, smax_f, bad);
   if (bad) atomicAdd(&ctr->np_dt, bad);
-  __syncthreads();
-  if (wid == 0) {
-    smax = lane < 8 ? wmax[lane] : 0u;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-    if (lane == 0 && smax)
-      atomicMax(&ctr->smax_bits,
-                (unsigned long long)__double_as_longlong(f2d(__uint_as_float(smax))));
-  }
+  block_max_to(&ctr->smax_bits, smax);
 }
 
 // Batched CFL maximum: block b reduces chunk c of mesh m (dt_blocks[b]) and
@@ -554,25 +558,13 @@ k_batch_dt(const double* __restrict__ U, BatchMesh* __restrict__ meshes,
   const long long n = (long long)mesh.P.nx * mesh.P.ny * mesh.P.nz;
   const long long lo = (long long)bm.y * kBatchDtChunk;
   const long long hi = min(n, lo + kBatchDtChunk);
-  unsigned smax = 0;
+  double smax = 0.0;
+  float smax_f = 0.0f;
   unsigned long long bad = 0;
   for (long long m = lo + threadIdx.x; m < hi; m += blockDim.x)
-    smax = max(smax, cell_speed_bits(U + mesh.offset, mesh.P, mesh.Q, m, bad));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-  __shared__ unsigned wmax[8];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) wmax[wid] = smax;
+    fold_cell(U + mesh.offset, mesh.P, mesh.Q, m, smax, smax_f, bad);
   if (bad) atomicAdd(&ctr->np_dt, bad);
-  __syncthreads();
-  if (wid == 0) {
-    smax = lane < 8 ? wmax[lane] : 0u;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-    if (lane == 0 && smax)
-      atomicMax(&mesh.smax_bits,
-                (unsigned long long)__double_as_longlong(f2d(__uint_as_float(smax))));
-  }
+  block_max_to(&mesh.smax_bits, smax);
 }
 
 // Clears the per-mesh maxima and the work counters before a step.
@@ -602,6 +594,14 @@ k_batch_ghosts(double* __restrict__ base, const BatchMesh* __restrict__ meshes,
 
 }  // namespace
 
+// The nearest floats below and above x (equal when x is a float).
+static void bracket_f32(double x, float& lo, float& hi) {
+  const float f = (float)x;
+  lo = hi = f;
+  if ((double)f > x) lo = std::nextafter(f, -std::numeric_limits<float>::infinity());
+  if ((double)f < x) hi = std::nextafter(f, std::numeric_limits<float>::infinity());
+}
+
 Params32 make_params32(const fvd::Params& P, double vacuum_ratio) {
   Params32 Q;
   Q.gamma = (float)P.gamma;
@@ -611,6 +611,10 @@ Params32 make_params32(const fvd::Params& P, double vacuum_ratio) {
   for (int a = 0; a < 3; ++a) Q.inv_d[a] = (float)P.inv_d[a];
   Q.gm1_d = P.gm1;
   Q.vacuum_ratio = (float)vacuum_ratio;
+  float lo;
+  bracket_f32(P.gm1, Q.gm1_lo, Q.gm1_hi);
+  bracket_f32(P.gamma, lo, Q.gamma_hi);
+  for (int a = 0; a < 3; ++a) bracket_f32(P.inv_d[a], lo, Q.inv_hi[a]);
   return Q;
 }
 
@@ -716,7 +720,7 @@ cudaError_t launch_reduce_dt(const double* U, const fvd::Params& P, double vacuu
   if (e != cudaSuccess) return e;
   const long long n = (long long)P.nx * P.ny * P.nz;
   long long blocks = (n + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > 8LL * fv_sm_count()) blocks = 8LL * fv_sm_count();
   k_reduce_dt32<<<(unsigned)blocks, 256, 0, s>>>(U, P, make_params32(P, vacuum_ratio), ctr);
   return cudaGetLastError();
 }

@@ -85,7 +85,26 @@ def test_batch_dt_per_mesh_matches_oracle():
     for m, s in enumerate(spec):
         om = oracle.mesh(*s["shape"])
         dto, _, _ = oracle.reduce_dt(om, oracle.ghosted_from_interior(om, s["U0"]), 0.4)
-        assert abs(dts[m] - dto) <= 1e-6 * dto, (m, dts[m], dto)
+        assert dts[m] == dto, (m, dts[m], dto)
+
+
+def test_batch_stage2_maxima_give_the_oracles_dt():
+    """The second substep takes each mesh's FP64 CFL maximum of the state it
+    writes; the next step's dt is the oracle's dt of that state, bit for bit."""
+    from paper_1812_07977_gb300.fv import Batch
+    spec = _small_batch(count=6, seed=9)
+    with Batch([s["shape"] for s in spec]) as b:
+        for m, s in enumerate(spec):
+            b.set_state(m, s["U0"])
+        for _ in range(3):
+            b.step(0.4)
+            states = [b.get_state(m).cpu().numpy() for m in range(len(spec))]
+            b.step(0.4)
+            dts = b.dts()
+            for m, s in enumerate(spec):
+                om = oracle.mesh(*s["shape"])
+                dto, _, _ = oracle.reduce_dt(om, oracle.ghosted_from_interior(om, states[m]), 0.4)
+                assert dts[m] == dto, (m, dts[m], dto)
 
 
 @pytest.mark.parametrize("use_graph", [False, True])

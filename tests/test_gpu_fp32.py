@@ -319,3 +319,36 @@ def test_integer_conversions_match_hardware(tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
     print(r.stdout)
     assert r.returncode == 0 and "mismatches 0" in r.stdout, r.stdout + r.stderr
+
+
+def test_fp32_bulk_dt_is_the_oracles_bitwise():
+    """FP64 is kept for the CFL time step: the FP32-bulk path takes every
+    cell's speed in FP64 (the FP64 method's operations; FP32 interval bounds
+    only skip cells that cannot raise the maximum), so its dt is the
+    oracle's, bit for bit -- from the separate pass after set_state, on
+    states whose speeds span many orders of magnitude, near ties and operands
+    outside the bound's range, and from stage 2's maximum of the state it
+    writes."""
+    from test_gpu_parity import _wide_range_states
+    from paper_1812_07977_gb300.fv import Mesh
+    n = (128, 120, 96)
+    for seed, U0 in enumerate(_wide_range_states(*n, seed=3)):
+        om = oracle.mesh(*n, ly=2.0)
+        dto, _, bad = oracle.reduce_dt(om, oracle.ghosted_from_interior(om, U0), 0.4)
+        with Mesh(*n, ly=2.0, precision="fp32_bulk") as m:
+            m.set_state(U0)
+            assert m.reduce_dt(0.4) == dto, seed
+            assert m.counters()[0] == bad
+    for U0, bc in ((problems.riemann_oblique(33, 17, 9), (OUT, OUT, OUT)),
+                   (problems.random_smooth_periodic(20, 24, 16, seed=11), (PER, PER, PER))):
+        nn = U0.shape[1:][::-1]
+        om = oracle.mesh(*nn, bc=bc)
+        m = _mesh32(nn, bc)
+        m.set_state(U0)
+        for _ in range(4):
+            dt = m.reduce_dt(0.4)        # after the first step: stage 2's maximum
+            U = m.get_state().cpu().numpy()
+            dto, _, _ = oracle.reduce_dt(om, oracle.ghosted_from_interior(om, U), 0.4)
+            assert dt == dto
+            m.step(dt)
+        m.close()
