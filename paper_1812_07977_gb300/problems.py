@@ -88,11 +88,15 @@ def riemann_planar(nx, ny, nz, axis=0, left=SOD_LEFT, right=SOD_RIGHT, x0=0.5,
     return conserved_from_primitive(rho, v[0], v[1], v[2], p, gamma)
 
 
-def riemann_oblique(nx, ny, nz, left=SOD_LEFT, right=SOD_RIGHT, gamma=GAMMA) -> np.ndarray:
+def riemann_oblique(nx, ny, nz, left=SOD_LEFT, right=SOD_RIGHT, gamma=GAMMA,
+                    planes=None) -> np.ndarray:
     """Sod states split by the plane through (1/2,1/2,1/2) with normal
     (1,1,1)/sqrt(3): left where (x-1/2)+(y-1/2)+(z-1/2) < 0.  The velocity
-    (along the normal) is zero in both Sod states."""
+    (along the normal) is zero in both Sod states.  planes=(k0, k1): only the
+    z planes k0 .. k1-1 of that state (a slab, without building the rest)."""
     x, y, z = _grid(nx, ny, nz)
+    if planes is not None:
+        z = z[planes[0]:planes[1]]
     s = (x - 0.5) + (y - 0.5) + (z - 0.5)
     is_left = s < 0.0
     rho = np.where(is_left, left[0], right[0])

@@ -108,3 +108,10 @@ def test_shear_layer_device_matches_host():
     b = problems.shear_layer_device(n, amp, gamma=gamma, modes=8, seed=0, device="cpu")
     assert isinstance(b, torch.Tensor) and tuple(b.shape) == a.shape
     assert np.allclose(b.numpy(), a, rtol=1e-14, atol=1e-15)
+
+
+def test_oblique_slab_equals_the_slice_of_the_whole_state():
+    whole = problems.riemann_oblique(24, 20, 16)
+    for k0, k1 in ((0, 4), (6, 10), (13, 16)):
+        slab = problems.riemann_oblique(24, 20, 16, planes=(k0, k1))
+        assert np.array_equal(slab, whole[:, k0:k1])
