@@ -4,7 +4,7 @@
 (1,1,1) through the cube centre, gamma 1.4, outflow, CFL 0.4).
 
 One step = ComputeTimeStep (CFL min-reduction, one 32-byte device-to-host
-read) + the full RK2 step (prim, three sweeps and a ghost fill per substep);
+read) + the full RK2 step (one fused kernel and a ghost fill per substep);
 one zone-update = one interior cell advanced by one step.  The timed region
 starts from the initial state already resident in HBM and covers K steps of
 the workload.  Prints one JSON line (rank 0).
@@ -33,9 +33,8 @@ sys.path.insert(0, ROOT)
 METRIC = "zone-updates/s per RK2 step at 256^3 (FP64 vs FP32) and % of HBM roofline"
 CFL = 0.4
 N = 256
-SM_COUNT = 152
 # FP64 issue rate measured on this GPU: 2 DFMA lane-operations per SM per
-# clock (598 G DFMA/s over 152 SMs at ~1.92 GHz); 2 flops per DFMA.
+# clock; 2 flops per DFMA.
 DFMA_PER_SM_CLK = 2.0
 # Algorithmic FP64 flops of the method (divide and square root count one
 # each), from the operation counts of the definition:
@@ -43,30 +42,28 @@ DFMA_PER_SM_CLK = 2.0
 #             + HLL denominator and product 3 + 5 components x 7 = 82
 #   per cell and axis: differences 5 + limited slopes 5x4 + face states 5x4
 #             + one face 82 = 127
-#   divergence: x 2, y 3, z 3 per component; z sweep adds dt* (1) and the
-#             RK combine (stage 1: 1 add, stage 2: 2 adds + 1 multiply).
+#   divergence: x 2, y 3, z 3 per component; z adds dt* (1) and the RK
+#             combine (stage 1: 1 add, stage 2: 2 adds + 1 multiply).
 FLOPS_SWEEP = {"sweep_x": 127 + 5 * 2, "sweep_y": 127 + 5 * 3,
                "sweep_z": 127 + 5 * 3 + 5 * 1 + 5 * 2}     # z: stage average of RK
 # Of these, 127 per cell belong to its face (differences, slopes, face states,
-# HLL flux); a face whose flux the sweep reuses (a run of equal cells) skips
-# them, so the FP64 flops executed are 127 per evaluated face plus the
-# divergence / RK part per cell.
+# HLL flux); a face whose flux is reused (a run of equal cells) skips them,
+# so the FP64 flops executed are 127 per evaluated face plus the rest per cell.
 FLOPS_FACE = 127
-FLOPS_PRIM = 12          # per ghosted cell
+FLOPS_PRIM = 12          # per cell converted to primitives
 FLOPS_DT = 23            # per interior cell
+# The fused substep per cell and launch, besides its faces: the primitives of
+# the cell and of its share of the tile's two-cell halo (32 x 8 tiles: 1.69
+# conversions per cell), the divergence (40) and the RK combine (average 10).
+FLOPS_FUSED_CELL = round(FLOPS_PRIM * (36 * 12) / (32 * 8)) + 40 + 10
 # Algorithmic HBM bytes per zone-update for a fused step with in-place
 # stage 2: stage 1 reads U^n, writes U^1 (80 B); stage 2 reads U^1, U^n and
 # writes U^{n+1} (120 B).
 BYTES_PER_ZONE_UPDATE = 200
-# DRAM bytes (read + write) per sweep launch, mean of the x, y and z sweeps of
-# the FP64-FMA build at 256^3 (lines in 10 segments, stage-1 z sweep with its
-# unchanged-cell flags) from one ncu capture
-# (profiles/k_sweep_fp64_fma_oblique256.md); None for builds not captured.
-SWEEP_TRAFFIC = {"fp64_fma": 2.23e9}
-# The same for the fused FP32-bulk substep kernel (mean of stage 1 and 2, 32 x 8
-# tiles, staging ring, stage 2 with the next step's CFL maximum;
-# profiles/k_stage32_fp32_oblique256.md).
-FUSED_TRAFFIC = 1.72e9
+# DRAM bytes (read + write) per launch of the fused kernels at 256^3 (mean of
+# stage 1 and 2) from ncu captures of the current kernels; None where no
+# capture of the current kernel exists.
+FUSED_TRAFFIC = {"fp64_fma": None, "fp64": None, "fp32_bulk": None}
 
 
 def fp64_probe():
@@ -429,6 +426,33 @@ def run_shear(args, dev):
                     "CFL steps, so the two end times agree to the dt difference"}
 
 
+def _fused_roofline(prof, faces, zones, bytes_per_launch_cell, peak_tflops, hbm, flops):
+    """The fused substep kernel's figures: FP64 flops executed per launch
+    (FLOPS_FACE per evaluated face + FLOPS_FUSED_CELL per cell) against the
+    FP64 peak, and its algorithmic HBM bytes against the copy bandwidth."""
+    ms, launches = prof["fused"]
+    launches = max(launches, 1)
+    evaluated, defined = faces
+    sec = ms / 1e3
+    out = {"kernel_ms": ms, "launches": launches, "avg_launch_ms": ms / launches,
+           "faces_evaluated": evaluated, "faces_defined": defined,
+           "faces_evaluated_fraction": evaluated / max(defined, 1)}
+    b = bytes_per_launch_cell * zones
+    out["hbm"] = {"achieved": b * launches / sec / 1e9 if sec > 0 else None, "peak": hbm,
+                  "unit": "GB/s", "bytes_per_launch": b,
+                  "frac": b * launches / sec / 1e9 / hbm if sec > 0 else None}
+    if flops:
+        executed = evaluated * FLOPS_FACE + FLOPS_FUSED_CELL * zones * launches
+        method = defined * FLOPS_FACE + FLOPS_FUSED_CELL * zones * launches
+        out["alu"] = {"achieved": executed / sec / 1e12 if sec > 0 else None,
+                      "peak": peak_tflops, "unit": "TFLOP/s",
+                      "frac": executed / sec / 1e12 / peak_tflops if sec > 0 else None,
+                      "flops_per_launch": executed / launches,
+                      "method_flops_per_launch": method / launches,
+                      "effective_tflops": method / sec / 1e12 if sec > 0 else None}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -440,6 +464,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     probe = fp64_probe() if rank == 0 else None
     dev = torch.device("cuda", local)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     n = args.n
     zones = n ** 3
     U0 = problems.riemann_oblique(n, n, n)
@@ -474,38 +499,54 @@ def run_ours(args):
            "steps": args.e2e_steps}
     m.close()
 
-    # the other arithmetic variants of the same step, fewer steps each
+    peaks = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    derived_peak = DFMA_PER_SM_CLK * 2.0 * sms * sm_max * 1e6 / 1e12     # TFLOP/s
+    if probe and probe.get("dfma_per_s"):
+        fp64_peak = 2.0 * probe["dfma_per_s"] / 1e12
+        peak_source = ("FP64 peak measured live by paper_1812_07977_gb300/_build/fp64_probe "
+                       "(DFMA rate x 2 flops), of measured")
+    else:
+        fp64_peak = derived_peak
+        peak_source = (f"FP64 issue rate 2 DFMA/SM/clk x {sms} SMs x {sm_max:.0f} MHz "
+                       "(MEASURED_PEAKS sm_max_mhz)")
+
+    def variant(prec, U0v, nsteps, bc=("outflow",) * 3):
+        U0v_dev = torch.from_numpy(U0v).to(dev) if isinstance(U0v, np.ndarray) else U0v
+        mv = Mesh(n, n, n, precision=prec, bc=bc)
+        vms_max, _, vprof, _, vfaces = _timed_run(mv, U0v_dev, nsteps, args.warmup, world, dev,
+                                                  rank, False)
+        mv.close()
+        vval = world * zones * nsteps / (vms_max / 1e3)
+        out = {"value": vval, "unit": "zone-updates/s", "ms_per_step": vms_max / nsteps,
+               "steps": nsteps,
+               "kernel_ms_per_step": {c: v[0] / nsteps for c, v in vprof.items()},
+               "faces_evaluated_fraction": vfaces[0] / max(vfaces[1], 1),
+               "hbm_roofline_whole_step": {
+                   "achieved": BYTES_PER_ZONE_UPDATE * vval / 1e9, "peak": hbm, "unit": "GB/s",
+                   "frac": BYTES_PER_ZONE_UPDATE * vval / 1e9 / hbm}}
+        if vprof["fused"][1] > 0:
+            out["fused_kernel"] = _fused_roofline(vprof, vfaces, zones, 100, fp64_peak, hbm,
+                                                  prec != "fp32_bulk")
+        return out
+
+    # the other arithmetic variants on the same workload, fewer steps each,
+    # and every variant on a state with no equal neighbours (a seeded smooth
+    # periodic 256^3 state: every face evaluated, nothing reused)
     variants = {}
     for prec in args.variants:
-        if prec == args.precision:
-            continue
-        mv = Mesh(n, n, n, precision=prec)
-        vms_max, _, vprof, _, vfaces = _timed_run(mv, U0_dev, args.variant_steps, args.warmup,
-                                                  world, dev, rank, False)
-        mv.close()
-        vval = world * zones * args.variant_steps / (vms_max / 1e3)
-        variants[prec] = {"value": vval, "unit": "zone-updates/s",
-                          "ms_per_step": vms_max / args.variant_steps,
-                          "steps": args.variant_steps,
-                          "kernel_ms_per_step": {c: v[0] / args.variant_steps
-                                                 for c, v in vprof.items()},
-                          "faces_evaluated_fraction": vfaces[0] / max(vfaces[1], 1)}
-        if prec == "fp32_bulk":
-            hbm = float(_peaks().get("hbm_gbs", 6800.0))
-            fused_ms = vprof["fused"][0]
-            fused_launches = max(vprof["fused"][1], 1)
-            # fused substep kernel: stage 1 moves 80 B, stage 2 120 B per cell
-            fused_bytes = 100 * zones * fused_launches
-            variants[prec]["roofline"] = {
-                "bound": "hbm", "kernel": "k_stage32 (fused substep)",
-                "achieved": fused_bytes / (fused_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                "frac": fused_bytes / (fused_ms / 1e3) / 1e9 / hbm,
-                "avg_launch_ms": fused_ms / fused_launches,
-                "bytes_per_launch": 100 * zones,
-                "traffic": FUSED_TRAFFIC if n == N else None}
-            variants[prec]["hbm_roofline_whole_step"] = {
-                "achieved": BYTES_PER_ZONE_UPDATE * vval / 1e9, "peak": hbm, "unit": "GB/s",
-                "frac": BYTES_PER_ZONE_UPDATE * vval / 1e9 / hbm}
+        if prec != args.precision:
+            variants[prec] = variant(prec, U0, args.variant_steps)
+    if args.noreuse_steps > 0:
+        smooth = problems.random_smooth_periodic(n, n, n, seed=12345)
+        for prec in [args.precision] + [p for p in args.variants if p != args.precision]:
+            variants[prec + "_no_reuse"] = variant(prec, smooth, args.noreuse_steps,
+                                                   bc=("periodic",) * 3)
+            variants[prec + "_no_reuse"]["workload"] = (
+                "seeded smooth periodic 256^3 state (3 random Fourier modes per field, rho and "
+                "p within 20% of 1, |v| <= 0.5): no two neighbouring cells equal")
+        del smooth
 
     if args.batch_steps > 0:
         variants["batched_fp32"] = run_batched(args, world, dev, rank)
@@ -517,47 +558,28 @@ def run_ours(args):
     if rank != 0:
         return 0
 
-    # roofline of the dominant kernel class (the three sweeps)
-    peaks = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    derived_peak = DFMA_PER_SM_CLK * 2.0 * SM_COUNT * sm_max * 1e6 / 1e12     # TFLOP/s
-    if probe and probe.get("dfma_per_s"):
-        fp64_peak = 2.0 * probe["dfma_per_s"] / 1e12
-        peak_source = ("FP64 peak measured live by paper_1812_07977_gb300/_build/fp64_probe "
-                       "(DFMA rate x 2 flops), of measured")
-    else:
-        fp64_peak = derived_peak
-        peak_source = ("FP64 issue rate 2 DFMA/SM/clk x 152 SMs x "
-                       f"{sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz)")
-    sweep_ms = sum(prof[c][0] for c in FLOPS_SWEEP)
-    sweep_launches = sum(prof[c][1] for c in FLOPS_SWEEP)
-    # the method's flops (every face evaluated) and the flops executed (faces
-    # whose flux was reused skip FLOPS_FACE each)
-    sweep_flops = sum(FLOPS_SWEEP[c] * zones * prof[c][1] for c in FLOPS_SWEEP)
-    evaluated, defined = faces
-    executed_flops = evaluated * FLOPS_FACE + sum(
-        (FLOPS_SWEEP[c] - FLOPS_FACE) * zones * prof[c][1] for c in FLOPS_SWEEP)
-    achieved = executed_flops / (sweep_ms / 1e3) / 1e12 if sweep_ms > 0 else None
-    effective = sweep_flops / (sweep_ms / 1e3) / 1e12 if sweep_ms > 0 else None
-    roofline = {"bound": "alu", "kernel": "k_sweep (x, y, z)", "achieved": achieved,
-                "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak if achieved else None,
-                "traffic": args.traffic if args.traffic else
-                (SWEEP_TRAFFIC.get(args.precision) if n == N else None),
-                "peak_source": peak_source, "derived_peak": derived_peak,
-                "flops_per_launch": executed_flops / max(sweep_launches, 1),
-                "avg_launch_ms": sweep_ms / max(sweep_launches, 1),
-                "flops": "FP64 flops executed: 127 per evaluated face + the divergence and RK "
-                         "part per cell",
-                "faces_evaluated": evaluated, "faces_defined": defined,
-                "faces_evaluated_fraction": evaluated / max(defined, 1),
-                "method_flops_per_launch": sweep_flops / max(sweep_launches, 1),
-                "effective_tflops": effective}
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
     hbm_achieved = BYTES_PER_ZONE_UPDATE * zones * args.steps / (ms / 1e3) / 1e9
     launches = sum(v[1] for v in prof.values())
-    total_flops_step = (sum(FLOPS_SWEEP.values()) * 2 + FLOPS_DT) * zones + \
-        2 * FLOPS_PRIM * (n + 4) ** 3
+    fused = _fused_roofline(prof, faces, zones, 100, fp64_peak, hbm, True)
+    alu = fused["alu"]
+    traffic = args.traffic if args.traffic else (FUSED_TRAFFIC.get(args.precision)
+                                                 if n == N else None)
+    roofline = {"bound": "alu", "kernel": "k_stage64 (fused FP64 substep)",
+                "achieved": alu["achieved"], "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": alu["frac"], "traffic": traffic,
+                "traffic_note": "DRAM bytes per launch from an ncu capture of this kernel "
+                                "(null: no capture of the current kernel)",
+                "peak_source": peak_source, "derived_peak": derived_peak,
+                "avg_launch_ms": fused["avg_launch_ms"],
+                "flops": f"FP64 flops executed: {FLOPS_FACE} per evaluated face + "
+                         f"{FLOPS_FUSED_CELL} per cell and launch",
+                "flops_per_launch": alu["flops_per_launch"],
+                "method_flops_per_launch": alu["method_flops_per_launch"],
+                "effective_tflops": alu["effective_tflops"],
+                "faces_evaluated": fused["faces_evaluated"],
+                "faces_defined": fused["faces_defined"],
+                "faces_evaluated_fraction": fused["faces_evaluated_fraction"],
+                "hbm_view": fused["hbm"]}
     line = {
         "metric": METRIC, "value": value, "unit": "zone-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -566,14 +588,13 @@ def run_ours(args):
         "config": {"workload": "oblique Riemann problem 256^3 (Sod states, plane normal "
                                "(1,1,1), gamma 1.4, outflow, CFL 0.4), steps 1..K",
                    "precision": args.precision, "cells": zones,
-                   "l2": "inputs larger than L2 (0.70 GB per ghosted state, 2.8 GB resident)",
+                   "l2": "inputs larger than L2 (0.70 GB per ghosted state, 1.4 GB resident)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roofline,
         "hbm_roofline": {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm, "unit": "GB/s",
                          "frac": hbm_achieved / hbm,
                          "bytes_per_zone_update": BYTES_PER_ZONE_UPDATE,
                          "note": "whole step vs the algorithmic minimum traffic, of measured"},
-        "method_flop_rate_whole_step_tflops": total_flops_step * args.steps / (ms / 1e3) / 1e12,
         "kernel_ms_per_step": {c: v[0] / args.steps for c, v in prof.items()},
         "variants": variants,
         "gpu_launches": launches,
@@ -599,6 +620,9 @@ def main():
     ap.add_argument("--variants", nargs="*", default=["fp64", "fp32_bulk"],
                     help="other precisions timed beside the headline one")
     ap.add_argument("--variant-steps", type=int, default=50)
+    ap.add_argument("--noreuse-steps", type=int, default=10,
+                    help="steps of each precision on a 256^3 state without equal neighbours "
+                         "(0: skip)")
     ap.add_argument("--batch-steps", type=int, default=50,
                     help="steps of the 96-mesh batched workload (0: skip)")
     ap.add_argument("--learned-epochs", type=int, default=16,
@@ -614,7 +638,7 @@ def main():
     ap.add_argument("--n", type=int, default=N)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--traffic", type=float, default=None,
-                    help="DRAM bytes per sweep launch from an ncu capture of this kernel")
+                    help="DRAM bytes per fused-kernel launch from an ncu capture of it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -199,7 +199,7 @@ typedef enum {
   FV_KERNEL_SWEEP_X = 1,  /* differences, reconstruction, HLL fluxes, update: x */
   FV_KERNEL_SWEEP_Y = 2,  /* the same along y */
   FV_KERNEL_SWEEP_Z = 3,  /* the same along z, with the RK combine */
-  FV_KERNEL_FUSED = 4,    /* the whole substep in one kernel (FP32-bulk path) */
+  FV_KERNEL_FUSED = 4,    /* the whole substep in one kernel (fused paths) */
   FV_KERNEL_GHOST = 5,    /* ghost fill */
   FV_KERNEL_DT = 6,       /* CFL time-step reduction */
   FV_KERNEL_OTHER = 7,    /* state copies and conservation sums */
@@ -385,8 +385,9 @@ FV_API fv_status fv_conserved_sums_noalloc(const double* U, int nx, int ny, int 
                                            void* cuda_stream, double out[5]);
 
 /* Tuning knobs (not part of the paper).
- *  FV_TUNE_KCHUNK        z planes per CTA of the fused FP32-bulk kernel
- *                        (integer >= 1; default 32, or nz when nz < 64)
+ *  FV_TUNE_KCHUNK        z planes per CTA of the fused kernels (FP32-bulk
+ *                        and FP64; integer >= 1; default 32, or nz when
+ *                        nz < 64)
  *  FV_TUNE_VACUUM_RATIO  FP32-bulk: recover the pressure in FP64 where the
  *                        kinetic energy exceeds this fraction of E (default
  *                        0.99; a value > 1 turns the recovery off)
@@ -396,20 +397,28 @@ FV_API fv_status fv_conserved_sums_noalloc(const double* U, int nx, int ny, int 
  *  FV_TUNE_TILE_Y        tile height of the fused FP32-bulk kernel: 4, 8
  *                        (default) or 16 (tiles of 32 x 4 / 8 / 16 columns,
  *                        CTAs of 128 / 256 / 512 threads); the same bits
- *  FV_TUNE_SWEEP_SEGMENTS  FP64 paths: pieces each grid line of a sweep is
+ *  FV_TUNE_SWEEP_SEGMENTS  FP64 sweeps: pieces each grid line of a sweep is
  *                        cut into, to run more, shorter work items (integer
  *                        in [0, 4096], capped at the line's length; 0, the
  *                        default, picks by mesh size).  The results are the
  *                        same bits for every value; each extra piece
  *                        evaluates one face flux twice, which
  *                        fv_get_face_counts counts.
+ *  FV_TUNE_FP64_FUSED    FP64 paths: 1 (default) runs each substep as one
+ *                        fused kernel over tiles of 32 x 8 columns and z
+ *                        chunks of FV_TUNE_KCHUNK planes, with the next
+ *                        step's CFL maximum taken by stage 2; 0 runs the
+ *                        per-axis passes (primitives, then x, y and z line
+ *                        sweeps).  Both give the same bits.  Not between
+ *                        the two substeps.
  * Errors: INVALID_ARG for an unknown key or a value out of range. */
 typedef enum {
   FV_TUNE_KCHUNK = 0,
   FV_TUNE_VACUUM_RATIO = 1,
   FV_TUNE_OCCUPANCY = 2,
   FV_TUNE_SWEEP_SEGMENTS = 3,
-  FV_TUNE_TILE_Y = 4
+  FV_TUNE_TILE_Y = 4,
+  FV_TUNE_FP64_FUSED = 5
 } fv_tuning_key;
 FV_API fv_status fv_set_tuning(fv_mesh_t m, int key, double value);
 

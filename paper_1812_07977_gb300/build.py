@@ -31,6 +31,9 @@ UNITS = [
     ("fv_step_fp64_exact.o", "fv_step_kernels.cu", ["--fmad=false", "-DFV_NS=fv_fp64_exact"]),
     ("fv_step_fp64_fma.o", "fv_step_kernels.cu", ["--fmad=true", "-DFV_NS=fv_fp64_fma",
                                                          "-DFV_NEWTON_DIVSQRT"]),
+    ("fv_fused64_exact.o", "fv_fused64_kernels.cu", ["--fmad=false", "-DFV_NS=fv_fp64_exact"]),
+    ("fv_fused64_fma.o", "fv_fused64_kernels.cu", ["--fmad=true", "-DFV_NS=fv_fp64_fma",
+                                                   "-DFV_NEWTON_DIVSQRT"]),
     ("fv_step_fp32.o", "fv_step32_kernels.cu", ["--fmad=false"]),
     ("fv_aux.o", "fv_aux.cu", ["--fmad=false"]),
     ("fv_core.o", "fv_core.cu", ["--fmad=false"]),

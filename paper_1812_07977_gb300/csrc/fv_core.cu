@@ -62,8 +62,9 @@ struct fv_mesh_s {
   int occupancy;            // CTAs per SM the fused kernel is compiled for (2 or 3)
   int tile_y;               // tile height of the fused kernel (4, 8 or 16)
   int segments;             // pieces per grid line of the FP64 sweeps (0: automatic)
-  bool w_current;           // FP64: W holds the primitives of U (from the dt pass)
-  bool smax_current;        // FP32-bulk: ctr->smax_next is the CFL maximum of U
+  bool fused64;             // FP64: one fused kernel per substep (else the per-axis sweeps)
+  bool w_current;           // FP64 sweeps: W holds the primitives of U (from the dt pass)
+  bool smax_current;        // fused paths: ctr->smax_next is the CFL maximum of U
   // profiling
   bool prof_on;
   std::vector<cudaEvent_t> event_pool;
@@ -248,6 +249,26 @@ long long faces_normal_to(const fvd::Params& P, int axis) {
 
 cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
   for (int axis = 0; axis < 3; ++axis) m->faces_defined += faces_normal_to(m->P, axis);
+  const bool fma = m->desc.precision == FV_PREC_FP64_FMA;
+  if (m->desc.precision != FV_PREC_FP32_BULK && m->fused64) {
+    // one kernel per substep; stage 2 also takes the CFL maximum of its output
+    m->smax_current = false;
+    m->w_current = false;
+    cudaError_t e = cudaSuccess;
+    if (stage == 2)
+      e = cudaMemsetAsync(&m->buf.ctr->smax_next, 0, sizeof(unsigned long long), m->stream);
+    if (e == cudaSuccess)
+      e = timed(m, FV_KERNEL_FUSED, 1, [&] {
+        return fma ? fv_fp64_fma::launch_fused(stage, m->buf, m->P, dt, m->kchunk, m->stream)
+                   : fv_fp64_exact::launch_fused(stage, m->buf, m->P, dt, m->kchunk,
+                                                 m->stream);
+      });
+    if (e != cudaSuccess) return e;
+    double* dst = stage == 1 ? m->buf.U1 : m->buf.U;
+    e = timed(m, FV_KERNEL_GHOST, 1, [&] { return launch_fill_ghosts(dst, m->P, m->stream); });
+    m->smax_current = e == cudaSuccess && stage == 2;
+    return e;
+  }
   if (m->desc.precision == FV_PREC_FP32_BULK) {
     // stage 2 also takes the CFL maximum of its output (the next dt's)
     m->smax_current = false;
@@ -265,7 +286,6 @@ cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
     m->smax_current = e == cudaSuccess && stage == 2;
     return e;
   }
-  const bool fma = m->desc.precision == FV_PREC_FP64_FMA;
   const double* src = stage == 1 ? m->buf.U : m->buf.U1;
   cudaError_t e = cudaSuccess;
   // the dt pass since the state last changed left U's primitives in W
@@ -318,6 +338,7 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   m->occupancy = 2;
   m->tile_y = 8;
   m->segments = 0;
+  m->fused64 = true;
   m->w_current = false;
   m->smax_current = false;
   for (int c = 0; c < FV_KERNEL_NCLASS; ++c) m->launches[c] = 0;
@@ -326,6 +347,9 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device);
   if (e == cudaSuccess && desc->precision == FV_PREC_FP32_BULK) e = fv_fp32::prepare_kernels();
+  if (e == cudaSuccess && desc->precision != FV_PREC_FP32_BULK)
+    e = desc->precision == FV_PREC_FP64_FMA ? fv_fp64_fma::prepare_fused()
+                                            : fv_fp64_exact::prepare_fused();
   if (e != cudaSuccess) {
     delete m;
     return cuda_fail(e, "cudaGetDevice");
@@ -464,18 +488,22 @@ fv_status fv_reduce_dt(fv_mesh_t m, double cfl, double* dt_out) {
   }
   DeviceGuard g(m->device);
   const bool fp32 = m->desc.precision == FV_PREC_FP32_BULK;
-  // FP32-bulk: the last stage 2 took the maximum of the current state
-  const bool cached = fp32 && m->smax_current;
+  const bool fma = m->desc.precision == FV_PREC_FP64_FMA;
+  const bool fused = fp32 || m->fused64;
+  // fused paths: the last stage 2 took the maximum of the current state
+  const bool cached = fused && m->smax_current;
   if (!cached) {
     cudaError_t e = timed(m, FV_KERNEL_DT, 1, [&] {
-      return fp32 ? fv_fp32::launch_reduce_dt(m->buf.U, m->P, m->vacuum_ratio, m->buf.ctr,
-                                              m->stream)
-             : m->desc.precision == FV_PREC_FP64_FMA
-                 ? fv_fp64_fma::launch_prim_dt(m->buf.U, m->buf, m->P, m->stream)
+      if (fp32)
+        return fv_fp32::launch_reduce_dt(m->buf.U, m->P, m->vacuum_ratio, m->buf.ctr, m->stream);
+      if (m->fused64)
+        return fma ? fv_fp64_fma::launch_dt(m->buf.U, m->buf, m->P, m->stream)
+                   : fv_fp64_exact::launch_dt(m->buf.U, m->buf, m->P, m->stream);
+      return fma ? fv_fp64_fma::launch_prim_dt(m->buf.U, m->buf, m->P, m->stream)
                  : fv_fp64_exact::launch_prim_dt(m->buf.U, m->buf, m->P, m->stream);
     });
     if (e != cudaSuccess) return cuda_fail(e, "time-step kernel");
-    m->w_current = !fp32;
+    m->w_current = !fused;
   }
   if ((st = read_counters(m)) != FV_OK) return st;
   double smax;
@@ -610,6 +638,20 @@ fv_status fv_set_tuning(fv_mesh_t m, int key, double value) {
       return FV_ERR_INVALID_ARG;
     }
     m->tile_y = (int)value;
+    return FV_OK;
+  }
+  if (key == FV_TUNE_FP64_FUSED) {
+    if (value != 0.0 && value != 1.0) {
+      set_error("FV_TUNE_FP64_FUSED must be 0 or 1 (got %g)", value);
+      return FV_ERR_INVALID_ARG;
+    }
+    if (m->stage_pending) {
+      set_error("FV_TUNE_FP64_FUSED changed between the two RK substeps");
+      return FV_ERR_INVALID_ARG;
+    }
+    m->fused64 = value != 0.0;
+    m->w_current = false;
+    m->smax_current = false;
     return FV_OK;
   }
   if (key == FV_TUNE_SWEEP_SEGMENTS) {

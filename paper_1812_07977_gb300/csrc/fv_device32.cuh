@@ -90,8 +90,8 @@ struct Params32 {
   float inv_d[3];
   double gm1_d;             // gamma - 1 in FP64 (near-vacuum pressure recovery)
   float vacuum_ratio;       // recover p in FP64 when kinetic / total energy > this
-  // FP32 brackets of the FP64 constants of the CFL speed (lo <= x <= hi)
-  float gm1_lo, gm1_hi, gamma_hi, inv_hi[3];
+  // FP32 upper bounds of the FP64 constants of the CFL speed
+  float gm1_hi, gamma_hi, inv_hi[3];
 };
 
 // p = (gamma-1)(E - |m|^2 / (2 rho)) in FP64, rounded to float.
@@ -201,82 +201,107 @@ __device__ __forceinline__ void hll_flux(const Prim32& wl, const Prim32& wr, con
 }
 
 // ---------------------------------------------------------------- CFL bound
-// |x| rounded down (lo) and up (hi) to FP32, on the integer pipe; `ok` is
-// cleared unless x is +-0 or 2^-100 <= |x| < 2^100.
-__device__ __forceinline__ void f32_bracket(double x, float& lo, float& hi, bool& ok) {
-  const unsigned h = (unsigned)__double2hiint(x) & 0x7FFFFFFFu, l = (unsigned)__double2loint(x);
-  if ((h | l) == 0u) {
-    lo = hi = 0.0f;
-    return;
-  }
-  const unsigned e = h >> 20;
-  ok = ok && e - (1023u - 100u) < 200u;
-  const unsigned f = ((e - 896u) << 23) | ((h & 0x000FFFFFu) << 3) | (l >> 29);
-  lo = __uint_as_float(f);
-  hi = __uint_as_float(f + ((l & 0x1FFFFFFFu) != 0u ? 1u : 0u));
-}
-
 // An upper bound, in FP32, of the FP64 CFL signal speed that fvd::cell_speed
 // computes (IEEE operations) for a cell of conserved state u, and whether
-// the cell is certainly physical (rho > 0 and p > 0 in FP64): interval
-// arithmetic with directed rounding on FP32 brackets of the inputs, so every
-// bound holds the exact real value of its quantity.  The FP64 evaluation is
-// within a few 2^-53 (relative) of those values in its velocities, sound
-// speed and sum, and within a few 2^-53 (E + ke) in its pressure, which the
-// absolute margin 2^-48 (E + ke) on p and the final factor 1 + 2^-20 cover.
-// Returns +inf (sure = false) when an input is outside [2^-100, 2^100), rho
+// the cell is certainly physical (rho > 0 and p > 0 in FP64).  The inputs
+// are truncated to FP32 (relative error below 2^-23), the reciprocal and
+// inverse square root are the SFU approximations (relative error below
+// 2^-22, the PTX ISA's bounds for rcp.approx and rsqrt.approx), and each
+// other FP32 operation rounds to nearest (2^-24): the FP32 velocity, kinetic
+// energy and sound speed are within 2^-19 of the exact values of the FP64
+// state, and E - ke within 2^-19 (E + ke), which an explicit margin of
+// 2^-18 (E + ke) on the pressure covers (with the FP64 evaluation's own
+// errors, a few 2^-53).  The final factor 1 + 2^-16 covers the relative
+// errors, so the bound holds for any state inside the operand range.
+// Returns +inf (sure = false) when an input is outside [2^-100, 2^101), rho
 // or E is not positive, or p could be <= 0.
 __device__ __forceinline__ float speed_upper(const double u[NF], const Params32& Q, bool& sure) {
   const float kInf = __int_as_float(0x7F800000);
   sure = false;
-  bool ok = (__double2hiint(u[0]) | __double2hiint(u[4])) >= 0;   // rho, E not negative
-  float r_lo, r_hi, e_lo, e_hi, m_lo[3], m_hi[3];
-  f32_bracket(u[0], r_lo, r_hi, ok);
-  f32_bracket(u[4], e_lo, e_hi, ok);
-#pragma unroll
-  for (int d = 0; d < 3; ++d) f32_bracket(u[1 + d], m_lo[d], m_hi[d], ok);
-  if (!ok || !(r_lo > 0.0f) || !(e_lo > 0.0f)) return kInf;
-  float v_hi[3], ke_lo = 0.0f, ke_hi = 0.0f;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    v_hi[d] = __fdiv_ru(m_hi[d], r_lo);
-    ke_lo = __fadd_rd(ke_lo, __fdiv_rd(__fmul_rd(m_lo[d], m_lo[d]), r_hi));
-    ke_hi = __fadd_ru(ke_hi, __fmul_ru(m_hi[d], v_hi[d]));
-  }
-  ke_lo = __fmul_rd(ke_lo, 0.5f);
-  ke_hi = __fmul_ru(ke_hi, 0.5f);
-  const float margin = __fmul_ru(Q.gm1_hi, __fmul_ru(__fadd_ru(e_hi, ke_hi), 0x1p-48f));
-  const float p_hi = __fadd_ru(__fmul_ru(Q.gm1_hi, __fsub_ru(e_hi, ke_lo)), margin);
-  const float p_lo = __fsub_rd(__fmul_rd(Q.gm1_lo, __fsub_rd(e_lo, ke_hi)), margin);
-  if (!(p_lo > 0.0f) || !(p_hi < kInf)) return kInf;
+  bool ok = true;
+  const float r = fvd::trunc_f32(u[0], ok), E = fvd::trunc_f32(u[4], ok);
+  const float mx = fabsf(fvd::trunc_f32(u[1], ok)), my = fabsf(fvd::trunc_f32(u[2], ok)),
+              mz = fabsf(fvd::trunc_f32(u[3], ok));
+  if (!ok || !(r > 0.0f) || !(E > 0.0f)) return kInf;
+  const float ir = rcp(r);
+  const float vx = __fmul_rn(mx, ir), vy = __fmul_rn(my, ir), vz = __fmul_rn(mz, ir);
+  const float ke = __fmul_rn(0.5f, __fadd_rn(__fadd_rn(__fmul_rn(mx, vx), __fmul_rn(my, vy)),
+                                              __fmul_rn(mz, vz)));
+  const float margin = __fmul_rn(0x1p-18f, __fadd_rn(E, ke));
+  const float pm = __fsub_rn(E, ke);
+  if (!(__fsub_rn(pm, margin) > 0.0f)) return kInf;
   sure = true;
-  const float c = __fsqrt_ru(__fdiv_ru(__fmul_ru(Q.gamma_hi, p_hi), r_lo));
-  const float sp = __fadd_ru(__fadd_ru(__fmul_ru(__fadd_ru(v_hi[0], c), Q.inv_hi[0]),
-                                       __fmul_ru(__fadd_ru(v_hi[1], c), Q.inv_hi[1])),
-                             __fmul_ru(__fadd_ru(v_hi[2], c), Q.inv_hi[2]));
-  return __fmul_ru(sp, 1.0f + 0x1p-20f);
+  const float c2 = __fmul_rn(__fmul_rn(Q.gamma_hi, __fadd_rn(pm, margin)), __fmul_rn(Q.gm1_hi, ir));
+  const float c = __fmul_rn(c2, rsqrtf(c2));
+  const float sp = __fadd_rn(__fadd_rn(__fmul_rn(__fadd_rn(vx, c), Q.inv_hi[0]),
+                                       __fmul_rn(__fadd_rn(vy, c), Q.inv_hi[1])),
+                             __fmul_rn(__fadd_rn(vz, c), Q.inv_hi[2]));
+  return __fmul_rn(sp, 1.0f + 0x1p-16f);
 }
 
-// Folds one cell's FP64 CFL speed (fvd::cell_speed, IEEE operations) into a
-// running maximum smax (with smax_f <= smax as a float), and counts the
-// cell in `bad` if its FP64 primitives are non-physical.  The FP64 speed is
-// computed only when the FP32 bound could raise the maximum or the cell is
-// not certainly physical: the maximum and the count are the bits and the
-// number that evaluating every cell gives.
+// The last cell a thread folded (fold_speed): its state and whether it was
+// non-physical.  A cell equal to it bit for bit changes neither the maximum
+// nor anything but the count -- the usual case in uniform regions, where
+// the FP32 bound of an equal speed would not exclude it.
+struct SpeedCache {
+  double u[NF];
+  unsigned bad;
+  bool valid;
+};
+
+// Running maximum of FP64 CFL speeds shared by a whole launch: *gmax holds the
+// bits of the largest speed any thread has computed so far (non-negative
+// doubles order like their bits), so it is a lower bound of the final
+// maximum at every moment, and any cell whose FP32 bound is below it cannot
+// change the result.  refresh_max raises a thread's threshold (smax, and
+// smax_f <= smax as a float) to the shared value.
+__device__ __forceinline__ void set_threshold(double s, double& smax, float& smax_f) {
+  smax = s;
+  bool in = true;
+  const float t = fvd::trunc_f32(s, in);
+  smax_f = in ? t : (s > 1.0 ? 0x1p100f : 0.0f);
+}
+
+__device__ __forceinline__ void refresh_max(const unsigned long long* gmax, double& smax,
+                                            float& smax_f) {
+  const unsigned long long g = *(const volatile unsigned long long*)gmax;
+  if (g > (unsigned long long)__double_as_longlong(smax))
+    set_threshold(__longlong_as_double((long long)g), smax, smax_f);
+}
+
+// Folds one cell's FP64 CFL speed (fvd::cell_speed, IEEE operations) into the
+// shared maximum *gmax, and counts the cell in `bad` if its FP64 primitives
+// are non-physical.  The FP64 speed is computed only when the cell differs
+// from the thread's last one and its FP32 bound could reach the threshold
+// smax (a speed already computed) or it is not certainly physical: the
+// maximum and the count are the bits and the number that evaluating every
+// cell gives.
 __device__ __forceinline__ void fold_speed(const double u[NF], const fvd::Params& P,
                                            const Params32& Q, double& smax, float& smax_f,
-                                           unsigned long long& bad) {
+                                           unsigned long long& bad, SpeedCache& cache,
+                                           unsigned long long* gmax) {
+  bool eq = cache.valid;
+#pragma unroll
+  for (int q = 0; q < NF; ++q) {
+    eq = eq && __double_as_longlong(u[q]) == __double_as_longlong(cache.u[q]);
+    cache.u[q] = u[q];
+  }
+  if (eq) {
+    bad += cache.bad;
+    return;
+  }
+  cache.valid = true;
+  cache.bad = 0;
   bool sure;
   const float ub = speed_upper(u, Q, sure);
   if (sure && ub < smax_f) return;
   const fvd::Prim w = fvd::cons_to_prim(u, P);
-  if (!(fvd::is_pos(w.r) && fvd::is_pos(w.p))) ++bad;
+  cache.bad = !(fvd::is_pos(w.r) && fvd::is_pos(w.p));
+  bad += cache.bad;
   const double s = fvd::cell_speed(w, P);
   if (s > smax) {
-    smax = s;
-    bool in = true;
-    const float t = fvd::trunc_f32(smax, in);
-    smax_f = in ? t : (smax > 1.0 ? 0x1p100f : 0.0f);
+    set_threshold(s, smax, smax_f);
+    atomicMax(gmax, (unsigned long long)__double_as_longlong(s));
   }
 }
 

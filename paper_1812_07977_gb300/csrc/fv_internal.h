@@ -47,6 +47,13 @@ struct StepBuffers {
 // launch_prim_dt: the CFL maximum of U into ctr->smax_bits and, in the same
 // pass, U's primitives into b.W, which a following substep 1 may use in
 // place of its launch_prim.
+// The fused form (fv_fused64_kernels.cu, the same two arithmetic variants):
+// launch_fused runs a whole substep (stage 1: U1 = U + dU(U); stage 2:
+// U = (U + U1 + dU(U1))/2 with the CFL maximum of the new U into
+// ctr->smax_next) in one kernel over tiles of 32 x 8 columns and z chunks of
+// `kchunk` planes; launch_dt takes the CFL maximum of U with the same
+// arithmetic into ctr->smax_bits; prepare_fused raises the fused kernels'
+// shared-memory limit on the current device (before their first launch).
 #define FV_DECLARE_STEP_VARIANT(ns)                                                        \
   namespace ns {                                                                           \
   cudaError_t launch_prim(const double* src, const StepBuffers& b, const fvd::Params& P,   \
@@ -55,6 +62,11 @@ struct StepBuffers {
                            double dt, int segments, int num_sms, cudaStream_t s);          \
   cudaError_t launch_prim_dt(const double* U, const StepBuffers& b, const fvd::Params& P,  \
                              cudaStream_t s);                                              \
+  cudaError_t prepare_fused();                                                             \
+  cudaError_t launch_fused(int stage, const StepBuffers& b, const fvd::Params& P,          \
+                           double dt, int kchunk, cudaStream_t s);                         \
+  cudaError_t launch_dt(const double* U, const StepBuffers& b, const fvd::Params& P,       \
+                        cudaStream_t s);                                                   \
   }
 FV_DECLARE_STEP_VARIANT(fv_fp64_exact)
 FV_DECLARE_STEP_VARIANT(fv_fp64_fma)

@@ -194,9 +194,9 @@ __device__ __forceinline__ void face_flux(const Prim32& a0, const Prim32& a1, co
 // substep (U for stage 1, U1 for stage 2) has its ghosts filled.  Counts of
 // face fallbacks and non-physical cells accumulate in the caller's counters.
 // MC: the limiter parameter is 2.  NEXT (stage 2): also the FP64 CFL speed
-// of each output cell (the next time step's), its maximum into smax_next
-// (with smax_next_f <= smax_next as a float) and its non-physical cells
-// into bad_next.
+// of each output cell (the next time step's), its maximum into *gmax (a
+// maximum shared by the launch, see fvd32::fold_speed; smax_next, smax_next_f
+// the thread's threshold) and its non-physical cells into bad_next.
 template <class S, int STAGE, bool MC, bool NEXT>
 __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
                                              double* __restrict__ U1, const fvd::Params& P,
@@ -204,7 +204,10 @@ __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
                                              int k0, int k1, unsigned& fallbacks_out,
                                              unsigned long long& bad_out, unsigned& evaluated,
                                              double& smax_next, float& smax_next_f,
-                                             unsigned long long& bad_next) {
+                                             unsigned long long& bad_next,
+                                             unsigned long long* gmax) {
+  SpeedCache speed_cache;
+  speed_cache.valid = false;
   const double* __restrict__ src = STAGE == 1 ? U : U1;
   const int tid = threadIdx.x;
   const int ti = tid % TX, tj = tid / TX;
@@ -299,6 +302,7 @@ __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
 
   for (int k = k0; k < k1; ++k) {
     if (owner && !physical(w0)) ++bad;   // each interior cell once per substep
+    if (NEXT && STAGE == 2) refresh_max(gmax, smax_next, smax_next_f);
     stage_in(k + kStageDepth);
     cp_async_wait<kStageDepth>();        // this iteration's group has landed
     const int slot = k % kRing;
@@ -417,7 +421,8 @@ __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
           U[q * nf + g] = un[q];
         }
       }
-      if (NEXT && STAGE == 2) fold_speed(un, P, Q, smax_next, smax_next_f, bad_next);
+      if (NEXT && STAGE == 2)
+        fold_speed(un, P, Q, smax_next, smax_next_f, bad_next, speed_cache, gmax);
     }
 #pragma unroll
     for (int q = 0; q < NF; ++q) fz_lo[q] = fz_hi[q];
@@ -444,7 +449,7 @@ k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params
   const int k0 = blockIdx.z * kchunk;
   stage32_tile<S, STAGE, MC, STAGE == 2>(s, U, U1, P, Q, dt, blockIdx.x * TX, blockIdx.y * TY,
                                          k0, min(k0 + kchunk, P.nz), fallbacks, bad, evaluated,
-                                         smax_next, smax_next_f, bad_next);
+                                         smax_next, smax_next_f, bad_next, &ctr->smax_next);
   if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
   if (bad) atomicAdd(&ctr->np_step, bad);
   warp_count(&ctr->faces, evaluated);
@@ -484,7 +489,7 @@ k_stage32_batch(double* __restrict__ U, double* __restrict__ U1, BatchMesh* __re
     stage32_tile<S, STAGE, MC, STAGE == 2>(s, U + m.offset, U1 + m.offset, m.P, m.Q,
                                            (float)m.dt, w.y * TX, w.z * TY, k0,
                                            min(k0 + kchunk, m.P.nz), fallbacks, bad, evaluated,
-                                           smax_next, smax_next_f, bad_next);
+                                           smax_next, smax_next_f, bad_next, &m.smax_bits);
     if (STAGE == 2) max_speed_to(&m.smax_bits, smax_next);
   }
   if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
@@ -497,13 +502,15 @@ k_stage32_batch(double* __restrict__ U, double* __restrict__ U1, BatchMesh* __re
 // maximum (fold_speed).
 __device__ __forceinline__ void fold_cell(const double* __restrict__ U, const fvd::Params& P,
                                           const Params32& Q, long long m, double& smax,
-                                          float& smax_f, unsigned long long& bad) {
+                                          float& smax_f, unsigned long long& bad,
+                                          SpeedCache& cache, unsigned long long* gmax) {
   const long long k = m / ((long long)P.nx * P.ny);
   const long long r = m - k * ((long long)P.nx * P.ny);
   const long long j = r / P.nx, i = r - j * P.nx;
   double u[NF];
   load_state(U, P.nfield, (k + 2) * P.sz + (j + 2) * P.sy + (i + 2), u);
-  fold_speed(u, P, Q, smax, smax_f, bad);
+  refresh_max(gmax, smax, smax_f);
+  fold_speed(u, P, Q, smax, smax_f, bad, cache, gmax);
 }
 
 // Block maximum of the threads' speeds (doubles >= 0), folded into *dst;
@@ -541,9 +548,11 @@ k_reduce_dt32(const double* __restrict__ U, fvd::Params P, Params32 Q, DevCounte
   double smax = 0.0;
   float smax_f = 0.0f;
   unsigned long long bad = 0;
+  SpeedCache cache;
+  cache.valid = false;
   for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < n;
        m += (long long)gridDim.x * blockDim.x)
-    fold_cell(U, P, Q, m, smax, smax_f, bad);
+    fold_cell(U, P, Q, m, smax, smax_f, bad, cache, &ctr->smax_bits);
   if (bad) atomicAdd(&ctr->np_dt, bad);
   block_max_to(&ctr->smax_bits, smax);
 }
@@ -561,8 +570,10 @@ k_batch_dt(const double* __restrict__ U, BatchMesh* __restrict__ meshes,
   double smax = 0.0;
   float smax_f = 0.0f;
   unsigned long long bad = 0;
+  SpeedCache cache;
+  cache.valid = false;
   for (long long m = lo + threadIdx.x; m < hi; m += blockDim.x)
-    fold_cell(U + mesh.offset, mesh.P, mesh.Q, m, smax, smax_f, bad);
+    fold_cell(U + mesh.offset, mesh.P, mesh.Q, m, smax, smax_f, bad, cache, &mesh.smax_bits);
   if (bad) atomicAdd(&ctr->np_dt, bad);
   block_max_to(&mesh.smax_bits, smax);
 }
@@ -612,7 +623,7 @@ Params32 make_params32(const fvd::Params& P, double vacuum_ratio) {
   Q.gm1_d = P.gm1;
   Q.vacuum_ratio = (float)vacuum_ratio;
   float lo;
-  bracket_f32(P.gm1, Q.gm1_lo, Q.gm1_hi);
+  bracket_f32(P.gm1, lo, Q.gm1_hi);
   bracket_f32(P.gamma, lo, Q.gamma_hi);
   for (int a = 0; a < 3; ++a) bracket_f32(P.inv_d[a], lo, Q.inv_hi[a]);
   return Q;

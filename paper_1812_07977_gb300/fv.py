@@ -268,7 +268,7 @@ class Mesh:
 
     def set_tuning(self, key: str, value):
         keys = {"kchunk": 0, "vacuum_ratio": 1, "occupancy": 2, "sweep_segments": 3,
-                "tile_y": 4}
+                "tile_y": 4, "fp64_fused": 5}
         _check(self._lib.fv_set_tuning(self._h, keys[key], float(value)), "fv_set_tuning")
 
     def profile(self, on: bool = True):

@@ -331,29 +331,34 @@ def test_signed_zeros_bit_for_bit():
 def test_face_counts():
     """fv_get_face_counts: the FP64 sweeps evaluate every face of a state
     without equal neighbours and reuse almost every flux of a uniform state
-    (one evaluated face per grid line and sweep); the fused FP32-bulk kernel
-    evaluates every face of the first (tile edges twice) and reuses most of
-    the second."""
+    (one evaluated face per grid line and sweep); the fused kernels (FP64 and
+    FP32-bulk) evaluate every face of the first (tile and chunk edges twice)
+    and reuse most of the second."""
     from paper_1812_07977_gb300.fv import Mesh
     n = (40, 36, 33)
     nx, ny, nz = n
     defined = 2 * ((nx + 1) * ny * nz + nx * (ny + 1) * nz + nx * ny * (nz + 1))
     lines = 2 * (ny * nz + nx * nz + nx * ny)
-    for prec in ("fp64", "fp64_fma", "fp32_bulk"):
+    for prec, fused in (("fp64", 0), ("fp64_fma", 0), ("fp64", 1), ("fp64_fma", 1),
+                        ("fp32_bulk", 1)):
         with Mesh(*n, bc=("periodic",) * 3, precision=prec) as m:
             m.set_tuning("sweep_segments", 1)
+            if prec != "fp32_bulk":
+                m.set_tuning("fp64_fused", fused)
             m.set_state(problems.random_smooth_periodic(*n, seed=9))
             m.step(m.reduce_dt(0.4))
             ev, de = m.face_counts()
             assert de == defined
-            assert (ev == de) if prec != "fp32_bulk" else (ev >= de)
+            assert (ev == de) if not fused else (ev >= de)
         with Mesh(*n, precision=prec) as m:
             m.set_tuning("sweep_segments", 1)
+            if prec != "fp32_bulk":
+                m.set_tuning("fp64_fused", fused)
             m.set_state(problems.uniform(*n, 1.0, (0.3, 0.2, 0.1), 1.0))
             m.step(m.reduce_dt(0.4))
             ev, de = m.face_counts()
             assert de == defined
-            assert (ev == lines) if prec != "fp32_bulk" else (ev < de // 4)
+            assert (ev == lines) if not fused else (ev < de // 4)
             m.set_state(problems.uniform(*n, 1.0, (0.3, 0.2, 0.1), 1.0))
             assert m.face_counts() == (0, 0)
 
@@ -373,6 +378,7 @@ def test_sweep_segments_bitwise_and_counted(segments):
     n = (33, 17, 29)
     U0 = problems.riemann_oblique(*n)
     om, Uo, m = _pair(*n, U0)
+    m.set_tuning("fp64_fused", 0)
     m.set_tuning("sweep_segments", segments)
     _run_both(om, Uo, m, 4)
     got = m.get_state().cpu().numpy()
@@ -381,6 +387,7 @@ def test_sweep_segments_bitwise_and_counted(segments):
     states = []
     for sg in (1, segments):
         with Mesh(*n, precision="fp64_fma") as mf:
+            mf.set_tuning("fp64_fused", 0)
             mf.set_tuning("sweep_segments", sg)
             mf.set_state(torch.from_numpy(U0).cuda())
             for _ in range(4):
@@ -390,6 +397,7 @@ def test_sweep_segments_bitwise_and_counted(segments):
     # a state without equal neighbours: every face evaluated, boundaries twice
     nx, ny, nz = n
     with Mesh(*n, bc=("periodic",) * 3, precision="fp64_fma") as mp:
+        mp.set_tuning("fp64_fused", 0)
         mp.set_tuning("sweep_segments", segments)
         mp.set_state(problems.random_smooth_periodic(*n, seed=9))
         mp.step(mp.reduce_dt(0.4))
@@ -404,6 +412,7 @@ def test_sweep_segments_bitwise_and_counted(segments):
     z = np.zeros(tx)
     Ut = problems.conserved_from_primitive(np.ones(tx), z, z, z, p).reshape(5, 1, 1, tx)
     om, Uo, m = _pair(tx, 1, 1, np.ascontiguousarray(Ut))
+    m.set_tuning("fp64_fused", 0)
     m.set_tuning("sweep_segments", 2 if segments == 64 else segments)
     dU, bad, fb = oracle.compute_update(om, Uo, 1e-3)
     m.substep(1, 1e-3)
@@ -631,3 +640,48 @@ def test_shear_layer_512_sampled_windows():
         win = got[:, k0:k0 + w, j0:j0 + w, i0:i0 + w].cpu().numpy()
         err = np.abs(win - ref).reshape(5, -1).max(1) / scale
         assert np.all(err < 1e-6), ((i0, j0, k0), err)
+
+
+@pytest.mark.parametrize("kchunk", [1, 5, 32])
+def test_fused_and_sweeps_same_bits(kchunk):
+    """The fused FP64 kernel (one launch per substep over 32 x 8 tiles and z
+    chunks) and the per-axis sweeps compute the same operations in the same
+    order: the exact build gives the oracle's bits both ways -- on ragged
+    meshes (tiles cut at every edge), z chunks of several sizes, outflow and
+    periodic faces, a non-default limiter -- with the same dt, fallback and
+    non-physical counts."""
+    from paper_1812_07977_gb300.fv import Mesh
+    cases = [((45, 19, 23), problems.riemann_oblique(45, 19, 23), (OUT, OUT, OUT), 2.0),
+             ((33, 10, 12), problems.random_smooth_periodic(33, 10, 12, seed=3),
+              (PER, OUT, PER), 1.3)]
+    for n, U0, bc, theta in cases:
+        runs = []
+        for fused in (1, 0):
+            om, Uo, m = _pair(*n, U0, bc=bc, theta=theta)
+            m.set_tuning("fp64_fused", fused)
+            m.set_tuning("kchunk", kchunk)
+            _run_both(om, Uo, m, 4)
+            got = m.get_state().cpu().numpy()
+            assert np.array_equal(got.view(np.uint64),
+                                  np.ascontiguousarray(oracle.interior(Uo)).view(np.uint64))
+            runs.append(m.counters())
+            m.close()
+        assert runs[0] == runs[1]
+
+
+def test_fused_fma_matches_sweeps_fma_within_1e12():
+    """The FMA build in its two forms (fused kernel and sweeps) stays within
+    1e-12 of each field's scale of the other after 20 steps of the oblique
+    problem (the contractions can differ between the two kernels)."""
+    from paper_1812_07977_gb300.fv import Mesh
+    n = (40, 36, 33)
+    U0 = problems.riemann_oblique(*n)
+    out = []
+    for fused in (1, 0):
+        with Mesh(*n, precision="fp64_fma") as m:
+            m.set_tuning("fp64_fused", fused)
+            m.set_state(U0)
+            for _ in range(20):
+                m.step(m.reduce_dt(0.4))
+            out.append(m.get_state().cpu().numpy())
+    assert np.all(_field_rel_err(out[0], out[1]) <= 1e-12)
