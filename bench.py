@@ -514,7 +514,10 @@ def run_ours(args):
 
     def variant(prec, U0v, nsteps, bc=("outflow",) * 3):
         U0v_dev = torch.from_numpy(U0v).to(dev) if isinstance(U0v, np.ndarray) else U0v
-        mv = Mesh(n, n, n, precision=prec, bc=bc)
+        fused = prec.endswith("_fused")
+        mv = Mesh(n, n, n, precision=prec[:-len("_fused")] if fused else prec, bc=bc)
+        if fused:
+            mv.set_tuning("fp64_fused", 1)
         vms_max, _, vprof, _, vfaces = _timed_run(mv, U0v_dev, nsteps, args.warmup, world, dev,
                                                   rank, False)
         mv.close()
@@ -528,7 +531,7 @@ def run_ours(args):
                    "frac": BYTES_PER_ZONE_UPDATE * vval / 1e9 / hbm}}
         if vprof["fused"][1] > 0:
             out["fused_kernel"] = _fused_roofline(vprof, vfaces, zones, 100, fp64_peak, hbm,
-                                                  prec != "fp32_bulk")
+                                                  not prec.startswith("fp32"))
         return out
 
     # the other arithmetic variants on the same workload, fewer steps each,
@@ -614,10 +617,11 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64_fma", choices=["fp64", "fp64_fma"],
+    ap.add_argument("--precision", default="fp64_ff", choices=["fp64", "fp64_fma", "fp64_ff"],
                     help="FP64 arithmetic of the headline line (fp32_bulk is reported as a "
                          "variant)")
-    ap.add_argument("--variants", nargs="*", default=["fp64", "fp32_bulk"],
+    ap.add_argument("--variants", nargs="*",
+                    default=["fp64", "fp64_fma", "fp64_fused", "fp32_bulk"],
                     help="other precisions timed beside the headline one")
     ap.add_argument("--variant-steps", type=int, default=50)
     ap.add_argument("--noreuse-steps", type=int, default=10,

@@ -80,12 +80,29 @@ typedef enum { FV_BC_OUTFLOW = 0, FV_BC_PERIODIC = 1 } fv_bc;
  *                    as an FP32 seed refined by two Newton-Raphson steps in
  *                    FP64: the same method, a few ulp per operation away from
  *                    FV_PREC_FP64 (held to 1e-12 relative of each field).
+ *  FV_PREC_FP64_FF   FP64 state, primitives (Newton forms), RK combine and
+ *                    CFL time step as FV_PREC_FP64_FMA; the work per face --
+ *                    differences, limited slopes, face states, sound speeds,
+ *                    HLL fluxes -- and the flux divergence in float-float
+ *                    arithmetic (pairs of FP32 numbers, 48-bit significand)
+ *                    on the FP32 pipe, in one fused kernel per substep; held
+ *                    to 1e-12 relative of each field against FV_PREC_FP64.
+ *                    Its operand range is density and pressure of magnitude
+ *                    2^-30 .. 2^30 and velocities below 2^20: a step of a
+ *                    state with a physical cell outside it is reported
+ *                    (FV_ERR_INVALID_ARG at the next synchronising call) and
+ *                    leaves the state unspecified.
  *  The values 0 and 1 are those of the boundary's original two-value enum;
- *  the FMA build was added after them.  Both FP64 forms evaluate a face's
+ *  the later variants take new values.  The FP64 forms evaluate a face's
  *  flux once and reuse it, bit for bit, for the next face of a grid line
  *  when the cells around both are equal (see fv_get_face_counts).
  */
-typedef enum { FV_PREC_FP64 = 0, FV_PREC_FP32_BULK = 1, FV_PREC_FP64_FMA = 2 } fv_precision;
+typedef enum {
+  FV_PREC_FP64 = 0,
+  FV_PREC_FP32_BULK = 1,
+  FV_PREC_FP64_FMA = 2,
+  FV_PREC_FP64_FF = 3
+} fv_precision;
 
 typedef struct {
   int nx, ny, nz;       /* interior cells per axis, each >= 1 */
@@ -404,13 +421,16 @@ FV_API fv_status fv_conserved_sums_noalloc(const double* U, int nx, int ny, int 
  *                        same bits for every value; each extra piece
  *                        evaluates one face flux twice, which
  *                        fv_get_face_counts counts.
- *  FV_TUNE_FP64_FUSED    FP64 paths: 1 (default) runs each substep as one
- *                        fused kernel over tiles of 32 x 8 columns and z
- *                        chunks of FV_TUNE_KCHUNK planes, with the next
- *                        step's CFL maximum taken by stage 2; 0 runs the
+ *  FV_TUNE_FP64_FUSED    FP64 and FP64-FMA builds: 0 (default) runs the
  *                        per-axis passes (primitives, then x, y and z line
- *                        sweeps).  Both give the same bits.  Not between
- *                        the two substeps.
+ *                        sweeps); 1 runs each substep as one fused kernel
+ *                        over tiles of 32 x 8 columns and z chunks of
+ *                        FV_TUNE_KCHUNK planes, with the next step's CFL
+ *                        maximum taken by stage 2 (fewer bytes, slightly more
+ *                        FP64 instructions per zone-update: on this GPU the
+ *                        FP64 pipe decides, and the sweeps are faster).
+ *                        Both give the same bits.  Not between the two
+ *                        substeps.  FP64_FF always runs fused.
  * Errors: INVALID_ARG for an unknown key or a value out of range. */
 typedef enum {
   FV_TUNE_KCHUNK = 0,

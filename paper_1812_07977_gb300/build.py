@@ -34,6 +34,7 @@ UNITS = [
     ("fv_fused64_exact.o", "fv_fused64_kernels.cu", ["--fmad=false", "-DFV_NS=fv_fp64_exact"]),
     ("fv_fused64_fma.o", "fv_fused64_kernels.cu", ["--fmad=true", "-DFV_NS=fv_fp64_fma",
                                                    "-DFV_NEWTON_DIVSQRT"]),
+    ("fv_fused_ff.o", "fv_fused_ff_kernels.cu", ["--fmad=false", "-DFV_NEWTON_DIVSQRT"]),
     ("fv_step_fp32.o", "fv_step32_kernels.cu", ["--fmad=false"]),
     ("fv_aux.o", "fv_aux.cu", ["--fmad=false"]),
     ("fv_core.o", "fv_core.cu", ["--fmad=false"]),

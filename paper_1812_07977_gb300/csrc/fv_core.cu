@@ -143,7 +143,7 @@ fv_status validate_desc(const fv_mesh_desc* d) {
     return FV_ERR_INVALID_ARG;
   }
   if (d->precision != FV_PREC_FP64 && d->precision != FV_PREC_FP64_FMA &&
-      d->precision != FV_PREC_FP32_BULK) {
+      d->precision != FV_PREC_FP32_BULK && d->precision != FV_PREC_FP64_FF) {
     set_error("precision %d unknown", d->precision);
     return FV_ERR_INVALID_ARG;
   }
@@ -200,6 +200,12 @@ fv_status read_counters(fv_mesh_t m) {
 }
 
 fv_status nonphysical_status(fv_mesh_t m) {
+  if (m->host_ctr->ff_range) {
+    set_error("%llu cells outside the float-float operand range (density and pressure "
+              "2^-30 .. 2^30, velocities below 2^20): the state since is not valid; step "
+              "such states with FV_PREC_FP64 or FV_PREC_FP64_FMA", m->host_ctr->ff_range);
+    return FV_ERR_INVALID_ARG;
+  }
   if (m->host_ctr->np_step || m->host_ctr->np_dt) {
     set_error("non-physical state: %llu cell detections in the step, %llu in the time step",
               m->host_ctr->np_step, m->host_ctr->np_dt);
@@ -250,7 +256,8 @@ long long faces_normal_to(const fvd::Params& P, int axis) {
 cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
   for (int axis = 0; axis < 3; ++axis) m->faces_defined += faces_normal_to(m->P, axis);
   const bool fma = m->desc.precision == FV_PREC_FP64_FMA;
-  if (m->desc.precision != FV_PREC_FP32_BULK && m->fused64) {
+  const bool ff = m->desc.precision == FV_PREC_FP64_FF;
+  if (m->desc.precision != FV_PREC_FP32_BULK && (m->fused64 || ff)) {
     // one kernel per substep; stage 2 also takes the CFL maximum of its output
     m->smax_current = false;
     m->w_current = false;
@@ -259,6 +266,7 @@ cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
       e = cudaMemsetAsync(&m->buf.ctr->smax_next, 0, sizeof(unsigned long long), m->stream);
     if (e == cudaSuccess)
       e = timed(m, FV_KERNEL_FUSED, 1, [&] {
+        if (ff) return fv_fp64_ff::launch_fused(stage, m->buf, m->P, dt, m->kchunk, m->stream);
         return fma ? fv_fp64_fma::launch_fused(stage, m->buf, m->P, dt, m->kchunk, m->stream)
                    : fv_fp64_exact::launch_fused(stage, m->buf, m->P, dt, m->kchunk,
                                                  m->stream);
@@ -338,7 +346,7 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   m->occupancy = 2;
   m->tile_y = 8;
   m->segments = 0;
-  m->fused64 = true;
+  m->fused64 = false;
   m->w_current = false;
   m->smax_current = false;
   for (int c = 0; c < FV_KERNEL_NCLASS; ++c) m->launches[c] = 0;
@@ -347,7 +355,8 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device);
   if (e == cudaSuccess && desc->precision == FV_PREC_FP32_BULK) e = fv_fp32::prepare_kernels();
-  if (e == cudaSuccess && desc->precision != FV_PREC_FP32_BULK)
+  if (e == cudaSuccess && desc->precision == FV_PREC_FP64_FF) e = fv_fp64_ff::prepare_fused();
+  else if (e == cudaSuccess && desc->precision != FV_PREC_FP32_BULK)
     e = desc->precision == FV_PREC_FP64_FMA ? fv_fp64_fma::prepare_fused()
                                             : fv_fp64_exact::prepare_fused();
   if (e != cudaSuccess) {
@@ -359,10 +368,13 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   const size_t sb = m->state_doubles * sizeof(double);
   const size_t db = m->dense_doubles * sizeof(double);
   const size_t wb = sums_work_doubles(m->P) * sizeof(double);
+  // the per-axis sweeps (FP64 and FP64-FMA builds) need primitive and flag arrays
+  const bool sweeps_possible =
+      desc->precision == FV_PREC_FP64 || desc->precision == FV_PREC_FP64_FMA;
   if ((e = cudaMalloc(&m->buf.U, sb)) != cudaSuccess ||
       (e = cudaMalloc(&m->buf.U1, sb)) != cudaSuccess ||
-      (desc->precision != FV_PREC_FP32_BULK && (e = cudaMalloc(&m->buf.W, sb)) != cudaSuccess) ||
-      (desc->precision != FV_PREC_FP32_BULK &&
+      (sweeps_possible && (e = cudaMalloc(&m->buf.W, sb)) != cudaSuccess) ||
+      (sweeps_possible &&
        (e = cudaMalloc(&m->buf.keep, m->dense_doubles / fvd::NF)) != cudaSuccess) ||
       (e = cudaMalloc(&m->buf.ACC, db)) != cudaSuccess ||
       (e = cudaMalloc(&m->buf.ctr, sizeof(DevCounters))) != cudaSuccess ||
@@ -489,13 +501,15 @@ fv_status fv_reduce_dt(fv_mesh_t m, double cfl, double* dt_out) {
   DeviceGuard g(m->device);
   const bool fp32 = m->desc.precision == FV_PREC_FP32_BULK;
   const bool fma = m->desc.precision == FV_PREC_FP64_FMA;
-  const bool fused = fp32 || m->fused64;
+  const bool ffp = m->desc.precision == FV_PREC_FP64_FF;
+  const bool fused = fp32 || ffp || m->fused64;
   // fused paths: the last stage 2 took the maximum of the current state
   const bool cached = fused && m->smax_current;
   if (!cached) {
     cudaError_t e = timed(m, FV_KERNEL_DT, 1, [&] {
       if (fp32)
         return fv_fp32::launch_reduce_dt(m->buf.U, m->P, m->vacuum_ratio, m->buf.ctr, m->stream);
+      if (ffp) return fv_fp64_ff::launch_dt(m->buf.U, m->buf, m->P, m->stream);
       if (m->fused64)
         return fma ? fv_fp64_fma::launch_dt(m->buf.U, m->buf, m->P, m->stream)
                    : fv_fp64_exact::launch_dt(m->buf.U, m->buf, m->P, m->stream);

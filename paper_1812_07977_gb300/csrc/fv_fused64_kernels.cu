@@ -35,6 +35,7 @@
 // bits that evaluating gives.
 #include "fv_device.cuh"
 #include "fv_device32.cuh"
+#include "fv_fused_common.cuh"
 #include "fv_internal.h"
 
 #ifndef FV_NS
@@ -42,30 +43,10 @@
 #endif
 
 using namespace fvd;
+using namespace fvfused;
 
 namespace FV_NS {
 namespace {
-
-constexpr int TX = 32;   // tile width: one warp per tile row
-
-template <int TY_>
-struct Shape64 {
-  static constexpr int TY = TY_;
-  static constexpr int kThreads = TX * TY;
-  static constexpr int PX = TX + 4;
-  static constexpr int PY = TY + 4;
-  static constexpr int kHalo = PX * PY - TX * TY;
-  static constexpr int kHaloPer = (kHalo + kThreads - 1) / kThreads;
-  static constexpr int kXSlopes = (TX + 2) * TY;   // cells -1 .. TX of each tile row
-  static constexpr int kYSlopes = TX * (TY + 2);   // rows -1 .. TY of each tile column
-  static constexpr int kSlopes = kXSlopes + kYSlopes;
-  static constexpr int kSlopePer = (kSlopes + kThreads - 1) / kThreads;
-  static constexpr int kXFaces = (TX + 1) * TY;
-  static constexpr int kYFaces = TX * (TY + 1);
-  static constexpr int kFaces = kXFaces + kYFaces;
-  static constexpr int kFacePer = (kFaces + kThreads - 1) / kThreads;
-  static_assert(kFacePer <= 8, "face fallback bits");
-};
 
 template <class S>
 struct Smem64 {
@@ -78,39 +59,6 @@ struct Smem64 {
   double fy[NF][S::TY + 1][TX];       // y face fluxes
   unsigned char same[S::PY][S::PX];   // the cell equals (bits) the cell a plane below
 };
-
-// Halo cell h of a tile (0 <= h < kHalo): two rows below the tile, two
-// above, then two columns on each side of every tile row; (row, col)
-// relative to the tile's first cell.
-template <class S>
-__device__ __forceinline__ void halo_cell(int h, int& row, int& col) {
-  constexpr int PX = S::PX;
-  if (h < 2 * PX) {
-    row = h / PX - 2;
-    col = h % PX - 2;
-  } else if (h < 4 * PX) {
-    row = S::TY + (h - 2 * PX) / PX;
-    col = (h - 2 * PX) % PX - 2;
-  } else {
-    const int u = h - 4 * PX;
-    row = u / 4;
-    const int c = u % 4;
-    col = c < 2 ? c - 2 : TX + c - 2;
-  }
-}
-
-__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
-                   (unsigned)__cvta_generic_to_shared(dst)),
-               "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-}
 
 __device__ __forceinline__ Prim load_cons_prim(const double* __restrict__ U, long long nf,
                                                long long off, const Params& P) {

@@ -16,7 +16,8 @@ struct DevCounters {
   unsigned long long fallback;     // faces that fell back to first order
   unsigned long long np_dt;        // non-physical interior cells seen by the dt pass
   unsigned long long faces;        // face fluxes evaluated (not reused) by the flux kernels
-  unsigned long long smax_next;    // FP32-bulk: CFL maximum of the last stage 2's output
+  unsigned long long smax_next;    // fused paths: CFL maximum of the last stage 2's output
+  unsigned long long ff_range;     // float-float path: cells outside its operand range
 };
 
 // Adds each lane's count to *ctr once per warp (the lanes present at the call).
@@ -70,6 +71,17 @@ struct StepBuffers {
   }
 FV_DECLARE_STEP_VARIANT(fv_fp64_exact)
 FV_DECLARE_STEP_VARIANT(fv_fp64_fma)
+
+// fv_fused_ff_kernels.cu: the fused substep with float-float face arithmetic
+// (FV_PREC_FP64_FF), its CFL maximum, and its shared-memory set-up; the
+// same contracts as the fused FP64 variants above.
+namespace fv_fp64_ff {
+cudaError_t prepare_fused();
+cudaError_t launch_fused(int stage, const StepBuffers& b, const fvd::Params& P, double dt,
+                         int kchunk, cudaStream_t s);
+cudaError_t launch_dt(const double* U, const StepBuffers& b, const fvd::Params& P,
+                      cudaStream_t s);
+}
 
 // One mesh of a batch, as the batched kernels see it.
 struct BatchMesh {

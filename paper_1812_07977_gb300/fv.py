@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfvgb.so")
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_BAD_HANDLE = range(7)
 BC = {"outflow": 0, "periodic": 1}
-PRECISION = {"fp64": 0, "fp32_bulk": 1, "fp64_fma": 2}
+PRECISION = {"fp64": 0, "fp32_bulk": 1, "fp64_fma": 2, "fp64_ff": 3}
 
 # Every entry point declared in include/fv.h.
 ABI_SYMBOLS = (
