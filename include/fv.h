@@ -404,13 +404,16 @@ FV_API fv_status fv_conserved_sums_noalloc(const double* U, int nx, int ny, int 
 /* Tuning knobs (not part of the paper).
  *  FV_TUNE_KCHUNK        z planes per CTA of the fused kernels (FP32-bulk
  *                        and FP64; integer >= 1; default 32, or nz when
- *                        nz < 64)
+ *                        nz < 64; 64 for FP64_FF meshes with nz >= 128)
  *  FV_TUNE_VACUUM_RATIO  FP32-bulk: recover the pressure in FP64 where the
  *                        kinetic energy exceeds this fraction of E (default
  *                        0.99; a value > 1 turns the recovery off)
  *  FV_TUNE_OCCUPANCY     occupancy the fused FP32-bulk kernel is built for:
  *                        2 (16 warps per SM, up to 128 registers, default)
- *                        or 3 (24 warps, 80 registers; tile height 8 only)
+ *                        or 3 (24 warps, 80 registers; tile height 8 only);
+ *                        for FP64_FF meshes the CTAs per SM of its fused
+ *                        kernel: 2 (16 warps, 128 registers, default) or 1
+ *                        (8 warps, up to 255 registers); the same bits
  *  FV_TUNE_TILE_Y        tile height of the fused FP32-bulk kernel: 4, 8
  *                        (default) or 16 (tiles of 32 x 4 / 8 / 16 columns,
  *                        CTAs of 128 / 256 / 512 threads); the same bits

@@ -63,6 +63,7 @@ struct fv_mesh_s {
   int tile_y;               // tile height of the fused kernel (4, 8 or 16)
   int segments;             // pieces per grid line of the FP64 sweeps (0: automatic)
   bool fused64;             // FP64: one fused kernel per substep (else the per-axis sweeps)
+  int ff_ctas_per_sm;       // FP64_FF: CTAs per SM its fused kernel is built for (1 or 2)
   bool w_current;           // FP64 sweeps: W holds the primitives of U (from the dt pass)
   bool smax_current;        // fused paths: ctr->smax_next is the CFL maximum of U
   // profiling
@@ -266,7 +267,9 @@ cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
       e = cudaMemsetAsync(&m->buf.ctr->smax_next, 0, sizeof(unsigned long long), m->stream);
     if (e == cudaSuccess)
       e = timed(m, FV_KERNEL_FUSED, 1, [&] {
-        if (ff) return fv_fp64_ff::launch_fused(stage, m->buf, m->P, dt, m->kchunk, m->stream);
+        if (ff)
+          return fv_fp64_ff::launch_fused(stage, m->buf, m->P, dt, m->kchunk,
+                                          m->ff_ctas_per_sm, m->stream);
         return fma ? fv_fp64_fma::launch_fused(stage, m->buf, m->P, dt, m->kchunk, m->stream)
                    : fv_fp64_exact::launch_fused(stage, m->buf, m->P, dt, m->kchunk,
                                                  m->stream);
@@ -341,12 +344,16 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   m->stream = (cudaStream_t)cuda_stream;
   m->stage_pending = 0;
   m->prof_on = false;
-  m->kchunk = desc->nz >= 64 ? 32 : desc->nz;
+  // z planes per CTA of the fused kernels: the float-float kernel measured
+  // fastest with 64 on the 256^3 workloads, the FP32-bulk one with 32
+  m->kchunk = desc->precision == FV_PREC_FP64_FF && desc->nz >= 128 ? 64
+              : desc->nz >= 64 ? 32 : desc->nz;
   m->vacuum_ratio = 0.99;
   m->occupancy = 2;
   m->tile_y = 8;
   m->segments = 0;
   m->fused64 = false;
+  m->ff_ctas_per_sm = 2;
   m->w_current = false;
   m->smax_current = false;
   for (int c = 0; c < FV_KERNEL_NCLASS; ++c) m->launches[c] = 0;
@@ -634,6 +641,14 @@ fv_status fv_set_tuning(fv_mesh_t m, int key, double value) {
       return FV_ERR_INVALID_ARG;
     }
     m->vacuum_ratio = value;
+    return FV_OK;
+  }
+  if (key == FV_TUNE_OCCUPANCY && m->desc.precision == FV_PREC_FP64_FF) {
+    if (value != 1.0 && value != 2.0) {
+      set_error("FV_TUNE_OCCUPANCY of the float-float kernel must be 1 or 2 (got %g)", value);
+      return FV_ERR_INVALID_ARG;
+    }
+    m->ff_ctas_per_sm = (int)value;
     return FV_OK;
   }
   if (key == FV_TUNE_OCCUPANCY) {

@@ -226,41 +226,43 @@ struct ParamsF {
 // p e_n, (E + p) vn), c = t rsqrt(t rho) with t = gamma p; a+ = max(0,
 // vL + cL, vR + cR), a- = max(0, cL - vL, cR - vR);
 // F = ((a+ FL + a- FR) - a+ a- (UR - UL)) (1 / (a+ + a-)).
+// Evaluated component by component (each side's U and F of a component
+// formed where it is used), so few values are live at once.
 template <int AXIS>
 __device__ __forceinline__ void hll_flux(const PrimF& wl, const PrimF& wr, const ParamsF& Q,
                                          ff F[NF]) {
-  ff UL[NF], UR[NF], FL[NF], FR[NF], c[2], vn[2];
+  ff vn[2], c[2], E[2];
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const PrimF& w = s == 0 ? wl : wr;
-    ff* U = s == 0 ? UL : UR;
-    ff* Fs = s == 0 ? FL : FR;
-    const ff mx = mul(w.r, w.vx), my = mul(w.r, w.vy), mz = mul(w.r, w.vz);
-    const ff ke = half(add(add(mul(mx, w.vx), mul(my, w.vy)), mul(mz, w.vz)));
-    U[0] = w.r;
-    U[1] = mx;
-    U[2] = my;
-    U[3] = mz;
-    U[4] = add(mul(w.p, Q.igm1), ke);
-    const ff v = AXIS == 0 ? w.vx : AXIS == 1 ? w.vy : w.vz;
-    const ff mn = AXIS == 0 ? mx : AXIS == 1 ? my : mz;
-    vn[s] = v;
+    const ff ke = half(add(add(mul(mul(w.r, w.vx), w.vx), mul(mul(w.r, w.vy), w.vy)),
+                           mul(mul(w.r, w.vz), w.vz)));
+    E[s] = add(mul(w.p, Q.igm1), ke);
+    vn[s] = AXIS == 0 ? w.vx : AXIS == 1 ? w.vy : w.vz;
     const ff t = mul(Q.gamma, w.p);
     c[s] = mul(t, rsqrt(mul(t, w.r)));
-    Fs[0] = mn;
-    Fs[1] = mul(mn, w.vx);
-    Fs[2] = mul(mn, w.vy);
-    Fs[3] = mul(mn, w.vz);
-    Fs[1 + AXIS] = add(Fs[1 + AXIS], w.p);
-    Fs[4] = mul(add(U[4], w.p), v);
   }
   const ff ap = max0(add(vn[0], c[0]), add(vn[1], c[1]));
   const ff am = max0(sub(c[0], vn[0]), sub(c[1], vn[1]));
   const ff r = recip(add(ap, am));
   const ff apm = mul(ap, am);
+  const ff mnl = mul(wl.r, vn[0]), mnr = mul(wr.r, vn[1]);
+  auto combine = [&](ff ul, ff ur, ff fl, ff fr) {
+    return mul(sub(add(mul(ap, fl), mul(am, fr)), mul(apm, sub(ur, ul))), r);
+  };
+  F[0] = combine(wl.r, wr.r, mnl, mnr);
 #pragma unroll
-  for (int q = 0; q < NF; ++q)
-    F[q] = mul(sub(add(mul(ap, FL[q]), mul(am, FR[q])), mul(apm, sub(UR[q], UL[q]))), r);
+  for (int q = 1; q <= 3; ++q) {
+    const ff vl = q == 1 ? wl.vx : q == 2 ? wl.vy : wl.vz;
+    const ff vr = q == 1 ? wr.vx : q == 2 ? wr.vy : wr.vz;
+    ff fl = mul(mnl, vl), fr = mul(mnr, vr);
+    if (q == 1 + AXIS) {
+      fl = add(fl, wl.p);
+      fr = add(fr, wr.p);
+    }
+    F[q] = combine(mul(wl.r, vl), mul(wr.r, vr), fl, fr);
+  }
+  F[4] = combine(E[0], E[1], mul(add(E[0], wl.p), vn[0]), mul(add(E[1], wr.p), vn[1]));
 }
 
 }  // namespace fvff

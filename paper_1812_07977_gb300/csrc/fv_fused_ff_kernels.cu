@@ -43,6 +43,7 @@ struct SmemFF {
   ff fx[NF][S::TY][TX + 1];         // x face fluxes
   ff fy[NF][S::TY + 1][TX];         // y face fluxes
   unsigned char same[S::PY][S::PX]; // the cell equals (bits) the cell a plane below
+  double last[NF][S::kThreads];     // stage 2: the state of the column's last cell written
 };
 
 struct ConstFF {
@@ -145,8 +146,7 @@ __device__ __forceinline__ void stageff_tile(SmemFF<S>& s, double* __restrict__ 
   }
   unsigned fallbacks = 0, xyfb = 0;
   unsigned long long bad = 0, range = 0;
-  fvd32::SpeedCache cache;
-  cache.valid = false;
+  unsigned last_bad = 0;   // stage 2: whether the column's last cell written was non-physical
 
   // z window prologue: planes k0-2 .. k0+1 of the column; per plane whether
   // its cell is physical and inside the float-float range (counted at k)
@@ -162,8 +162,7 @@ __device__ __forceinline__ void stageff_tile(SmemFF<S>& s, double* __restrict__ 
   bool ph0, ok0, ph1, ok1;
   PrimF w0 = load_ff(k0 + 2, ph0, ok0);
   PrimF w1 = load_ff(k0 + 3, ph1, ok1);
-  PrimF d1 = fvff::psub(w1, w0);
-  PrimF h0 = fvff::half_slopes<MC>(Q.theta, fvff::psub(w0, wm1), d1);
+  PrimF h0 = fvff::half_slopes<MC>(Q.theta, fvff::psub(w0, wm1), fvff::psub(w1, w0));
   ff fz_lo[NF];
   bool zfb;
   {
@@ -224,6 +223,20 @@ __device__ __forceinline__ void stageff_tile(SmemFF<S>& s, double* __restrict__ 
     }
     const bool same2 = eqc || fvff::same_bits(w2, w1);
     run = same2 ? run + 1 : 1;
+    // (c) z flux of face k+1/2
+    PrimF h1;
+    ff fz_hi[NF];
+    if (__all_sync(0xffffffffu, run >= 5)) {
+      const ff z{0.0f, 0.0f};
+      h1 = PrimF{z, z, z, z, z};
+#pragma unroll
+      for (int q = 0; q < NF; ++q) fz_hi[q] = fz_lo[q];
+    } else {
+      h1 = fvff::half_slopes<MC>(Q.theta, fvff::psub(w1, w0), fvff::psub(w2, w1));
+      face_flux<2>(w0, h0, w1, h1, Q, fz_hi, zfb);
+      ++evaluated;
+    }
+    if (zfb && owner) ++fallbacks;
     // (b) the halo cells of plane k
     double uh[kHaloPer][NF];
     bool eqh[kHaloPer];
@@ -237,23 +250,7 @@ __device__ __forceinline__ void stageff_tile(SmemFF<S>& s, double* __restrict__ 
         eqh[e] = eqh[e] && (h >= kHalo || bits(uh[e][q]) == bits(s.halo[prev][q][h]));
       }
     }
-    stage_in(k + 1);
-    // (c) z flux of face k+1/2
-    PrimF d2, h1;
-    ff fz_hi[NF];
-    if (__all_sync(0xffffffffu, run >= 5)) {
-      const ff z{0.0f, 0.0f};
-      d2 = PrimF{z, z, z, z, z};
-      h1 = d2;
-#pragma unroll
-      for (int q = 0; q < NF; ++q) fz_hi[q] = fz_lo[q];
-    } else {
-      d2 = fvff::psub(w2, w1);
-      h1 = fvff::half_slopes<MC>(Q.theta, d1, d2);
-      face_flux<2>(w0, h0, w1, h1, Q, fz_hi, zfb);
-      ++evaluated;
-    }
-    if (zfb && owner) ++fallbacks;
+    stage_in(k + 1);   // into the other slot, now compared
     // (d) the plane's primitives into shared memory
     smem_w_store(s, tj + 2, ti + 2, w0);
     s.same[tj + 2][ti + 2] = later && same0;
@@ -348,16 +345,14 @@ __device__ __forceinline__ void stageff_tile(SmemFF<S>& s, double* __restrict__ 
     // (g) update: float-float divergence, the RK combine in FP64 on the FP64
     // state (a copy / half sum where every flux difference is zero)
     if (owner) {
-      ff fxl[NF], fxr[NF], fyl[NF], fyr[NF];
+      // first the zero test over all components, then the arithmetic one
+      // component at a time (few values live at once)
       bool zero = true;
 #pragma unroll
       for (int q = 0; q < NF; ++q) {
-        fxl[q] = s.fx[q][tj][ti];
-        fxr[q] = s.fx[q][tj][ti + 1];
-        fyl[q] = s.fy[q][tj][ti];
-        fyr[q] = s.fy[q][tj + 1][ti];
-        zero = zero && same_ff(fxl[q], fxr[q]) && same_ff(fyl[q], fyr[q]) &&
-               same_ff(fz_lo[q], fz_hi[q]) && finite_ff(fxr[q]) && finite_ff(fyr[q]) &&
+        const ff xr = s.fx[q][tj][ti + 1], yr = s.fy[q][tj + 1][ti];
+        zero = zero && same_ff(s.fx[q][tj][ti], xr) && same_ff(s.fy[q][tj][ti], yr) &&
+               same_ff(fz_lo[q], fz_hi[q]) && finite_ff(xr) && finite_ff(yr) &&
                finite_ff(fz_hi[q]);
       }
       double un[NF];
@@ -371,8 +366,9 @@ __device__ __forceinline__ void stageff_tile(SmemFF<S>& s, double* __restrict__ 
       } else {
 #pragma unroll
         for (int q = 0; q < NF; ++q) {
-          ff acc = fvff::mul(fvff::sub(fxl[q], fxr[q]), C.inv[0]);
-          acc = fvff::sub(acc, fvff::mul(fvff::sub(fyr[q], fyl[q]), C.inv[1]));
+          ff acc = fvff::mul(fvff::sub(s.fx[q][tj][ti], s.fx[q][tj][ti + 1]), C.inv[0]);
+          acc = fvff::sub(acc, fvff::mul(fvff::sub(s.fy[q][tj + 1][ti], s.fy[q][tj][ti]),
+                                         C.inv[1]));
           acc = fvff::sub(acc, fvff::mul(fvff::sub(fz_hi[q], fz_lo[q]), C.inv[2]));
           const double du = dt * fvff::to_double(acc);
           const double r0 = U[q * nf + g];
@@ -380,13 +376,24 @@ __device__ __forceinline__ void stageff_tile(SmemFF<S>& s, double* __restrict__ 
           else U[q * nf + g] = un[q] = half((r0 + U1[q * nf + g]) + du);
         }
       }
-      if (STAGE == 2) fvd32::fold_speed(un, P, Q32, smax, smax_f, bad_next, cache, gmax);
+      if (STAGE == 2) {
+        // the column's last cell written: a cell equal to it changes
+        // nothing but the count (fvd32::fold_speed, its cache in shared memory)
+        fvd32::SpeedCache cache;
+        cache.valid = k > k0;
+#pragma unroll
+        for (int q = 0; q < NF; ++q) cache.u[q] = s.last[q][tid];
+        cache.bad = last_bad;
+        fvd32::fold_speed(un, P, Q32, smax, smax_f, bad_next, cache, gmax);
+#pragma unroll
+        for (int q = 0; q < NF; ++q) s.last[q][tid] = un[q];
+        last_bad = cache.bad;
+      }
     }
 #pragma unroll
     for (int q = 0; q < NF; ++q) fz_lo[q] = fz_hi[q];
     w0 = w1;
     w1 = w2;
-    d1 = d2;
     h0 = h1;
     same0 = same1;
     same1 = same2;
@@ -412,8 +419,10 @@ __device__ __forceinline__ void max_to(unsigned long long* dst, double smax) {
 
 constexpr int kTileY = 8;
 
-template <int STAGE, bool MC>
-__global__ void __launch_bounds__(TX * kTileY, 1)
+// MINB: CTAs per SM the kernel is built for (1: up to 255 registers, 8 warps
+// per SM; 2: 128 registers, 16 warps per SM)
+template <int STAGE, bool MC, int MINB>
+__global__ void __launch_bounds__(TX * kTileY, MINB)
 k_stageff(double* __restrict__ U, double* __restrict__ U1, Params P, fvd32::Params32 Q32,
           ConstFF C, double dt, int kchunk, DevCounters* ctr) {
   using S = Shape64<kTileY>;
@@ -496,43 +505,53 @@ ConstFF make_const(const Params& P) {
   return C;
 }
 
-template <int STAGE, bool MC>
+template <int STAGE, bool MC, int MINB>
 cudaError_t launch_mc(const StepBuffers& b, const Params& P, double dt, int kchunk,
                       cudaStream_t s) {
   using S = Shape64<kTileY>;
   const dim3 grid((P.nx + TX - 1) / TX, (P.ny + kTileY - 1) / kTileY,
                   (P.nz + kchunk - 1) / kchunk);
-  k_stageff<STAGE, MC><<<grid, S::kThreads, sizeof(SmemFF<S>), s>>>(
+  k_stageff<STAGE, MC, MINB><<<grid, S::kThreads, sizeof(SmemFF<S>), s>>>(
       b.U, b.U1, P, fv_fp32::make_params32(P, 2.0), make_const(P), dt, kchunk, b.ctr);
   return cudaGetLastError();
 }
 
-template <bool MC>
+template <bool MC, int MINB>
 cudaError_t raise_smem() {
   const int bytes = (int)sizeof(SmemFF<Shape64<kTileY>>);
-  cudaError_t e = cudaFuncSetAttribute(k_stageff<1, MC>,
+  cudaError_t e = cudaFuncSetAttribute(k_stageff<1, MC, MINB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_stageff<2, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             bytes);
+    e = cudaFuncSetAttribute(k_stageff<2, MC, MINB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   return e;
 }
 
 }  // namespace
 
 cudaError_t prepare_fused() {
-  cudaError_t e = raise_smem<true>();
-  if (e == cudaSuccess) e = raise_smem<false>();
+  cudaError_t e = raise_smem<true, 1>();
+  if (e == cudaSuccess) e = raise_smem<false, 1>();
+  if (e == cudaSuccess) e = raise_smem<true, 2>();
+  if (e == cudaSuccess) e = raise_smem<false, 2>();
   return e;
 }
 
-cudaError_t launch_fused(int stage, const StepBuffers& b, const Params& P, double dt,
-                         int kchunk, cudaStream_t s) {
-  if (kchunk < 1) kchunk = 1;
+template <int MINB>
+cudaError_t launch_minb(int stage, const StepBuffers& b, const Params& P, double dt,
+                        int kchunk, cudaStream_t s) {
   const bool mc = P.theta == 2.0;
-  if (stage == 1) return mc ? launch_mc<1, true>(b, P, dt, kchunk, s)
-                            : launch_mc<1, false>(b, P, dt, kchunk, s);
-  return mc ? launch_mc<2, true>(b, P, dt, kchunk, s) : launch_mc<2, false>(b, P, dt, kchunk, s);
+  if (stage == 1) return mc ? launch_mc<1, true, MINB>(b, P, dt, kchunk, s)
+                            : launch_mc<1, false, MINB>(b, P, dt, kchunk, s);
+  return mc ? launch_mc<2, true, MINB>(b, P, dt, kchunk, s)
+            : launch_mc<2, false, MINB>(b, P, dt, kchunk, s);
+}
+
+cudaError_t launch_fused(int stage, const StepBuffers& b, const Params& P, double dt,
+                         int kchunk, int ctas_per_sm, cudaStream_t s) {
+  if (kchunk < 1) kchunk = 1;
+  return ctas_per_sm >= 2 ? launch_minb<2>(stage, b, P, dt, kchunk, s)
+                          : launch_minb<1>(stage, b, P, dt, kchunk, s);
 }
 
 cudaError_t launch_dt(const double* U, const StepBuffers& b, const Params& P, cudaStream_t s) {

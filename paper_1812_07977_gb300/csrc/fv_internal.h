@@ -77,8 +77,9 @@ FV_DECLARE_STEP_VARIANT(fv_fp64_fma)
 // same contracts as the fused FP64 variants above.
 namespace fv_fp64_ff {
 cudaError_t prepare_fused();
+// ctas_per_sm: 2 (16 warps per SM, 128 registers) or 1 (8 warps, 255)
 cudaError_t launch_fused(int stage, const StepBuffers& b, const fvd::Params& P, double dt,
-                         int kchunk, cudaStream_t s);
+                         int kchunk, int ctas_per_sm, cudaStream_t s);
 cudaError_t launch_dt(const double* U, const StepBuffers& b, const fvd::Params& P,
                       cudaStream_t s);
 }

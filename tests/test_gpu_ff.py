@@ -178,3 +178,23 @@ def test_ff_operand_range_is_guarded():
         m.get_state()
     assert e.value.status == ERR_INVALID_ARG
     m.close()
+
+
+def test_ff_launch_settings_same_bits():
+    """The float-float kernel built for one or two CTAs per SM, with z chunks
+    of several sizes, computes the same operations: the same bits."""
+    n = (45, 19, 30)
+    U0 = problems.riemann_oblique(*n)
+    out = []
+    for occ, kc in ((2, 64), (1, 64), (2, 7), (1, 1)):
+        m = _mesh(n)
+        m.set_tuning("occupancy", occ)
+        m.set_tuning("kchunk", kc)
+        m.set_state(U0)
+        for _ in range(3):
+            m.step(m.reduce_dt(0.4))
+        out.append((m.get_state().cpu().numpy(), m.counters()))
+        m.close()
+    for st, ct in out[1:]:
+        assert np.array_equal(st.view(np.uint64), out[0][0].view(np.uint64))
+        assert ct == out[0][1]
