@@ -60,6 +60,21 @@ FLOPS_FUSED_CELL = round(FLOPS_PRIM * (36 * 12) / (32 * 8)) + 40 + 10
 # stage 2: stage 1 reads U^n, writes U^1 (80 B); stage 2 reads U^1, U^n and
 # writes U^{n+1} (120 B).
 BYTES_PER_ZONE_UPDATE = 200
+# The float-float form (FV_PREC_FP64_FF) works on the FP32 pipe: its
+# algorithmic FP32 operations (each FP32 add, multiply, fused multiply-add,
+# reciprocal or reciprocal square root counted once; comparisons, sign
+# tests and the FP64 <-> float-float conversions not counted), from the
+# operation counts of its formulas (TwoSum 6, Fast2Sum 3, TwoProd 2;
+# float-float add 11, multiply 7, reciprocal 11, inverse square root 17):
+#   per face: the two face states 110; per side kinetic and total energy and
+#     sound speed 122 (x2); wave bounds, 1 / (a+ + a-), a+ a-, normal mass
+#     fluxes 87; the five HLL components 61 + 289 + 97 -> 888;
+#   per cell and axis (one per face): the two one-sided differences of the
+#     five primitives 110 and the half monotonised-central slopes 95 (theta
+#     = 2, the default: theta d is exact doubling) -> 205;
+#   per cell and launch: the float-float divergence 380.
+FF_OPS_FACE = 888 + 205
+FF_OPS_CELL = 380
 # DRAM bytes (read + write) per launch of the fused kernels at 256^3 (mean of
 # stage 1 and 2) from ncu captures of the current kernels; None where no
 # capture of the current kernel exists.
@@ -325,6 +340,8 @@ def run_batched(args, world, dev, rank):
     for m, s in enumerate(spec):
         b.set_state(m, torch.from_numpy(s["U0"]).to(dev))
     kc, occ, tile_y, tune_ms = b.autotune(CFL)
+    per_class = {f"class{c} ({('nx<=24', 'nx<=64', 'nx>64')[c]})": b.class_tuning(c)
+                 for c in range(3)}
     for _ in range(args.warmup):
         b.step(CFL, use_graph=True)
     for m, s in enumerate(spec):
@@ -345,8 +362,7 @@ def run_batched(args, world, dev, rank):
     return {"value": world * cells * args.batch_steps / el, "unit": "zone-updates/s",
             "ms_per_step": 1e3 * el / args.batch_steps, "steps": args.batch_steps,
             "meshes": nmesh, "cells": cells, "work_items": items,
-            "autotuned": {"kchunk": kc, "tile": f"32x{tile_y}", "occupancy": occ,
-                          "ms_per_step": tune_ms},
+            "autotuned": {"per_class": per_class, "ms_per_step": tune_ms},
             "timing": "CUDA events on the batch's stream around the graph launches",
             "nonphysical": bad}
 
@@ -426,10 +442,12 @@ def run_shear(args, dev):
                     "CFL steps, so the two end times agree to the dt difference"}
 
 
-def _fused_roofline(prof, faces, zones, bytes_per_launch_cell, peak_tflops, hbm, flops):
-    """The fused substep kernel's figures: FP64 flops executed per launch
-    (FLOPS_FACE per evaluated face + FLOPS_FUSED_CELL per cell) against the
-    FP64 peak, and its algorithmic HBM bytes against the copy bandwidth."""
+def _fused_roofline(prof, faces, zones, bytes_per_launch_cell, peak_tflops, hbm, flops,
+                    per_face=FLOPS_FACE, per_cell=FLOPS_FUSED_CELL):
+    """The fused substep kernel's figures: the operations executed per launch
+    (per_face per evaluated face + per_cell per cell: FP64 flops for the FP64
+    kernels, FP32 operations for the float-float one) against the peak of
+    that pipe, and its algorithmic HBM bytes against the copy bandwidth."""
     ms, launches = prof["fused"]
     launches = max(launches, 1)
     evaluated, defined = faces
@@ -442,8 +460,8 @@ def _fused_roofline(prof, faces, zones, bytes_per_launch_cell, peak_tflops, hbm,
                   "unit": "GB/s", "bytes_per_launch": b,
                   "frac": b * launches / sec / 1e9 / hbm if sec > 0 else None}
     if flops:
-        executed = evaluated * FLOPS_FACE + FLOPS_FUSED_CELL * zones * launches
-        method = defined * FLOPS_FACE + FLOPS_FUSED_CELL * zones * launches
+        executed = evaluated * per_face + per_cell * zones * launches
+        method = defined * per_face + per_cell * zones * launches
         out["alu"] = {"achieved": executed / sec / 1e12 if sec > 0 else None,
                       "peak": peak_tflops, "unit": "TFLOP/s",
                       "frac": executed / sec / 1e12 / peak_tflops if sec > 0 else None,
@@ -512,6 +530,17 @@ def run_ours(args):
         peak_source = (f"FP64 issue rate 2 DFMA/SM/clk x {sms} SMs x {sm_max:.0f} MHz "
                        "(MEASURED_PEAKS sm_max_mhz)")
 
+    # the float-float kernel's pipe: FP32 lane operations per second, measured
+    # live (FFMA rate of the probe) or 128 per SM and clock
+    derived_fp32 = 128.0 * sms * sm_max * 1e6 / 1e12
+    if probe and probe.get("ffma_per_s"):
+        fp32_peak = probe["ffma_per_s"] / 1e12
+        fp32_source = ("FP32 operation rate measured live by paper_1812_07977_gb300/_build/"
+                       "fp64_probe (FFMA lane operations per second), of measured")
+    else:
+        fp32_peak = derived_fp32
+        fp32_source = f"128 FP32 lanes per SM and clock x {sms} SMs x {sm_max:.0f} MHz"
+
     def variant(prec, U0v, nsteps, bc=("outflow",) * 3):
         U0v_dev = torch.from_numpy(U0v).to(dev) if isinstance(U0v, np.ndarray) else U0v
         fused = prec.endswith("_fused")
@@ -530,8 +559,12 @@ def run_ours(args):
                    "achieved": BYTES_PER_ZONE_UPDATE * vval / 1e9, "peak": hbm, "unit": "GB/s",
                    "frac": BYTES_PER_ZONE_UPDATE * vval / 1e9 / hbm}}
         if vprof["fused"][1] > 0:
-            out["fused_kernel"] = _fused_roofline(vprof, vfaces, zones, 100, fp64_peak, hbm,
-                                                  not prec.startswith("fp32"))
+            if prec == "fp64_ff":
+                out["fused_kernel"] = _fused_roofline(vprof, vfaces, zones, 100, fp32_peak, hbm,
+                                                      True, FF_OPS_FACE, FF_OPS_CELL)
+            else:
+                out["fused_kernel"] = _fused_roofline(vprof, vfaces, zones, 100, fp64_peak, hbm,
+                                                      not prec.startswith("fp32"))
         return out
 
     # the other arithmetic variants on the same workload, fewer steps each,
@@ -563,19 +596,31 @@ def run_ours(args):
 
     hbm_achieved = BYTES_PER_ZONE_UPDATE * zones * args.steps / (ms / 1e3) / 1e9
     launches = sum(v[1] for v in prof.values())
-    fused = _fused_roofline(prof, faces, zones, 100, fp64_peak, hbm, True)
+    ff = args.precision == "fp64_ff"
+    if ff:
+        fused = _fused_roofline(prof, faces, zones, 100, fp32_peak, hbm, True, FF_OPS_FACE,
+                                FF_OPS_CELL)
+        kernel, peak, src, dpeak = ("k_stageff (fused substep, float-float faces)", fp32_peak,
+                                    fp32_source, derived_fp32)
+        ops = (f"FP32 operations of the float-float arithmetic: {FF_OPS_FACE} per evaluated "
+               f"face + {FF_OPS_CELL} per cell and launch (each add, multiply or FMA once)")
+    else:
+        fused = _fused_roofline(prof, faces, zones, 100, fp64_peak, hbm, True)
+        kernel, peak, src, dpeak = ("k_stage64 (fused FP64 substep)", fp64_peak, peak_source,
+                                    derived_peak)
+        ops = (f"FP64 flops executed: {FLOPS_FACE} per evaluated face + {FLOPS_FUSED_CELL} "
+               f"per cell and launch")
     alu = fused["alu"]
     traffic = args.traffic if args.traffic else (FUSED_TRAFFIC.get(args.precision)
                                                  if n == N else None)
-    roofline = {"bound": "alu", "kernel": "k_stage64 (fused FP64 substep)",
-                "achieved": alu["achieved"], "peak": fp64_peak, "unit": "TFLOP/s",
+    roofline = {"bound": "alu", "kernel": kernel,
+                "achieved": alu["achieved"], "peak": peak, "unit": "TFLOP/s",
                 "frac": alu["frac"], "traffic": traffic,
                 "traffic_note": "DRAM bytes per launch from an ncu capture of this kernel "
                                 "(null: no capture of the current kernel)",
-                "peak_source": peak_source, "derived_peak": derived_peak,
+                "peak_source": src, "derived_peak": dpeak,
                 "avg_launch_ms": fused["avg_launch_ms"],
-                "flops": f"FP64 flops executed: {FLOPS_FACE} per evaluated face + "
-                         f"{FLOPS_FUSED_CELL} per cell and launch",
+                "flops": ops,
                 "flops_per_launch": alu["flops_per_launch"],
                 "method_flops_per_launch": alu["method_flops_per_launch"],
                 "effective_tflops": alu["effective_tflops"],
@@ -587,7 +632,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "zone-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "dtype": "f64 state; float-float (2 x f32) face arithmetic" if ff else "f64",
+        "data": "synthetic",
         "config": {"workload": "oblique Riemann problem 256^3 (Sod states, plane normal "
                                "(1,1,1), gamma 1.4, outflow, CFL 0.4), steps 1..K",
                    "precision": args.precision, "cells": zones,

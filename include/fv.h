@@ -240,10 +240,14 @@ FV_API fv_status fv_profile_read(fv_mesh_t m, double* ms, long long* launches);
  * Not in the paper (whose ranks each own one subdomain): the on-device
  * analogue of many independent RiemannProblem runs.  Every mesh of a batch
  * uses the FP32-bulk arithmetic (FV_PREC_FP32_BULK; the precision field of
- * the descriptions is ignored) and its own CFL time step.  One step is:
- * per-mesh dt = cfl / max signal speed (on the device, FP64 division), then
- * the two RK substeps, each ONE persistent launch over the work items
- * (mesh, 32x8 tile, z chunk) of all meshes, each followed by the ghost fill.
+ * the descriptions is ignored) and its own CFL time step.  The meshes fall
+ * into three size classes by their x extent (class 0: nx <= 24, class 1:
+ * nx <= 64, class 2: larger), each with its own launch configuration (tile
+ * shape, occupancy, z chunk).  One step is: per-mesh dt = cfl / max signal
+ * speed (on the device, FP64 speeds and division), then the two RK
+ * substeps, each one persistent launch per size class over the work items
+ * (mesh, tile, z chunk) of its meshes, each substep followed by the ghost
+ * fill of all meshes.
  * ------------------------------------------------------------------------ */
 typedef struct fv_batch_s* fv_batch_t;
 
@@ -271,18 +275,34 @@ FV_API fv_status fv_batch_step(fv_batch_t b, double cfl, int use_graph);
 /* The dt each mesh used in the last step (nmesh doubles).  Synchronising. */
 FV_API fv_status fv_batch_get_dt(fv_batch_t b, double* dt);
 
-/* Launch configuration: z planes per work item (kchunk in [1, 4096]), the
- * work item's tile of 32 x tile_y columns (tile_y 4, 8 or 16: CTAs of 128,
- * 256 or 512 threads) and occupancy 2 (16 warps per SM, up to 128
- * registers) or, for tile_y 8 only, 3 (80 registers).  Every configuration
- * gives the same bits.  Errors: INVALID_ARG. */
+/* Launch configuration of every size class at once: z planes per work item
+ * (kchunk in [1, 4096]), the work item's tile of 32 x tile_y columns (tile_y
+ * 4, 8 or 16: CTAs of 128, 256 or 512 threads) and occupancy 2 (16 warps per
+ * SM, up to 128 registers) or, for tile_y 8 only, 3 (80 registers).  Every
+ * configuration gives the same bits.  Errors: INVALID_ARG. */
 FV_API fv_status fv_batch_set_tuning(fv_batch_t b, int kchunk, int occupancy, int tile_y);
 
-/* Autotuner: times three steps for each z chunk in {8, 16, 32, 64} and each
- * (tile_y, occupancy) in {(4, 2), (8, 2), (8, 3), (16, 2)} on the batch's
- * current state, keeps the fastest and reports it (any output pointer may be
- * NULL).  The state and counters are restored afterwards (a snapshot buffer
- * of one state is allocated on first use).  Synchronising. */
+/* Launch configuration of one size class (cls 0, 1 or 2): tiles of tile_x x
+ * tile_y columns with occupancy, one of (32, 4, 2), (32, 8, 2), (32, 8, 3),
+ * (32, 16, 2), (16, 8, 2), (64, 4, 2), (64, 8, 2), (128, 4, 2) (occupancy 2:
+ * 16 warps per SM; 3: 24 warps), and z chunks of kchunk planes.  The same
+ * bits for every configuration.  Errors: INVALID_ARG. */
+FV_API fv_status fv_batch_set_class_tuning(fv_batch_t b, int cls, int tile_x, int tile_y,
+                                           int occupancy, int kchunk);
+/* The configuration of size class cls and how many meshes it holds (any
+ * output pointer may be NULL). */
+FV_API fv_status fv_batch_get_class_tuning(fv_batch_t b, int cls, int* tile_x, int* tile_y,
+                                           int* occupancy, int* kchunk, int* meshes);
+
+/* Autotuner: for each size class in turn (most cells first, the others at
+ * their best so far) times three steps of the whole batch for every built
+ * tile shape no wider than twice the class's widest mesh (32-wide shapes
+ * always) and every z chunk in {8, 16, 32, 64}, on the batch's current
+ * state, and keeps the fastest per class (fv_batch_get_class_tuning reads
+ * them).  Reports the configuration of the class with the most cells and
+ * the final step time (any output pointer may be NULL).  The state and
+ * counters are restored afterwards (a snapshot buffer of one state is
+ * allocated on first use).  Synchronising. */
 FV_API fv_status fv_batch_autotune(fv_batch_t b, double cfl, int* kchunk, int* occupancy,
                                    int* tile_y, double* ms_per_step);
 

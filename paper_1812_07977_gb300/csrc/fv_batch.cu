@@ -51,14 +51,22 @@ struct fv_batch_s {
   double* staging = nullptr;         // dense interior staging for host copies
   double* backup = nullptr;          // state snapshot used by the autotuner
   DevCounters* host_ctr = nullptr;
-  int kchunk = 32;
-  int occupancy = 2;
-  int tile_y = 8;                    // tile height of the fused kernel (4, 8 or 16)
+  // launch configuration per size class (fv_fp32::batch_class)
+  struct Tuning {
+    int tile_x = 32, tile_y = 8, occupancy = 2, kchunk = 32;
+    bool operator==(const Tuning& o) const {
+      return tile_x == o.tile_x && tile_y == o.tile_y && occupancy == o.occupancy &&
+             kchunk == o.kchunk;
+    }
+  };
+  Tuning tune[kBatchClasses];
+  int class_meshes[kBatchClasses] = {0, 0, 0};
+  long long class_cells[kBatchClasses] = {0, 0, 0};
   bool smax_current = false;         // meshes[].smax_bits hold the current states' maxima
-  // CUDA graph of one whole step
+  // CUDA graph of one whole step and the configuration it was captured with
   cudaGraphExec_t graph = nullptr;
   double graph_cfl = -1.0;
-  int graph_kchunk = -1, graph_occupancy = -1, graph_tile_y = -1;
+  Tuning graph_tune[kBatchClasses];
 };
 
 namespace {
@@ -99,10 +107,10 @@ void free_batch(fv_batch_s* b) {
   delete b;
 }
 
-// Fused-kernel work items for a z chunk and tile height: every (mesh, tile x,
-// tile y, chunk), largest meshes first so the tail of the persistent launch
-// is short.
-fv_status build_items(fv_batch_t b, int kchunk, int tile_y) {
+// Fused-kernel work items: for each size class, every (mesh, tile x, tile y,
+// z chunk) of its meshes in the class's tile shape and z chunk, largest
+// meshes first so the tail of each persistent launch is short.
+fv_status build_items(fv_batch_t b) {
   if (b->graph) {  // the captured step refers to the item table being replaced
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
@@ -114,14 +122,20 @@ fv_status build_items(fv_batch_t b, int kchunk, int tile_y) {
     return (long long)A.nx * A.ny * A.nz > (long long)C.nx * C.ny * C.nz;
   });
   std::vector<int4> items;
-  for (int m : order) {
-    const fvd::Params& P = b->host_meshes[m].P;
-    const int tx = (P.nx + fv_fp32::kTileX - 1) / fv_fp32::kTileX;
-    const int ty = (P.ny + tile_y - 1) / tile_y;
-    const int tz = (P.nz + kchunk - 1) / kchunk;
-    for (int z = 0; z < tz; ++z)
-      for (int y = 0; y < ty; ++y)
-        for (int x = 0; x < tx; ++x) items.push_back(make_int4(m, x, y, z));
+  for (int cls = 0; cls < kBatchClasses; ++cls) {
+    const fv_batch_s::Tuning& t = b->tune[cls];
+    b->dev.class_first[cls] = (int)items.size();
+    for (int m : order) {
+      const fvd::Params& P = b->host_meshes[m].P;
+      if (fv_fp32::batch_class(P.nx) != cls) continue;
+      const int tx = (P.nx + t.tile_x - 1) / t.tile_x;
+      const int ty = (P.ny + t.tile_y - 1) / t.tile_y;
+      const int tz = (P.nz + t.kchunk - 1) / t.kchunk;
+      for (int z = 0; z < tz; ++z)
+        for (int y = 0; y < ty; ++y)
+          for (int x = 0; x < tx; ++x) items.push_back(make_int4(m, x, y, z));
+    }
+    b->dev.class_count[cls] = (int)items.size() - b->dev.class_first[cls];
   }
   cudaFree(b->dev.items);
   b->dev.items = nullptr;
@@ -130,8 +144,6 @@ fv_status build_items(fv_batch_t b, int kchunk, int tile_y) {
   e = cudaMemcpy(b->dev.items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "uploading work items");
   b->dev.nitems = (int)items.size();
-  b->kchunk = kchunk;
-  b->tile_y = tile_y;
   return FV_OK;
 }
 
@@ -141,9 +153,11 @@ fv_status build_items(fv_batch_t b, int kchunk, int tile_y) {
 cudaError_t launch_step_body(fv_batch_t b, double cfl) {
   cudaError_t e = fv_fp32::launch_batch_dt(b->dev, cfl, b->stream);
   for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage) {
-    e = fv_fp32::launch_batch_stage(stage, b->dev, b->kchunk, b->occupancy, b->tile_y,
-                                    b->num_sms,
-                                    b->stream);
+    for (int cls = 0; cls < kBatchClasses && e == cudaSuccess; ++cls) {
+      const fv_batch_s::Tuning& t = b->tune[cls];
+      e = fv_fp32::launch_batch_stage(stage, b->dev, cls, t.kchunk, t.occupancy, t.tile_x,
+                                      t.tile_y, b->num_sms, b->stream);
+    }
     if (e == cudaSuccess) e = fv_fp32::launch_batch_ghosts(stage, b->dev, b->stream);
   }
   return e;
@@ -218,6 +232,8 @@ fv_status fv_batch_create(const fv_mesh_desc* descs, int nmesh, void* cuda_strea
     off += (doubles + 31) / 32 * 32;
     const long long n = (long long)bm.P.nx * bm.P.ny * bm.P.nz;
     b->total_cells += n;
+    b->class_meshes[fv_fp32::batch_class(bm.P.nx)] += 1;
+    b->class_cells[fv_fp32::batch_class(bm.P.nx)] += n;
     b->max_dense = std::max(b->max_dense, (size_t)(fvd::NF * n));
     for (long long c = 0; c * fv_fp32::kBatchDtChunk < n; ++c) dt_blocks.push_back(make_int2(m, (int)c));
     const long long ring = fvd::ring_cells(bm.P);
@@ -232,7 +248,7 @@ fv_status fv_batch_create(const fv_mesh_desc* descs, int nmesh, void* cuda_strea
       (e = cudaMalloc(&b->dev.meshes, nmesh * sizeof(BatchMesh))) != cudaSuccess ||
       (e = cudaMalloc(&b->dev.dt_blocks, dt_blocks.size() * sizeof(int2))) != cudaSuccess ||
       (e = cudaMalloc(&b->dev.ghost_blocks, ghost_blocks.size() * sizeof(int2))) != cudaSuccess ||
-      (e = cudaMalloc(&b->dev.next_item, 2 * sizeof(unsigned))) != cudaSuccess ||
+      (e = cudaMalloc(&b->dev.next_item, 2 * kBatchClasses * sizeof(unsigned))) != cudaSuccess ||
       (e = cudaMalloc(&b->dev.ctr, sizeof(DevCounters))) != cudaSuccess ||
       (e = cudaMalloc(&b->staging, b->max_dense * sizeof(double))) != cudaSuccess ||
       (e = cudaMallocHost(&b->host_ctr, sizeof(DevCounters))) != cudaSuccess) {
@@ -258,7 +274,7 @@ fv_status fv_batch_create(const fv_mesh_desc* descs, int nmesh, void* cuda_strea
     free_batch(b);
     return cuda_fail(e, "initialising batch storage");
   }
-  fv_status st = build_items(b, 32, 8);
+  fv_status st = build_items(b);
   if (st != FV_OK) {
     free_batch(b);
     return st;
@@ -334,8 +350,9 @@ fv_status fv_batch_step(fv_batch_t b, double cfl, int use_graph) {
     if (e != cudaSuccess) return cuda_fail(e, "batch step kernels");
     return FV_OK;
   }
-  if (!b->graph || b->graph_cfl != cfl || b->graph_kchunk != b->kchunk ||
-      b->graph_occupancy != b->occupancy || b->graph_tile_y != b->tile_y) {
+  bool same_tuning = true;
+  for (int c = 0; c < kBatchClasses; ++c) same_tuning = same_tuning && b->graph_tune[c] == b->tune[c];
+  if (!b->graph || b->graph_cfl != cfl || !same_tuning) {
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;
@@ -356,9 +373,7 @@ fv_status fv_batch_step(fv_batch_t b, double cfl, int use_graph) {
       return cuda_fail(e, "instantiating the step graph");
     }
     b->graph_cfl = cfl;
-    b->graph_kchunk = b->kchunk;
-    b->graph_occupancy = b->occupancy;
-    b->graph_tile_y = b->tile_y;
+    for (int c = 0; c < kBatchClasses; ++c) b->graph_tune[c] = b->tune[c];
   }
   e = launch_max_if_stale(b);
   if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, b->stream);
@@ -391,10 +406,42 @@ fv_status fv_batch_set_tuning(fv_batch_t b, int kchunk, int occupancy, int tile_
                 kchunk, tile_y, occupancy);
   DeviceGuard g(b->device);
   cudaStreamSynchronize(b->stream);
-  if ((kchunk != b->kchunk || tile_y != b->tile_y) &&
-      (st = build_items(b, kchunk, tile_y)) != FV_OK)
-    return st;
-  b->occupancy = occupancy;
+  for (int c = 0; c < kBatchClasses; ++c) {
+    b->tune[c].tile_x = 32;
+    b->tune[c].tile_y = tile_y;
+    b->tune[c].occupancy = occupancy;
+    b->tune[c].kchunk = kchunk;
+  }
+  return build_items(b);
+}
+
+fv_status fv_batch_set_class_tuning(fv_batch_t b, int cls, int tile_x, int tile_y,
+                                    int occupancy, int kchunk) {
+  fv_status st = check(b);
+  if (st != FV_OK) return st;
+  if (cls < 0 || cls >= kBatchClasses || kchunk < 1 || kchunk > 4096 ||
+      !fv_fp32::valid_batch_config(tile_x, tile_y, occupancy))
+    return fail(FV_ERR_INVALID_ARG,
+                "class %d must be 0 .. 2, kchunk %d in [1, 4096] and (tile_x, tile_y, "
+                "occupancy) = (%d, %d, %d) one of the built shapes",
+                cls, kchunk, tile_x, tile_y, occupancy);
+  DeviceGuard g(b->device);
+  cudaStreamSynchronize(b->stream);
+  b->tune[cls] = fv_batch_s::Tuning{tile_x, tile_y, occupancy, kchunk};
+  return build_items(b);
+}
+
+fv_status fv_batch_get_class_tuning(fv_batch_t b, int cls, int* tile_x, int* tile_y,
+                                    int* occupancy, int* kchunk, int* meshes) {
+  fv_status st = check(b);
+  if (st != FV_OK) return st;
+  if (cls < 0 || cls >= kBatchClasses) return fail(FV_ERR_INVALID_ARG, "class %d not 0 .. 2", cls);
+  const fv_batch_s::Tuning& t = b->tune[cls];
+  if (tile_x) *tile_x = t.tile_x;
+  if (tile_y) *tile_y = t.tile_y;
+  if (occupancy) *occupancy = t.occupancy;
+  if (kchunk) *kchunk = t.kchunk;
+  if (meshes) *meshes = b->class_meshes[cls];
   return FV_OK;
 }
 
@@ -418,36 +465,54 @@ fv_status fv_batch_autotune(fv_batch_t b, double cfl, int* kchunk_out, int* occu
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  // times three whole steps (after one to warm up) with the current tuning
+  auto time_step = [&](double& ms_out) -> cudaError_t {
+    cudaError_t r = launch_step(b, cfl);
+    cudaEventRecord(e0, b->stream);
+    for (int i = 0; i < 3 && r == cudaSuccess; ++i) r = launch_step(b, cfl);
+    cudaEventRecord(e1, b->stream);
+    if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (r == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    ms_out = ms / 3.0;
+    return r;
+  };
+  // one size class at a time (largest first), the others at their best so
+  // far: every built shape no wider than twice the class's widest mesh and
+  // every z chunk in {8, 16, 32, 64}
   const int kcs[] = {8, 16, 32, 64};
-  const int cfgs[4][2] = {{4, 2}, {8, 2}, {8, 3}, {16, 2}};   // tile height, occupancy
+  int cls_order[kBatchClasses] = {2, 1, 0};
+  std::sort(cls_order, cls_order + kBatchClasses,
+            [&](int a, int c) { return b->class_cells[a] > b->class_cells[c]; });
   double best = 1e300;
-  int best_kc = b->kchunk, best_occ = b->occupancy, best_ty = b->tile_y;
-  for (int kc : kcs) {
-    for (const auto& cfg : cfgs) {
-      if ((st = build_items(b, kc, cfg[0])) != FV_OK) break;
-      const int occ = cfg[1];
-      b->occupancy = occ;
-      e = launch_step(b, cfl);  // warm-up
-      cudaEventRecord(e0, b->stream);
-      for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_step(b, cfl);
-      cudaEventRecord(e1, b->stream);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      if (e != cudaSuccess) break;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms / 3.0 < best) {
-        best = ms / 3.0;
-        best_kc = kc;
-        best_occ = occ;
-        best_ty = cfg[0];
+  for (int oi = 0; oi < kBatchClasses && e == cudaSuccess && st == FV_OK; ++oi) {
+    const int cls = cls_order[oi];
+    if (b->class_meshes[cls] == 0) continue;
+    int widest = 0;
+    for (const BatchMesh& m : b->host_meshes)
+      if (fv_fp32::batch_class(m.P.nx) == cls) widest = std::max(widest, m.P.nx);
+    fv_batch_s::Tuning keep = b->tune[cls];
+    double class_best = 1e300;
+    for (const auto& shape : fv_fp32::kBatchShapes) {
+      if (shape[0] > 2 * widest && shape[0] > 32) continue;
+      for (int kc : kcs) {
+        b->tune[cls] = fv_batch_s::Tuning{shape[0], shape[1], shape[2], kc};
+        if ((st = build_items(b)) != FV_OK) break;
+        double ms = 0.0;
+        if ((e = time_step(ms)) != cudaSuccess) break;
+        if (ms < class_best) {
+          class_best = ms;
+          keep = b->tune[cls];
+        }
       }
+      if (e != cudaSuccess || st != FV_OK) break;
     }
-    if (e != cudaSuccess || st != FV_OK) break;
+    b->tune[cls] = keep;
+    best = class_best;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (st == FV_OK && e == cudaSuccess) st = build_items(b, best_kc, best_ty);
-  b->occupancy = best_occ;
+  if (st == FV_OK && e == cudaSuccess) st = build_items(b);
   // restore the state (ghosts included) and the counters
   cudaError_t r = cudaMemcpyAsync(b->dev.U, b->backup, sb, cudaMemcpyDeviceToDevice, b->stream);
   if (r == cudaSuccess)
@@ -457,9 +522,11 @@ fv_status fv_batch_autotune(fv_batch_t b, double cfl, int* kchunk_out, int* occu
   if (e != cudaSuccess) return cuda_fail(e, "autotuning");
   if (r != cudaSuccess) return cuda_fail(r, "restoring the state after autotuning");
   if (st != FV_OK) return st;
-  if (kchunk_out) *kchunk_out = best_kc;
-  if (occupancy_out) *occupancy_out = best_occ;
-  if (tile_y_out) *tile_y_out = best_ty;
+  // report the configuration of the class with the most cells
+  const fv_batch_s::Tuning& t = b->tune[cls_order[0]];
+  if (kchunk_out) *kchunk_out = t.kchunk;
+  if (occupancy_out) *occupancy_out = t.occupancy;
+  if (tile_y_out) *tile_y_out = t.tile_y;
   if (ms_per_step_out) *ms_per_step_out = best;
   return FV_OK;
 }

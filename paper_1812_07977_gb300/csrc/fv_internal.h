@@ -93,7 +93,11 @@ struct BatchMesh {
   unsigned long long smax_bits;  // CFL maximum of this step (bits of a double >= 0)
 };
 
-// Device-side tables of a batch.
+// Device-side tables of a batch.  Its meshes fall into size classes by
+// their x extent (fv_fp32::batch_class), each with its own launch
+// configuration; the work items of class c are items[class_first[c] ..
+// class_first[c] + class_count[c]).
+constexpr int kBatchClasses = 3;
 struct BatchDevice {
   double* U;
   double* U1;
@@ -101,11 +105,13 @@ struct BatchDevice {
   int nmesh;
   int4* items;          // fused-kernel work items: mesh, tile x, tile y, z chunk
   int nitems;
+  int class_first[kBatchClasses];
+  int class_count[kBatchClasses];
   int2* dt_blocks;      // CFL kernel blocks: mesh, chunk of 2048 interior cells
   int ndt_blocks;
   int2* ghost_blocks;   // ghost kernel blocks: mesh, chunk of 256 ring cells
   int nghost_blocks;
-  unsigned* next_item;  // two work counters (stage 1, stage 2)
+  unsigned* next_item;  // two work counters (stage 1, stage 2) per class
   DevCounters* ctr;
   bool all_mc;          // every mesh has limiter parameter 2
 };
@@ -120,6 +126,12 @@ cudaError_t prepare_kernels();
 // {4, 8, 16}, at occupancy 2 (16 warps per SM, 128 registers), and for
 // 32 x 8 tiles also at occupancy 3 (80 registers).
 bool valid_config(int tile_y, int occupancy);
+// The batched kernel is built for these (tile x, tile y, occupancy).
+constexpr int kBatchShapes[8][3] = {{32, 4, 2}, {32, 8, 2}, {32, 8, 3}, {32, 16, 2},
+                                    {16, 8, 2}, {64, 4, 2}, {64, 8, 2}, {128, 4, 2}};
+bool valid_batch_config(int tile_x, int tile_y, int occupancy);
+// Size class of a mesh of nx cells along x: 0 up to 24, 1 up to 64, 2 above.
+inline int batch_class(int nx) { return nx <= 24 ? 0 : nx <= 64 ? 1 : 2; }
 cudaError_t launch_stage(int stage, const StepBuffers& b, const fvd::Params& P, double dt,
                          int kchunk, double vacuum_ratio, int occupancy, int tile_y,
                          cudaStream_t s);
@@ -132,11 +144,13 @@ cudaError_t launch_reduce_dt(const double* U, const fvd::Params& P, double vacuu
 // and the ghost fill.
 constexpr int kBatchDtChunk = 2048;
 constexpr int kBatchGhostChunk = 256;
-constexpr int kTileX = 32;
 cudaError_t launch_batch_max(const BatchDevice& b, cudaStream_t s);
 cudaError_t launch_batch_dt(const BatchDevice& b, double cfl, cudaStream_t s);
-cudaError_t launch_batch_stage(int stage, const BatchDevice& b, int kchunk, int occupancy,
-                               int tile_y, int num_sms, cudaStream_t s);
+// One persistent launch over the work items of size class `cls` (a no-op if
+// the class has none).
+cudaError_t launch_batch_stage(int stage, const BatchDevice& b, int cls, int kchunk,
+                               int occupancy, int tile_x, int tile_y, int num_sms,
+                               cudaStream_t s);
 cudaError_t launch_batch_ghosts(int stage, const BatchDevice& b, cudaStream_t s);
 fvd32::Params32 make_params32(const fvd::Params& P, double vacuum_ratio);
 }

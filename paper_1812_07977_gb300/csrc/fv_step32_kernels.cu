@@ -38,18 +38,19 @@ using namespace fvd32;
 namespace fv_fp32 {
 namespace {
 
-constexpr int TX = 32;   // tile width: one warp per tile row
-
-// A tile of TX x TY columns (TY = 4, 8 or 16: 128, 256 or 512 threads, one
-// per column) with its plane buffer (two-cell halo), halo cells and faces.
-template <int TY_>
+// A tile of TX x TY columns (one thread per column: TX = 32 is one warp per
+// tile row; the single-mesh kernel uses 32 x 4, 8 or 16, batches also 16 x 8,
+// 64 x 4, 64 x 8 and 128 x 4) with its plane buffer (two-cell halo), halo
+// cells and faces.
+template <int TX_, int TY_>
 struct Shape {
+  static constexpr int TX = TX_;
   static constexpr int TY = TY_;
   static constexpr int kThreads = TX * TY;
   static constexpr int PX = TX + 4;
   static constexpr int PY = TY + 4;
-  static constexpr int kHalo = PX * PY - TX * TY;        // 160, 176, 208
-  static constexpr int kHaloPer = (kHalo + kThreads - 1) / kThreads;  // 2, 1, 1
+  static constexpr int kHalo = PX * PY - TX * TY;
+  static constexpr int kHaloPer = (kHalo + kThreads - 1) / kThreads;
   static constexpr int kXFaces = (TX + 1) * TY;
   static constexpr int kYFaces = TX * (TY + 1);
   static_assert(kXFaces <= 2 * kThreads && kYFaces <= 2 * kThreads, "two face passes");
@@ -80,7 +81,7 @@ __device__ __forceinline__ void halo_cell(int h, int& row, int& col) {
     const int u = h - 4 * PX;
     row = u / 4;
     const int c = u % 4;
-    col = c < 2 ? c - 2 : TX + c - 2;
+    col = c < 2 ? c - 2 : S::TX + c - 2;
   }
 }
 
@@ -100,8 +101,8 @@ struct Smem {
   double col[kRing][NF][S::kThreads];
   double halo[kRing][NF][S::kHalo];
   float w[NF][S::PY][S::PX];
-  float fx[NF][S::TY][TX + 1];
-  float fy[NF][S::TY + 1][TX];
+  float fx[NF][S::TY][S::TX + 1];
+  float fy[NF][S::TY + 1][S::TX];
   unsigned char same[S::PY][S::PX];   // cell equals (bit for bit) the cell one plane below
 };
 
@@ -209,6 +210,7 @@ __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
   SpeedCache speed_cache;
   speed_cache.valid = false;
   const double* __restrict__ src = STAGE == 1 ? U : U1;
+  constexpr int TX = S::TX;
   const int tid = threadIdx.x;
   const int ti = tid % TX, tj = tid / TX;
   const long long nf = P.nfield;
@@ -435,11 +437,11 @@ __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
   bad_out += bad;
 }
 
-template <int STAGE, int TY, int MINB, bool MC>
+template <int STAGE, int TX, int TY, int MINB, bool MC>
 __global__ void __launch_bounds__(TX * TY, MINB)
 k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params32 Q, float dt,
           int kchunk, DevCounters* ctr) {
-  using S = Shape<TY>;
+  using S = Shape<TX, TY>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<S>& s = *reinterpret_cast<Smem<S>*>(smem_raw);
   unsigned fallbacks = 0, evaluated = 0;
@@ -464,12 +466,12 @@ k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params
 // (mesh, tile x, tile y, z chunk) from an atomic counter until none is left.
 // Stage 2 also folds the CFL maximum of each item's output cells into its
 // mesh's smax_bits (the next step's dt).
-template <int STAGE, int TY, int MINB, bool MC>
+template <int STAGE, int TX, int TY, int MINB, bool MC>
 __global__ void __launch_bounds__(TX * TY, MINB)
 k_stage32_batch(double* __restrict__ U, double* __restrict__ U1, BatchMesh* __restrict__ meshes,
                 const int4* __restrict__ items, int nitems, int kchunk,
                 unsigned* __restrict__ next_item, DevCounters* ctr) {
-  using S = Shape<TY>;
+  using S = Shape<TX, TY>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<S>& s = *reinterpret_cast<Smem<S>*>(smem_raw);
   __shared__ int s_item;
@@ -581,7 +583,7 @@ k_batch_dt(const double* __restrict__ U, BatchMesh* __restrict__ meshes,
 // Clears the per-mesh maxima and the work counters before a step.
 __global__ void k_batch_reset(BatchMesh* __restrict__ meshes, int nmesh, unsigned* next_item) {
   for (int m = threadIdx.x; m < nmesh; m += blockDim.x) meshes[m].smax_bits = 0ULL;
-  if (threadIdx.x < 2) next_item[threadIdx.x] = 0u;
+  if (threadIdx.x < 2 * kBatchClasses) next_item[threadIdx.x] = 0u;
 }
 
 // dt = cfl / max, formed in FP64 per mesh (0 if the mesh had no physical cell).
@@ -629,31 +631,48 @@ Params32 make_params32(const fvd::Params& P, double vacuum_ratio) {
   return Q;
 }
 
-// Kernel configurations: tile height TY and CTAs per SM (MINB).  Occupancy 2
-// is 16 warps per SM at up to 128 registers for every tile height; occupancy
-// 3 (24 warps, 80 registers) exists for the 32 x 8 tile.
-__host__ __device__ constexpr int minb_of(int tile_y, int occupancy) {
-  return occupancy == 2 ? 16 / tile_y : occupancy == 3 && tile_y == 8 ? 3 : 0;
+// Kernel configurations: tile (TX x TY) and CTAs per SM (MINB).  Occupancy 2
+// is 16 warps per SM at up to 128 registers for every tile; occupancy 3
+// (24 warps, 80 registers) exists for the 32 x 8 tile.
+__host__ __device__ constexpr int minb_of(int tile_x, int tile_y, int occupancy) {
+  return occupancy == 2 ? 512 / (tile_x * tile_y)
+         : occupancy == 3 && tile_x == 32 && tile_y == 8 ? 3 : 0;
 }
 
-// Calls fn.template run<STAGE, TY, MINB, MC>() for a configuration, or
-// returns cudaErrorInvalidValue for one that is not built.
-template <class Fn>
-static cudaError_t dispatch(int stage, int tile_y, int occupancy, bool mc, Fn& fn) {
-#define FV32_CASE(TYV, MB)                                                                  \
-  if (tile_y == TYV && minb_of(tile_y, occupancy) == MB) {                                  \
-    if (mc)                                                                                 \
-      return stage == 1 ? fn.template run<1, TYV, MB, true>() : fn.template run<2, TYV, MB, true>(); \
-    return stage == 1 ? fn.template run<1, TYV, MB, false>()                                \
-                      : fn.template run<2, TYV, MB, false>();                               \
+// Calls fn.template run<STAGE, TX, TY, MINB, MC>() for a configuration, or
+// returns cudaErrorInvalidValue for one that is not built.  The single-mesh
+// kernel is built for the 32-wide tiles, the batched one for all.
+#define FV32_CASE(TXV, TYV, MB)                                                              \
+  if (tile_x == TXV && tile_y == TYV && minb_of(tile_x, tile_y, occupancy) == MB) {          \
+    if (mc)                                                                                  \
+      return stage == 1 ? fn.template run<1, TXV, TYV, MB, true>()                           \
+                        : fn.template run<2, TXV, TYV, MB, true>();                          \
+    return stage == 1 ? fn.template run<1, TXV, TYV, MB, false>()                            \
+                      : fn.template run<2, TXV, TYV, MB, false>();                           \
   }
-  FV32_CASE(4, 4)
-  FV32_CASE(8, 2)
-  FV32_CASE(8, 3)
-  FV32_CASE(16, 1)
-#undef FV32_CASE
+template <class Fn>
+static cudaError_t dispatch_mesh(int stage, int tile_x, int tile_y, int occupancy, bool mc,
+                                 Fn& fn) {
+  FV32_CASE(32, 4, 4)
+  FV32_CASE(32, 8, 2)
+  FV32_CASE(32, 8, 3)
+  FV32_CASE(32, 16, 1)
   return cudaErrorInvalidValue;
 }
+template <class Fn>
+static cudaError_t dispatch_batch(int stage, int tile_x, int tile_y, int occupancy, bool mc,
+                                  Fn& fn) {
+  FV32_CASE(32, 4, 4)
+  FV32_CASE(32, 8, 2)
+  FV32_CASE(32, 8, 3)
+  FV32_CASE(32, 16, 1)
+  FV32_CASE(16, 8, 4)
+  FV32_CASE(64, 4, 2)
+  FV32_CASE(64, 8, 1)
+  FV32_CASE(128, 4, 1)
+  return cudaErrorInvalidValue;
+}
+#undef FV32_CASE
 
 struct LaunchMesh {
   const StepBuffers& b;
@@ -662,11 +681,11 @@ struct LaunchMesh {
   float dt;
   int kchunk;
   cudaStream_t s;
-  template <int STAGE, int TY, int MINB, bool MC>
+  template <int STAGE, int TX, int TY, int MINB, bool MC>
   cudaError_t run() {
-    using S = Shape<TY>;
+    using S = Shape<TX, TY>;
     const dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + kchunk - 1) / kchunk);
-    k_stage32<STAGE, TY, MINB, MC><<<grid, S::kThreads, sizeof(Smem<S>), s>>>(
+    k_stage32<STAGE, TX, TY, MINB, MC><<<grid, S::kThreads, sizeof(Smem<S>), s>>>(
         b.U, b.U1, P, Q, dt, kchunk, b.ctr);
     return cudaGetLastError();
   }
@@ -674,54 +693,69 @@ struct LaunchMesh {
 
 struct LaunchBatch {
   const BatchDevice& b;
+  int cls;
   int kchunk;
-  int grid_per_sm_unit;  // SMs
+  int sms;
   unsigned* counter;
   cudaStream_t s;
-  template <int STAGE, int TY, int MINB, bool MC>
+  template <int STAGE, int TX, int TY, int MINB, bool MC>
   cudaError_t run() {
-    using S = Shape<TY>;
-    k_stage32_batch<STAGE, TY, MINB, MC><<<grid_per_sm_unit * MINB, S::kThreads,
-                                           sizeof(Smem<S>), s>>>(
-        b.U, b.U1, b.meshes, b.items, b.nitems, kchunk, counter, b.ctr);
+    using S = Shape<TX, TY>;
+    k_stage32_batch<STAGE, TX, TY, MINB, MC><<<sms * MINB, S::kThreads, sizeof(Smem<S>), s>>>(
+        b.U, b.U1, b.meshes, b.items + b.class_first[cls], b.class_count[cls], kchunk, counter,
+        b.ctr);
     return cudaGetLastError();
   }
 };
 
-// Raises the dynamic shared-memory limit of both kernels of a configuration
-// (the plane buffers and staging ring take more than the default 48 KB).
-struct RaiseSmem {
-  template <int STAGE, int TY, int MINB, bool MC>
+// Raises the dynamic shared-memory limit of a configuration's kernels (the
+// plane buffers and staging ring take more than the default 48 KB).
+struct RaiseSmemMesh {
+  template <int STAGE, int TX, int TY, int MINB, bool MC>
   cudaError_t run() {
-    const int bytes = (int)sizeof(Smem<Shape<TY>>);
-    cudaError_t e = cudaFuncSetAttribute(k_stage32<STAGE, TY, MINB, MC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_stage32_batch<STAGE, TY, MINB, MC>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return e;
+    return cudaFuncSetAttribute(k_stage32<STAGE, TX, TY, MINB, MC>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(Smem<Shape<TX, TY>>));
+  }
+};
+struct RaiseSmemBatch {
+  template <int STAGE, int TX, int TY, int MINB, bool MC>
+  cudaError_t run() {
+    return cudaFuncSetAttribute(k_stage32_batch<STAGE, TX, TY, MINB, MC>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(Smem<Shape<TX, TY>>));
   }
 };
 
 bool valid_config(int tile_y, int occupancy) {
-  return (tile_y == 4 || tile_y == 8 || tile_y == 16) && minb_of(tile_y, occupancy) > 0;
+  return (tile_y == 4 || tile_y == 8 || tile_y == 16) && minb_of(32, tile_y, occupancy) > 0;
+}
+
+bool valid_batch_config(int tile_x, int tile_y, int occupancy) {
+  for (const auto& c : kBatchShapes)
+    if (c[0] == tile_x && c[1] == tile_y && c[2] == occupancy) return true;
+  return false;
 }
 
 cudaError_t launch_stage(int stage, const StepBuffers& b, const fvd::Params& P, double dt,
                          int kchunk, double vacuum_ratio, int occupancy, int tile_y,
                          cudaStream_t s) {
   LaunchMesh fn{b, P, make_params32(P, vacuum_ratio), (float)dt, kchunk < 1 ? 1 : kchunk, s};
-  return dispatch(stage, tile_y, occupancy, fn.Q.theta == 2.0f, fn);
+  return dispatch_mesh(stage, 32, tile_y, occupancy, fn.Q.theta == 2.0f, fn);
 }
 
 cudaError_t prepare_kernels() {
-  RaiseSmem fn;
+  RaiseSmemMesh fm;
+  RaiseSmemBatch fb;
   const int cfg[4][2] = {{4, 2}, {8, 2}, {8, 3}, {16, 2}};
   cudaError_t e = cudaSuccess;
-  for (int c = 0; c < 4 && e == cudaSuccess; ++c)
-    for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage)
-      for (int mc = 0; mc < 2 && e == cudaSuccess; ++mc)
-        e = dispatch(stage, cfg[c][0], cfg[c][1], mc != 0, fn);
+  for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage)
+    for (int mc = 0; mc < 2 && e == cudaSuccess; ++mc) {
+      for (int c = 0; c < 4 && e == cudaSuccess; ++c)
+        e = dispatch_mesh(stage, 32, cfg[c][0], cfg[c][1], mc != 0, fm);
+      for (const auto& c : kBatchShapes)
+        if (e == cudaSuccess) e = dispatch_batch(stage, c[0], c[1], c[2], mc != 0, fb);
+    }
   return e;
 }
 
@@ -754,10 +788,12 @@ cudaError_t launch_batch_dt(const BatchDevice& b, double cfl, cudaStream_t s) {
 
 // The MC form when every mesh of the batch has limiter parameter 2, else the
 // general form for all (same results as each mesh's single-mesh kernel).
-cudaError_t launch_batch_stage(int stage, const BatchDevice& b, int kchunk, int occupancy,
-                               int tile_y, int num_sms, cudaStream_t s) {
-  LaunchBatch fn{b, kchunk, num_sms, b.next_item + (stage == 1 ? 0 : 1), s};
-  return dispatch(stage, tile_y, occupancy, b.all_mc, fn);
+cudaError_t launch_batch_stage(int stage, const BatchDevice& b, int cls, int kchunk,
+                               int occupancy, int tile_x, int tile_y, int num_sms,
+                               cudaStream_t s) {
+  if (b.class_count[cls] == 0) return cudaSuccess;
+  LaunchBatch fn{b, cls, kchunk, num_sms, b.next_item + 2 * cls + (stage == 1 ? 0 : 1), s};
+  return dispatch_batch(stage, tile_x, tile_y, occupancy, b.all_mc, fn);
 }
 
 cudaError_t launch_batch_ghosts(int stage, const BatchDevice& b, cudaStream_t s) {

@@ -29,7 +29,8 @@ ABI_SYMBOLS = (
     "fv_mesh_info", "fv_status_string", "fv_last_error", "fv_conserved_sums_noalloc",
     "fv_batch_create", "fv_batch_destroy", "fv_batch_set_state", "fv_batch_get_state",
     "fv_batch_step", "fv_batch_get_dt", "fv_batch_set_tuning", "fv_batch_autotune",
-    "fv_batch_get_counters", "fv_batch_info",
+    "fv_batch_get_counters", "fv_batch_info", "fv_batch_set_class_tuning",
+    "fv_batch_get_class_tuning",
     "fv_net_param_count", "fv_net_create", "fv_net_destroy", "fv_net_set_params",
     "fv_net_get_params", "fv_net_set_scales", "fv_net_forward", "fv_net_train_step",
     "fv_step_learned", "fv_net_get_buffer",
@@ -94,6 +95,8 @@ def load_library(path: str | None = None):
         "fv_batch_set_tuning": ([vp, i, i, i], i),
         "fv_batch_autotune": ([vp, d, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                                dp], i),
+        "fv_batch_set_class_tuning": ([vp, i, i, i, i, i], i),
+        "fv_batch_get_class_tuning": ([vp, i] + [ctypes.POINTER(i)] * 5, i),
         "fv_batch_get_counters": ([vp, ctypes.POINTER(ctypes.c_longlong),
                                    ctypes.POINTER(ctypes.c_longlong)], i),
         "fv_batch_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong),
@@ -407,6 +410,20 @@ class Batch:
     def set_tuning(self, kchunk, occupancy=2, tile_y=8):
         _check(self._lib.fv_batch_set_tuning(self._h, int(kchunk), int(occupancy), int(tile_y)),
                "fv_batch_set_tuning")
+
+    def set_class_tuning(self, cls, tile_x, tile_y, occupancy, kchunk):
+        _check(self._lib.fv_batch_set_class_tuning(self._h, int(cls), int(tile_x), int(tile_y),
+                                                   int(occupancy), int(kchunk)),
+               "fv_batch_set_class_tuning")
+
+    def class_tuning(self, cls):
+        """{tile_x, tile_y, occupancy, kchunk, meshes} of size class cls."""
+        v = [ctypes.c_int() for _ in range(5)]
+        _check(self._lib.fv_batch_get_class_tuning(self._h, int(cls),
+                                                   *[ctypes.byref(x) for x in v]),
+               "fv_batch_get_class_tuning")
+        return dict(zip(("tile_x", "tile_y", "occupancy", "kchunk", "meshes"),
+                        (x.value for x in v)))
 
     def autotune(self, cfl=0.4):
         """(kchunk, occupancy, tile_y, ms per step) of the fastest configuration."""

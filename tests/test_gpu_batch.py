@@ -196,3 +196,46 @@ def test_batch_rejects_bad_arguments():
             b.set_tuning(8, 3, 16)
         with pytest.raises(FvError):
             b.step(-1.0)
+
+
+@pytest.mark.parametrize("shapes", [((16, 8, 2), (64, 4, 2), (128, 4, 2)),
+                                    ((32, 4, 2), (64, 8, 2), (64, 4, 2)),
+                                    ((16, 8, 2), (16, 8, 2), (32, 16, 2))])
+def test_batch_class_tunings_same_bits(shapes):
+    """Each size class with its own tile shape (16, 32, 64 or 128 columns
+    wide) and z chunk gives every mesh the bits of its single-mesh run: the
+    tiles change only which thread computes a face, not how."""
+    from paper_1812_07977_gb300.fv import Batch
+    spec = problems.batched_riemann(seed=21, count=7, lengths=(8, 16, 24, 40, 56, 72, 100))
+    ref = _single_runs(spec, 3)
+    with Batch([s["shape"] for s in spec]) as b:
+        for cls, (tx, ty, occ) in enumerate(shapes):
+            b.set_class_tuning(cls, tx, ty, occ, (5, 16, 64)[cls])
+            assert b.class_tuning(cls)["tile_x"] == tx
+        assert sum(b.class_tuning(c)["meshes"] for c in range(3)) == len(spec)
+        for m, s in enumerate(spec):
+            b.set_state(m, s["U0"])
+        for _ in range(3):
+            b.step(0.4)
+        for m in range(len(spec)):
+            assert np.array_equal(b.get_state(m).cpu().numpy(), ref[m]), m
+
+
+def test_batch_autotune_per_class_restores_state():
+    """The autotuner leaves a valid configuration per class and the state it
+    found; stepping afterwards matches single-mesh runs."""
+    from paper_1812_07977_gb300.fv import Batch
+    spec = problems.batched_riemann(seed=22, count=6, lengths=(16, 40, 72))
+    ref = _single_runs(spec, 2)
+    with Batch([s["shape"] for s in spec]) as b:
+        for m, s in enumerate(spec):
+            b.set_state(m, s["U0"])
+        kc, occ, ty, ms = b.autotune(0.4)
+        assert ms > 0
+        for cls in range(3):
+            t = b.class_tuning(cls)
+            assert t["tile_x"] in (16, 32, 64, 128) and t["kchunk"] in (8, 16, 32, 64)
+        for _ in range(2):
+            b.step(0.4)
+        for m in range(len(spec)):
+            assert np.array_equal(b.get_state(m).cpu().numpy(), ref[m]), m
