@@ -430,13 +430,21 @@ FV_API fv_status fv_conserved_sums_noalloc(const double* U, int nx, int ny, int 
  *                        0.99; a value > 1 turns the recovery off)
  *  FV_TUNE_OCCUPANCY     occupancy the fused FP32-bulk kernel is built for:
  *                        2 (16 warps per SM, up to 128 registers, default)
- *                        or 3 (24 warps, 80 registers; tile height 8 only);
+ *                        or 3 (24 warps, 80 registers; 32 x 8 tiles only);
  *                        for FP64_FF meshes the CTAs per SM of its fused
  *                        kernel: 2 (16 warps, 128 registers, default) or 1
  *                        (8 warps, up to 255 registers); the same bits
  *  FV_TUNE_TILE_Y        tile height of the fused FP32-bulk kernel: 4, 8
- *                        (default) or 16 (tiles of 32 x 4 / 8 / 16 columns,
- *                        CTAs of 128 / 256 / 512 threads); the same bits
+ *                        (default) or 16 (CTAs of TX x TY threads, one per
+ *                        column; 4 and 16 at width 32 only); for FP64_FF
+ *                        meshes 8 (default), or 12 or 16 at occupancy 1
+ *                        (set the occupancy first); the same bits
+ *  FV_TUNE_TILE_X        tile width of the fused FP32-bulk kernel: 16
+ *                        (default), 32, 64 or 128.  (tile x, tile y,
+ *                        occupancy) must be one of (32, 4|8|16, 2),
+ *                        (32, 8, 3), (16, 8, 2), (64, 4|8, 2), (128, 4, 2)
+ *                        after each change, so change them in an order that
+ *                        passes through built shapes; the same bits
  *  FV_TUNE_SWEEP_SEGMENTS  FP64 sweeps: pieces each grid line of a sweep is
  *                        cut into, to run more, shorter work items (integer
  *                        in [0, 4096], capped at the line's length; 0, the
@@ -461,7 +469,8 @@ typedef enum {
   FV_TUNE_OCCUPANCY = 2,
   FV_TUNE_SWEEP_SEGMENTS = 3,
   FV_TUNE_TILE_Y = 4,
-  FV_TUNE_FP64_FUSED = 5
+  FV_TUNE_FP64_FUSED = 5,
+  FV_TUNE_TILE_X = 6
 } fv_tuning_key;
 FV_API fv_status fv_set_tuning(fv_mesh_t m, int key, double value);
 

@@ -399,7 +399,7 @@ fv_status fv_batch_get_dt(fv_batch_t b, double* dt) {
 fv_status fv_batch_set_tuning(fv_batch_t b, int kchunk, int occupancy, int tile_y) {
   fv_status st = check(b);
   if (st != FV_OK) return st;
-  if (kchunk < 1 || kchunk > 4096 || !fv_fp32::valid_config(tile_y, occupancy))
+  if (kchunk < 1 || kchunk > 4096 || !fv_fp32::valid_config(32, tile_y, occupancy))
     return fail(FV_ERR_INVALID_ARG,
                 "kchunk %d must be in [1, 4096], tile_y (%d) 4, 8 or 16 and occupancy (%d) 2, "
                 "or 3 with tile_y 8",
@@ -420,7 +420,7 @@ fv_status fv_batch_set_class_tuning(fv_batch_t b, int cls, int tile_x, int tile_
   fv_status st = check(b);
   if (st != FV_OK) return st;
   if (cls < 0 || cls >= kBatchClasses || kchunk < 1 || kchunk > 4096 ||
-      !fv_fp32::valid_batch_config(tile_x, tile_y, occupancy))
+      !fv_fp32::valid_config(tile_x, tile_y, occupancy))
     return fail(FV_ERR_INVALID_ARG,
                 "class %d must be 0 .. 2, kchunk %d in [1, 4096] and (tile_x, tile_y, "
                 "occupancy) = (%d, %d, %d) one of the built shapes",
@@ -493,7 +493,7 @@ fv_status fv_batch_autotune(fv_batch_t b, double cfl, int* kchunk_out, int* occu
       if (fv_fp32::batch_class(m.P.nx) == cls) widest = std::max(widest, m.P.nx);
     fv_batch_s::Tuning keep = b->tune[cls];
     double class_best = 1e300;
-    for (const auto& shape : fv_fp32::kBatchShapes) {
+    for (const auto& shape : fv_fp32::kShapes) {
       if (shape[0] > 2 * widest && shape[0] > 32) continue;
       for (int kc : kcs) {
         b->tune[cls] = fv_batch_s::Tuning{shape[0], shape[1], shape[2], kc};

@@ -60,10 +60,11 @@ struct fv_mesh_s {
   int kchunk;               // z planes per CTA of the fused FP32-bulk kernel
   double vacuum_ratio;      // FP32-bulk FP64 pressure-recovery threshold
   int occupancy;            // CTAs per SM the fused kernel is compiled for (2 or 3)
-  int tile_y;               // tile height of the fused kernel (4, 8 or 16)
+  int tile_x, tile_y;       // tile of the fused FP32-bulk kernel (fv_fp32::kShapes)
   int segments;             // pieces per grid line of the FP64 sweeps (0: automatic)
   bool fused64;             // FP64: one fused kernel per substep (else the per-axis sweeps)
   int ff_ctas_per_sm;       // FP64_FF: CTAs per SM its fused kernel is built for (1 or 2)
+  int ff_tile_y;            // FP64_FF: tile height of its fused kernel (8, 12 or 16)
   bool w_current;           // FP64 sweeps: W holds the primitives of U (from the dt pass)
   bool smax_current;        // fused paths: ctr->smax_next is the CFL maximum of U
   // profiling
@@ -268,7 +269,7 @@ cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
     if (e == cudaSuccess)
       e = timed(m, FV_KERNEL_FUSED, 1, [&] {
         if (ff)
-          return fv_fp64_ff::launch_fused(stage, m->buf, m->P, dt, m->kchunk,
+          return fv_fp64_ff::launch_fused(stage, m->buf, m->P, dt, m->kchunk, m->ff_tile_y,
                                           m->ff_ctas_per_sm, m->stream);
         return fma ? fv_fp64_fma::launch_fused(stage, m->buf, m->P, dt, m->kchunk, m->stream)
                    : fv_fp64_exact::launch_fused(stage, m->buf, m->P, dt, m->kchunk,
@@ -289,7 +290,7 @@ cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
     if (e == cudaSuccess)
       e = timed(m, FV_KERNEL_FUSED, 1, [&] {
         return fv_fp32::launch_stage(stage, m->buf, m->P, dt, m->kchunk, m->vacuum_ratio,
-                                     m->occupancy, m->tile_y, m->stream);
+                                     m->occupancy, m->tile_x, m->tile_y, m->stream);
       });
     if (e != cudaSuccess) return e;
     double* dst = stage == 1 ? m->buf.U1 : m->buf.U;
@@ -350,10 +351,12 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
               : desc->nz >= 64 ? 32 : desc->nz;
   m->vacuum_ratio = 0.99;
   m->occupancy = 2;
+  m->tile_x = 16;   // 16 x 8: per-warp reuse decisions over 16 x 2 cells
   m->tile_y = 8;
   m->segments = 0;
   m->fused64 = false;
   m->ff_ctas_per_sm = 2;
+  m->ff_tile_y = 8;
   m->w_current = false;
   m->smax_current = false;
   for (int c = 0; c < FV_KERNEL_NCLASS; ++c) m->launches[c] = 0;
@@ -644,29 +647,43 @@ fv_status fv_set_tuning(fv_mesh_t m, int key, double value) {
     return FV_OK;
   }
   if (key == FV_TUNE_OCCUPANCY && m->desc.precision == FV_PREC_FP64_FF) {
-    if (value != 1.0 && value != 2.0) {
-      set_error("FV_TUNE_OCCUPANCY of the float-float kernel must be 1 or 2 (got %g)", value);
+    if ((value != 1.0 && value != 2.0) ||
+        !fv_fp64_ff::valid_fused_config(m->ff_tile_y, (int)value)) {
+      set_error("FV_TUNE_OCCUPANCY of the float-float kernel must be 1, or 2 with tile height "
+                "8 (got %g, tile height %d)", value, m->ff_tile_y);
       return FV_ERR_INVALID_ARG;
     }
     m->ff_ctas_per_sm = (int)value;
     return FV_OK;
   }
-  if (key == FV_TUNE_OCCUPANCY) {
-    if ((value != 2.0 && value != 3.0) || !fv_fp32::valid_config(m->tile_y, (int)value)) {
-      set_error("FV_TUNE_OCCUPANCY must be 2, or 3 with tile height 8 (got %g, tile height %d)",
-                value, m->tile_y);
+  if (key == FV_TUNE_TILE_Y && m->desc.precision == FV_PREC_FP64_FF) {
+    if ((value != 8.0 && value != 12.0 && value != 16.0) ||
+        !fv_fp64_ff::valid_fused_config((int)value, m->ff_ctas_per_sm)) {
+      set_error("FV_TUNE_TILE_Y of the float-float kernel must be 8, or 12 or 16 at occupancy 1 "
+                "(got %g, occupancy %d)", value, m->ff_ctas_per_sm);
       return FV_ERR_INVALID_ARG;
     }
-    m->occupancy = (int)value;
+    m->ff_tile_y = (int)value;
     return FV_OK;
   }
-  if (key == FV_TUNE_TILE_Y) {
-    if ((value != 4.0 && value != 8.0 && value != 16.0) ||
-        !fv_fp32::valid_config((int)value, m->occupancy)) {
-      set_error("FV_TUNE_TILE_Y must be 4, 8 or 16, and 8 at occupancy 3 (got %g)", value);
+  if (key == FV_TUNE_OCCUPANCY || key == FV_TUNE_TILE_Y || key == FV_TUNE_TILE_X) {
+    // the FP32-bulk kernel's (tile x, tile y, occupancy) must stay one of the
+    // built shapes after the change
+    const int v = (int)value;
+    const bool integral = value == (double)v;
+    const int tx = key == FV_TUNE_TILE_X ? v : m->tile_x;
+    const int ty = key == FV_TUNE_TILE_Y ? v : m->tile_y;
+    const int oc = key == FV_TUNE_OCCUPANCY ? v : m->occupancy;
+    if (!integral || !fv_fp32::valid_config(tx, ty, oc)) {
+      set_error("tuning key %d = %g would make (tile_x, tile_y, occupancy) = (%d, %d, %d), not "
+                "a built shape of the FP32-bulk kernel: (32, 4|8|16, 2), (32, 8, 3), (16, 8, 2), "
+                "(64, 4|8, 2), (128, 4, 2)",
+                (int)key, value, tx, ty, oc);
       return FV_ERR_INVALID_ARG;
     }
-    m->tile_y = (int)value;
+    m->tile_x = tx;
+    m->tile_y = ty;
+    m->occupancy = oc;
     return FV_OK;
   }
   if (key == FV_TUNE_FP64_FUSED) {

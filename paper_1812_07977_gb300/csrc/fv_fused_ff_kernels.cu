@@ -417,15 +417,16 @@ __device__ __forceinline__ void max_to(unsigned long long* dst, double smax) {
   if ((threadIdx.x & 31u) == 0u && b) atomicMax(dst, b);
 }
 
-constexpr int kTileY = 8;
-
-// MINB: CTAs per SM the kernel is built for (1: up to 255 registers, 8 warps
-// per SM; 2: 128 registers, 16 warps per SM)
-template <int STAGE, bool MC, int MINB>
-__global__ void __launch_bounds__(TX * kTileY, MINB)
+// TY: tile height (tiles of 32 x TY columns, one thread per column); MINB:
+// CTAs per SM the kernel is built for.  Built as 32 x 8 at 1 CTA per SM (8
+// warps, up to 255 registers) or 2 (16 warps, 128 registers, with spills),
+// 32 x 12 at 1 (12 warps, 168 registers) and 32 x 16 at 1 (16 warps, 128
+// registers): more columns per CTA share each halo cell's conversion.
+template <int STAGE, bool MC, int TY, int MINB>
+__global__ void __launch_bounds__(TX * TY, MINB)
 k_stageff(double* __restrict__ U, double* __restrict__ U1, Params P, fvd32::Params32 Q32,
           ConstFF C, double dt, int kchunk, DevCounters* ctr) {
-  using S = Shape64<kTileY>;
+  using S = Shape64<TY>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmemFF<S>& s = *reinterpret_cast<SmemFF<S>*>(smem_raw);
   unsigned fallbacks = 0, evaluated = 0;
@@ -433,7 +434,7 @@ k_stageff(double* __restrict__ U, double* __restrict__ U1, Params P, fvd32::Para
   double smax = 0.0;
   float smax_f = 0.0f;
   const int k0 = blockIdx.z * kchunk;
-  stageff_tile<S, STAGE, MC>(s, U, U1, P, Q32, C, dt, blockIdx.x * TX, blockIdx.y * kTileY, k0,
+  stageff_tile<S, STAGE, MC>(s, U, U1, P, Q32, C, dt, blockIdx.x * TX, blockIdx.y * TY, k0,
                              min(k0 + kchunk, P.nz), fallbacks, bad, range, evaluated, smax,
                              smax_f, bad_next, &ctr->smax_next);
   if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
@@ -505,53 +506,66 @@ ConstFF make_const(const Params& P) {
   return C;
 }
 
-template <int STAGE, bool MC, int MINB>
+template <int STAGE, bool MC, int TY, int MINB>
 cudaError_t launch_mc(const StepBuffers& b, const Params& P, double dt, int kchunk,
                       cudaStream_t s) {
-  using S = Shape64<kTileY>;
-  const dim3 grid((P.nx + TX - 1) / TX, (P.ny + kTileY - 1) / kTileY,
-                  (P.nz + kchunk - 1) / kchunk);
-  k_stageff<STAGE, MC, MINB><<<grid, S::kThreads, sizeof(SmemFF<S>), s>>>(
+  using S = Shape64<TY>;
+  const dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + kchunk - 1) / kchunk);
+  k_stageff<STAGE, MC, TY, MINB><<<grid, S::kThreads, sizeof(SmemFF<S>), s>>>(
       b.U, b.U1, P, fv_fp32::make_params32(P, 2.0), make_const(P), dt, kchunk, b.ctr);
   return cudaGetLastError();
 }
 
-template <bool MC, int MINB>
+template <bool MC, int TY, int MINB>
 cudaError_t raise_smem() {
-  const int bytes = (int)sizeof(SmemFF<Shape64<kTileY>>);
-  cudaError_t e = cudaFuncSetAttribute(k_stageff<1, MC, MINB>,
+  const int bytes = (int)sizeof(SmemFF<Shape64<TY>>);
+  cudaError_t e = cudaFuncSetAttribute(k_stageff<1, MC, TY, MINB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_stageff<2, MC, MINB>,
+    e = cudaFuncSetAttribute(k_stageff<2, MC, TY, MINB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   return e;
 }
 
+template <int TY, int MINB>
+cudaError_t raise_both() {
+  cudaError_t e = raise_smem<true, TY, MINB>();
+  return e == cudaSuccess ? raise_smem<false, TY, MINB>() : e;
+}
+
+template <int TY, int MINB>
+cudaError_t launch_shape(int stage, const StepBuffers& b, const Params& P, double dt,
+                         int kchunk, cudaStream_t s) {
+  const bool mc = P.theta == 2.0;
+  if (stage == 1) return mc ? launch_mc<1, true, TY, MINB>(b, P, dt, kchunk, s)
+                            : launch_mc<1, false, TY, MINB>(b, P, dt, kchunk, s);
+  return mc ? launch_mc<2, true, TY, MINB>(b, P, dt, kchunk, s)
+            : launch_mc<2, false, TY, MINB>(b, P, dt, kchunk, s);
+}
+
 }  // namespace
 
+bool valid_fused_config(int tile_y, int ctas_per_sm) {
+  return (tile_y == 8 && (ctas_per_sm == 1 || ctas_per_sm == 2)) ||
+         ((tile_y == 12 || tile_y == 16) && ctas_per_sm == 1);
+}
+
 cudaError_t prepare_fused() {
-  cudaError_t e = raise_smem<true, 1>();
-  if (e == cudaSuccess) e = raise_smem<false, 1>();
-  if (e == cudaSuccess) e = raise_smem<true, 2>();
-  if (e == cudaSuccess) e = raise_smem<false, 2>();
+  cudaError_t e = raise_both<8, 1>();
+  if (e == cudaSuccess) e = raise_both<8, 2>();
+  if (e == cudaSuccess) e = raise_both<12, 1>();
+  if (e == cudaSuccess) e = raise_both<16, 1>();
   return e;
 }
 
-template <int MINB>
-cudaError_t launch_minb(int stage, const StepBuffers& b, const Params& P, double dt,
-                        int kchunk, cudaStream_t s) {
-  const bool mc = P.theta == 2.0;
-  if (stage == 1) return mc ? launch_mc<1, true, MINB>(b, P, dt, kchunk, s)
-                            : launch_mc<1, false, MINB>(b, P, dt, kchunk, s);
-  return mc ? launch_mc<2, true, MINB>(b, P, dt, kchunk, s)
-            : launch_mc<2, false, MINB>(b, P, dt, kchunk, s);
-}
-
 cudaError_t launch_fused(int stage, const StepBuffers& b, const Params& P, double dt,
-                         int kchunk, int ctas_per_sm, cudaStream_t s) {
+                         int kchunk, int tile_y, int ctas_per_sm, cudaStream_t s) {
   if (kchunk < 1) kchunk = 1;
-  return ctas_per_sm >= 2 ? launch_minb<2>(stage, b, P, dt, kchunk, s)
-                          : launch_minb<1>(stage, b, P, dt, kchunk, s);
+  if (!valid_fused_config(tile_y, ctas_per_sm)) return cudaErrorInvalidValue;
+  if (tile_y == 12) return launch_shape<12, 1>(stage, b, P, dt, kchunk, s);
+  if (tile_y == 16) return launch_shape<16, 1>(stage, b, P, dt, kchunk, s);
+  return ctas_per_sm >= 2 ? launch_shape<8, 2>(stage, b, P, dt, kchunk, s)
+                          : launch_shape<8, 1>(stage, b, P, dt, kchunk, s);
 }
 
 cudaError_t launch_dt(const double* U, const StepBuffers& b, const Params& P, cudaStream_t s) {

@@ -77,9 +77,11 @@ FV_DECLARE_STEP_VARIANT(fv_fp64_fma)
 // same contracts as the fused FP64 variants above.
 namespace fv_fp64_ff {
 cudaError_t prepare_fused();
-// ctas_per_sm: 2 (16 warps per SM, 128 registers) or 1 (8 warps, 255)
+// tiles of 32 x tile_y columns at ctas_per_sm CTAs per SM: 8 at 2 (16 warps
+// per SM, 128 registers) or 1 (8 warps, 255); 12 or 16 at 1
+bool valid_fused_config(int tile_y, int ctas_per_sm);
 cudaError_t launch_fused(int stage, const StepBuffers& b, const fvd::Params& P, double dt,
-                         int kchunk, int ctas_per_sm, cudaStream_t s);
+                         int kchunk, int tile_y, int ctas_per_sm, cudaStream_t s);
 cudaError_t launch_dt(const double* U, const StepBuffers& b, const fvd::Params& P,
                       cudaStream_t s);
 }
@@ -122,18 +124,16 @@ namespace fv_fp32 {
 // Raises the shared-memory limit of the fused substep kernels on the current
 // device (they take more than the default 48 KB); before their first launch.
 cudaError_t prepare_kernels();
-// The fused substep is built for tiles of 32 x tile_y columns, tile_y in
-// {4, 8, 16}, at occupancy 2 (16 warps per SM, 128 registers), and for
-// 32 x 8 tiles also at occupancy 3 (80 registers).
-bool valid_config(int tile_y, int occupancy);
-// The batched kernel is built for these (tile x, tile y, occupancy).
-constexpr int kBatchShapes[8][3] = {{32, 4, 2}, {32, 8, 2}, {32, 8, 3}, {32, 16, 2},
-                                    {16, 8, 2}, {64, 4, 2}, {64, 8, 2}, {128, 4, 2}};
-bool valid_batch_config(int tile_x, int tile_y, int occupancy);
+// The fused substep (single-mesh and batched) is built for these (tile x,
+// tile y, occupancy): occupancy 2 is 16 warps per SM at up to 128 registers,
+// 3 (32 x 8 only) 24 warps at 80 registers.
+constexpr int kShapes[8][3] = {{32, 4, 2}, {32, 8, 2}, {32, 8, 3}, {32, 16, 2},
+                               {16, 8, 2}, {64, 4, 2}, {64, 8, 2}, {128, 4, 2}};
+bool valid_config(int tile_x, int tile_y, int occupancy);
 // Size class of a mesh of nx cells along x: 0 up to 24, 1 up to 64, 2 above.
 inline int batch_class(int nx) { return nx <= 24 ? 0 : nx <= 64 ? 1 : 2; }
 cudaError_t launch_stage(int stage, const StepBuffers& b, const fvd::Params& P, double dt,
-                         int kchunk, double vacuum_ratio, int occupancy, int tile_y,
+                         int kchunk, double vacuum_ratio, int occupancy, int tile_x, int tile_y,
                          cudaStream_t s);
 cudaError_t launch_reduce_dt(const double* U, const fvd::Params& P, double vacuum_ratio,
                              DevCounters* ctr, cudaStream_t s);

@@ -641,7 +641,7 @@ __host__ __device__ constexpr int minb_of(int tile_x, int tile_y, int occupancy)
 
 // Calls fn.template run<STAGE, TX, TY, MINB, MC>() for a configuration, or
 // returns cudaErrorInvalidValue for one that is not built.  The single-mesh
-// kernel is built for the 32-wide tiles, the batched one for all.
+// and batched kernels are built for the same shapes.
 #define FV32_CASE(TXV, TYV, MB)                                                              \
   if (tile_x == TXV && tile_y == TYV && minb_of(tile_x, tile_y, occupancy) == MB) {          \
     if (mc)                                                                                  \
@@ -651,17 +651,7 @@ __host__ __device__ constexpr int minb_of(int tile_x, int tile_y, int occupancy)
                       : fn.template run<2, TXV, TYV, MB, false>();                           \
   }
 template <class Fn>
-static cudaError_t dispatch_mesh(int stage, int tile_x, int tile_y, int occupancy, bool mc,
-                                 Fn& fn) {
-  FV32_CASE(32, 4, 4)
-  FV32_CASE(32, 8, 2)
-  FV32_CASE(32, 8, 3)
-  FV32_CASE(32, 16, 1)
-  return cudaErrorInvalidValue;
-}
-template <class Fn>
-static cudaError_t dispatch_batch(int stage, int tile_x, int tile_y, int occupancy, bool mc,
-                                  Fn& fn) {
+static cudaError_t dispatch(int stage, int tile_x, int tile_y, int occupancy, bool mc, Fn& fn) {
   FV32_CASE(32, 4, 4)
   FV32_CASE(32, 8, 2)
   FV32_CASE(32, 8, 3)
@@ -727,35 +717,29 @@ struct RaiseSmemBatch {
   }
 };
 
-bool valid_config(int tile_y, int occupancy) {
-  return (tile_y == 4 || tile_y == 8 || tile_y == 16) && minb_of(32, tile_y, occupancy) > 0;
-}
-
-bool valid_batch_config(int tile_x, int tile_y, int occupancy) {
-  for (const auto& c : kBatchShapes)
+bool valid_config(int tile_x, int tile_y, int occupancy) {
+  for (const auto& c : kShapes)
     if (c[0] == tile_x && c[1] == tile_y && c[2] == occupancy) return true;
   return false;
 }
 
 cudaError_t launch_stage(int stage, const StepBuffers& b, const fvd::Params& P, double dt,
-                         int kchunk, double vacuum_ratio, int occupancy, int tile_y,
+                         int kchunk, double vacuum_ratio, int occupancy, int tile_x, int tile_y,
                          cudaStream_t s) {
   LaunchMesh fn{b, P, make_params32(P, vacuum_ratio), (float)dt, kchunk < 1 ? 1 : kchunk, s};
-  return dispatch_mesh(stage, 32, tile_y, occupancy, fn.Q.theta == 2.0f, fn);
+  return dispatch(stage, tile_x, tile_y, occupancy, fn.Q.theta == 2.0f, fn);
 }
 
 cudaError_t prepare_kernels() {
   RaiseSmemMesh fm;
   RaiseSmemBatch fb;
-  const int cfg[4][2] = {{4, 2}, {8, 2}, {8, 3}, {16, 2}};
   cudaError_t e = cudaSuccess;
   for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage)
-    for (int mc = 0; mc < 2 && e == cudaSuccess; ++mc) {
-      for (int c = 0; c < 4 && e == cudaSuccess; ++c)
-        e = dispatch_mesh(stage, 32, cfg[c][0], cfg[c][1], mc != 0, fm);
-      for (const auto& c : kBatchShapes)
-        if (e == cudaSuccess) e = dispatch_batch(stage, c[0], c[1], c[2], mc != 0, fb);
-    }
+    for (int mc = 0; mc < 2 && e == cudaSuccess; ++mc)
+      for (const auto& c : kShapes) {
+        if (e == cudaSuccess) e = dispatch(stage, c[0], c[1], c[2], mc != 0, fm);
+        if (e == cudaSuccess) e = dispatch(stage, c[0], c[1], c[2], mc != 0, fb);
+      }
   return e;
 }
 
@@ -793,7 +777,7 @@ cudaError_t launch_batch_stage(int stage, const BatchDevice& b, int cls, int kch
                                cudaStream_t s) {
   if (b.class_count[cls] == 0) return cudaSuccess;
   LaunchBatch fn{b, cls, kchunk, num_sms, b.next_item + 2 * cls + (stage == 1 ? 0 : 1), s};
-  return dispatch_batch(stage, tile_x, tile_y, occupancy, b.all_mc, fn);
+  return dispatch(stage, tile_x, tile_y, occupancy, b.all_mc, fn);
 }
 
 cudaError_t launch_batch_ghosts(int stage, const BatchDevice& b, cudaStream_t s) {

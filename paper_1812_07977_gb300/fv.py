@@ -54,6 +54,11 @@ class MeshDesc(ctypes.Structure):
 _lib = None
 
 
+# fv_tuning_key (include/fv.h) by short name
+TUNING_KEYS = {"kchunk": 0, "vacuum_ratio": 1, "occupancy": 2, "sweep_segments": 3,
+               "tile_y": 4, "fp64_fused": 5, "tile_x": 6}
+
+
 def load_library(path: str | None = None):
     """Load libfvgb.so (raises if it has not been built)."""
     global _lib
@@ -270,9 +275,8 @@ class Mesh:
         return a.value, b.value
 
     def set_tuning(self, key: str, value):
-        keys = {"kchunk": 0, "vacuum_ratio": 1, "occupancy": 2, "sweep_segments": 3,
-                "tile_y": 4, "fp64_fused": 5}
-        _check(self._lib.fv_set_tuning(self._h, keys[key], float(value)), "fv_set_tuning")
+        _check(self._lib.fv_set_tuning(self._h, TUNING_KEYS[key], float(value)),
+               "fv_set_tuning")
 
     def profile(self, on: bool = True):
         _check(self._lib.fv_profile_enable(self._h, int(bool(on))), "fv_profile_enable")

@@ -117,3 +117,12 @@ def test_status_and_bc_enum_values():
     b = _enum_values("fv_bc")
     assert b == {"FV_BC_OUTFLOW": 0, "FV_BC_PERIODIC": 1}
     assert fv.BC == {"outflow": 0, "periodic": 1}
+
+
+def test_tuning_keys_match_the_header():
+    """The binding's tuning-key names map onto fv_tuning_key's numbers, one
+    name per key."""
+    v = _enum_values("fv_tuning_key")
+    assert len(set(v.values())) == len(v) == len(fv.TUNING_KEYS)
+    for name, num in fv.TUNING_KEYS.items():
+        assert v["FV_TUNE_" + name.upper()] == num

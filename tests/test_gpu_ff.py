@@ -181,14 +181,17 @@ def test_ff_operand_range_is_guarded():
 
 
 def test_ff_launch_settings_same_bits():
-    """The float-float kernel built for one or two CTAs per SM, with z chunks
-    of several sizes, computes the same operations: the same bits."""
-    n = (45, 19, 30)
+    """The float-float kernel built for one or two CTAs per SM, with tiles of
+    8, 12 or 16 rows and z chunks of several sizes, computes the same
+    operations: the same bits (45 x 29 x 30: ragged tiles of every height)."""
+    n = (45, 29, 30)
     U0 = problems.riemann_oblique(*n)
     out = []
-    for occ, kc in ((2, 64), (1, 64), (2, 7), (1, 1)):
+    for occ, ty, kc in ((2, 8, 64), (1, 8, 64), (2, 8, 7), (1, 8, 1), (1, 12, 64),
+                        (1, 16, 5)):
         m = _mesh(n)
         m.set_tuning("occupancy", occ)
+        m.set_tuning("tile_y", ty)
         m.set_tuning("kchunk", kc)
         m.set_state(U0)
         for _ in range(3):
@@ -198,3 +201,19 @@ def test_ff_launch_settings_same_bits():
     for st, ct in out[1:]:
         assert np.array_equal(st.view(np.uint64), out[0][0].view(np.uint64))
         assert ct == out[0][1]
+
+
+def test_ff_tile_height_needs_occupancy_one():
+    """Tiles of 12 or 16 rows exist only at one CTA per SM: the other orders
+    of setting them are rejected and leave the mesh as it was."""
+    from paper_1812_07977_gb300.fv import FvError
+    m = _mesh((16, 16, 16))
+    with pytest.raises(FvError):
+        m.set_tuning("tile_y", 12)      # occupancy is 2
+    m.set_tuning("occupancy", 1)
+    m.set_tuning("tile_y", 16)
+    with pytest.raises(FvError):
+        m.set_tuning("occupancy", 2)    # tile height is 16
+    with pytest.raises(FvError):
+        m.set_tuning("tile_y", 4)
+    m.close()

@@ -173,16 +173,20 @@ def test_stage2_cfl_maximum_same_dt(theta):
     m.close()
 
 
-@pytest.mark.parametrize("tile_y", [4, 16])
-def test_tile_shapes_same_bits(tile_y):
-    """The fused kernel built for 32 x 4 and 32 x 16 tiles (128 / 512
-    threads; the 32 x 4 tile has more halo cells than threads) gives the
-    32 x 8 tile's bits, dt and counts, on a ragged mesh with z chunks."""
+@pytest.mark.parametrize("shape", [(32, 8), (32, 4), (32, 16), (64, 4), (64, 8), (128, 4)])
+def test_tile_shapes_same_bits(shape):
+    """The fused kernel built for tiles of 32 to 128 columns by 4 to 16 rows
+    (128 to 512 threads; the short tiles have more halo cells than threads)
+    gives the default 16 x 8 tile's bits, dt and counts, on a ragged mesh
+    with z chunks."""
     n = (45, 38, 33)
     out = []
-    for ty in (8, tile_y):
+    for tx, ty in ((16, 8), shape):
         m = _mesh32(n)
+        # through built shapes only: width 32 first, then the height
+        m.set_tuning("tile_x", 32)
         m.set_tuning("tile_y", ty)
+        m.set_tuning("tile_x", tx)
         m.set_tuning("kchunk", 7)
         m.set_state(problems.riemann_oblique(*n))
         dts = []
@@ -352,3 +356,22 @@ def test_fp32_bulk_dt_is_the_oracles_bitwise():
             assert dt == dto
             m.step(dt)
         m.close()
+
+
+def test_tile_shape_changes_must_stay_built():
+    """Width, height and occupancy changes that would leave the built shapes
+    are rejected, and the mesh keeps its shape."""
+    from paper_1812_07977_gb300.fv import FvError
+    m = _mesh32((16, 16, 16))
+    with pytest.raises(FvError):
+        m.set_tuning("tile_x", 128)     # (128, 8) is not built
+    with pytest.raises(FvError):
+        m.set_tuning("tile_y", 4)       # (16, 4) is not built
+    m.set_tuning("tile_x", 32)
+    m.set_tuning("tile_y", 4)
+    m.set_tuning("tile_x", 128)
+    with pytest.raises(FvError):
+        m.set_tuning("occupancy", 3)
+    with pytest.raises(FvError):
+        m.set_tuning("tile_x", 48)
+    m.close()
