@@ -75,10 +75,18 @@ BYTES_PER_ZONE_UPDATE = 200
 #   per cell and launch: the float-float divergence 380.
 FF_OPS_FACE = 888 + 205
 FF_OPS_CELL = 380
-# DRAM bytes (read + write) per launch of the fused kernels at 256^3 (mean of
-# stage 1 and 2) from ncu captures of the current kernels; None where no
-# capture of the current kernel exists.
-FUSED_TRAFFIC = {"fp64_fma": None, "fp64": None, "fp32_bulk": None}
+# DRAM bytes (read + write) per launch of the fused kernels on the 256^3
+# oblique problem (mean of stage 1 and 2, second step) from ncu captures
+# (`--metrics dram__bytes_read.sum,dram__bytes_write.sum` of
+# `python -m paper_1812_07977_gb300.run_case PRECISION 256 oblique 3`) of the
+# kernels as they are now; None where the kernel has changed since.
+FUSED_TRAFFIC = {
+    "fp32_bulk": (1.714e9, "ncu capture 2026-12-04 of k_stage32<., 16, 8, 4, 1>: "
+                           "1.393 GB (stage 1) and 2.036 GB (stage 2)"),
+    "fp64_ff": None,
+    "fp64_fma": None,
+    "fp64": None,
+}
 
 
 def fp64_probe():
@@ -565,6 +573,10 @@ def run_ours(args):
             else:
                 out["fused_kernel"] = _fused_roofline(vprof, vfaces, zones, 100, fp64_peak, hbm,
                                                       not prec.startswith("fp32"))
+            cap = FUSED_TRAFFIC.get(prec)
+            if cap and U0v is U0 and n == N:
+                out["fused_kernel"]["hbm"]["traffic"] = cap[0]
+                out["fused_kernel"]["hbm"]["traffic_note"] = cap[1]
         return out
 
     # the other arithmetic variants on the same workload, fewer steps each,
@@ -611,13 +623,14 @@ def run_ours(args):
         ops = (f"FP64 flops executed: {FLOPS_FACE} per evaluated face + {FLOPS_FUSED_CELL} "
                f"per cell and launch")
     alu = fused["alu"]
-    traffic = args.traffic if args.traffic else (FUSED_TRAFFIC.get(args.precision)
-                                                 if n == N else None)
+    cap = FUSED_TRAFFIC.get(args.precision) if n == N else None
+    traffic = args.traffic if args.traffic else (cap[0] if cap else None)
     roofline = {"bound": "alu", "kernel": kernel,
                 "achieved": alu["achieved"], "peak": peak, "unit": "TFLOP/s",
                 "frac": alu["frac"], "traffic": traffic,
-                "traffic_note": "DRAM bytes per launch from an ncu capture of this kernel "
-                                "(null: no capture of the current kernel)",
+                "traffic_note": (cap[1] if cap and not args.traffic else
+                                 "DRAM bytes per launch from an ncu capture of this kernel "
+                                 "(null: no capture of the current kernel)"),
                 "peak_source": src, "derived_peak": dpeak,
                 "avg_launch_ms": fused["avg_launch_ms"],
                 "flops": ops,

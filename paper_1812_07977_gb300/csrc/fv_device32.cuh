@@ -262,12 +262,22 @@ __device__ __forceinline__ void set_threshold(double s, double& smax, float& sma
   smax_f = in ? t : (s > 1.0 ? 0x1p100f : 0.0f);
 }
 
-__device__ __forceinline__ void refresh_max(const unsigned long long* gmax, double& smax,
-                                            float& smax_f) {
-  const unsigned long long g = *(const volatile unsigned long long*)gmax;
+// The shared maximum's bits, read past the caches: whenever it is read, a
+// lower bound of the final maximum, so a value read early stays usable.
+__device__ __forceinline__ unsigned long long peek_max(const unsigned long long* gmax) {
+  return *(const volatile unsigned long long*)gmax;
+}
+
+__device__ __forceinline__ void raise_max(unsigned long long g, double& smax, float& smax_f) {
   if (g > (unsigned long long)__double_as_longlong(smax))
     set_threshold(__longlong_as_double((long long)g), smax, smax_f);
 }
+
+__device__ __forceinline__ void refresh_max(const unsigned long long* gmax, double& smax,
+                                            float& smax_f) {
+  raise_max(peek_max(gmax), smax, smax_f);
+}
+
 
 // Folds one cell's FP64 CFL speed (fvd::cell_speed, IEEE operations) into the
 // shared maximum *gmax, and counts the cell in `bad` if its FP64 primitives

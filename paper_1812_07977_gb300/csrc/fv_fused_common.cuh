@@ -47,6 +47,11 @@ __device__ __forceinline__ void halo_cell(int h, int& row, int& col) {
   }
 }
 
+// Hint: bring the line holding p into L2 (no register, no wait).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ void cp_async8(double* dst, const double* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
                    (unsigned)__cvta_generic_to_shared(dst)),

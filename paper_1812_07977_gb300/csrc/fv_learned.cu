@@ -107,10 +107,15 @@ __device__ __forceinline__ uint4 gather8(const float* __restrict__ in, long long
 // every A_o is the same no-swizzle K-major layout at a shifted start: 8 consecutive x cells
 // form a core matrix, the next row of the tile is one halo row (160 B) further, the next 8
 // channels one slab further.  The weights are [offset][slab][co][8 ch] in shared memory.
+//
+// Persistent CTAs (one per SM) walk the tiles with a two-deep pipeline: two input tiles in
+// shared memory and two accumulators in TMEM, so that while the tensor cores run tile i+1's
+// MMAs (issued by one thread, completion signalled on an mbarrier), the 12 warps write tile
+// i's outputs from TMEM and then gather tile i+2's input.  The weights are copied into shared
+// memory once per CTA.
 constexpr int UX = 8, UY = 16, UZ = 4;                 // output tile: UZ planes of 128 cells
 constexpr int UHX = UX + 2, UHY = UY + 2, UHZ = UZ + 2, UHN = UHX * UHY * UHZ;
-constexpr int UThreads = 384;                          // 12 warps gather the operands; warps
-                                                       // 0..3 read TMEM lanes 0..127 back
+constexpr int UThreads = 384;                          // 12 warps: gather and epilogue
 constexpr int kMmaPolls = 1 << 20;                     // bounded wait for the MMAs
 
 template <int CI, int CO>
@@ -120,9 +125,12 @@ struct UConv {
   static constexpr int KC = CIP / 8;                   // 8-channel slabs
   static constexpr size_t in_bytes = (size_t)KC * UHN * 16;
   static constexpr size_t w_bytes = (size_t)27 * KC * NP * 16;
-  static constexpr size_t smem = in_bytes + w_bytes;
-  static constexpr uint32_t tmem_cols = UZ * NP <= 32 ? 32 : UZ * NP <= 64 ? 64 : 128;
-  static_assert(NP <= 32 && UZ * NP <= 128, "accumulator layout");
+  static constexpr size_t smem = 2 * in_bytes + w_bytes;   // two input tiles, the weights
+  static constexpr uint32_t acc_cols = UZ * NP;             // one tile's accumulators
+  static constexpr uint32_t tmem_cols = 2 * acc_cols <= 32 ? 32 : 2 * acc_cols <= 64 ? 64 :
+                                        2 * acc_cols <= 128 ? 128 : 256;
+  static_assert(NP <= 32 && 2 * acc_cols <= 256, "accumulator layout");
+  static_assert(smem <= 227 * 1024, "shared memory");
 };
 
 // The weights in the convolution's shared-memory layout: entry (o, kc, n) =
@@ -143,98 +151,160 @@ __global__ void k_umma_weights(const bf16* __restrict__ w, uint4* __restrict__ w
   wl[t] = *reinterpret_cast<const uint4*>(v);
 }
 
-template <int CI, int CO, class TI, class TO, bool TANH, bool ICL, bool OCL>
-__global__ void __launch_bounds__(UThreads)
-k_conv_umma(const TI* __restrict__ in, const uint4* __restrict__ wl,
-            const float* __restrict__ bias, TO* __restrict__ out, Grid3 g,
-            unsigned* __restrict__ status) {
-  using C = UConv<CI, CO>;
-  extern __shared__ __align__(1024) unsigned char smem[];
-  uint4* xs = reinterpret_cast<uint4*>(smem);
-  uint4* ws = reinterpret_cast<uint4*>(smem + C::in_bytes);
-  __shared__ __align__(8) uint64_t mbar;
-  __shared__ uint32_t tmem_slot;
-  const int tid = threadIdx.x, warp = tid >> 5;
+__device__ __forceinline__ void tile_origin(int t, const Grid3& g, int& x0, int& y0, int& z0) {
   const int ntx = tiles(g.nx, UX), nty = tiles(g.ny, UY);
-  const int x0 = (blockIdx.x % ntx) * UX, y0 = ((blockIdx.x / ntx) % nty) * UY,
-            z0 = (blockIdx.x / (ntx * nty)) * UZ;
+  x0 = (t % ntx) * UX;
+  y0 = ((t / ntx) % nty) * UY;
+  z0 = (t / (ntx * nty)) * UZ;
+}
+
+// The input tile at (x0, y0, z0) with its periodic one-cell halo, as BF16 slabs.
+template <int CI, int KC, class TI, bool ICL>
+__device__ __forceinline__ void gather_tile(uint4* xs, const TI* __restrict__ in, const Grid3& g,
+                                            int x0, int y0, int z0) {
 #pragma unroll 4
-  for (int t = tid; t < 27 * C::KC * C::NP; t += UThreads) ws[t] = wl[t];
-  // input halo tile (periodic), as BF16 slabs
-#pragma unroll 4
-  for (int t = tid; t < C::KC * UHN; t += UThreads) {
+  for (int t = threadIdx.x; t < KC * UHN; t += UThreads) {
     const int c = t % UHN, kc = t / UHN;
     const int lz = c / (UHX * UHY), ly = (c / UHX) % UHY, lx = c % UHX;
     const long long cell = ((long long)wrap(z0 + lz - 1, g.nz) * g.ny + wrap(y0 + ly - 1, g.ny)) *
                                g.nx + wrap(x0 + lx - 1, g.nx);
     xs[t] = gather8<CI, ICL>(in, g.n, cell, kc);
   }
-  if (tid == 0) umma::mbar_init(&mbar, 1);
+}
+
+// One tile's MMAs (one thread): plane z accumulates into columns acc + z * NP.
+template <int CI, int CO>
+__device__ __forceinline__ void tile_mmas(uint32_t xa, uint32_t wa, uint32_t acc) {
+  using C = UConv<CI, CO>;
+  constexpr uint32_t idesc = umma::idesc_bf16(128, C::NP);
+  for (int z = 0; z < UZ; ++z) {
+    uint32_t accumulate = 0;
+    for (int o = 0; o < 27; ++o) {
+      const int dz = o / 9, dy = (o / 3) % 3, dx = o % 3;
+      const uint32_t cell0 = ((z + dz) * UHY + dy) * UHX + dx;
+#pragma unroll
+      for (int kk = 0; kk < C::CIP / 16; ++kk) {
+        const uint64_t a = umma::desc(xa + ((2 * kk) * UHN + cell0) * 16, UHN * 16, UHX * 16);
+        const uint64_t b = umma::desc(wa + ((o * C::KC + 2 * kk) * C::NP) * 16, C::NP * 16, 128);
+        umma::mma_bf16(acc + z * C::NP, a, b, idesc, accumulate);
+        accumulate = 1;
+      }
+    }
+  }
+}
+
+template <int CI, int CO, class TI, class TO, bool TANH, bool ICL, bool OCL>
+__global__ void __launch_bounds__(UThreads, 1)
+k_conv_umma(const TI* __restrict__ in, const uint4* __restrict__ wl,
+            const float* __restrict__ bias, TO* __restrict__ out, Grid3 g,
+            unsigned* __restrict__ status) {
+  using C = UConv<CI, CO>;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint4* xs[2] = {reinterpret_cast<uint4*>(smem), reinterpret_cast<uint4*>(smem + C::in_bytes)};
+  uint4* ws = reinterpret_cast<uint4*>(smem + 2 * C::in_bytes);
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = tiles(g.nx, UX) * tiles(g.ny, UY) * tiles(g.nz, UZ);
+  int t = blockIdx.x;
+  if (t >= ntiles) return;   // (the grid has at most one CTA per tile)
+#pragma unroll 4
+  for (int i = tid; i < 27 * C::KC * C::NP; i += UThreads) ws[i] = wl[i];
+  int x0, y0, z0;
+  tile_origin(t, g, x0, y0, z0);
+  gather_tile<CI, C::KC, TI, ICL>(xs[0], in, g, x0, y0, z0);
+  if (tid == 0) {
+    umma::mbar_init(&mbar[0], 1);
+    umma::mbar_init(&mbar[1], 1);
+  }
   if (warp == 0) umma::tmem_alloc(&tmem_slot, C::tmem_cols);
   umma::fence_smem_for_mma();
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = tmem_slot;
+  const uint32_t wa = umma::smem_addr(ws);
+  const uint32_t xa[2] = {umma::smem_addr(xs[0]), umma::smem_addr(xs[1])};
   if (tid == 0) {
-    constexpr uint32_t idesc = umma::idesc_bf16(128, C::NP);
-    const uint32_t xa = umma::smem_addr(xs), wa = umma::smem_addr(ws);
-    for (int z = 0; z < UZ; ++z) {
-      uint32_t acc = 0;
-      for (int o = 0; o < 27; ++o) {
-        const int dz = o / 9, dy = (o / 3) % 3, dx = o % 3;
-        const uint32_t cell0 = ((z + dz) * UHY + dy) * UHX + dx;
-#pragma unroll
-        for (int kk = 0; kk < C::CIP / 16; ++kk) {
-          const uint64_t a = umma::desc(xa + ((2 * kk) * UHN + cell0) * 16, UHN * 16, UHX * 16);
-          const uint64_t b = umma::desc(wa + ((o * C::KC + 2 * kk) * C::NP) * 16, C::NP * 16, 128);
-          umma::mma_bf16(tmem + z * C::NP, a, b, idesc, acc);
-          acc = 1;
-        }
-      }
-    }
-    umma::commit(&mbar);
+    tile_mmas<CI, CO>(xa[0], wa, tmem);
+    umma::commit(&mbar[0]);
   }
-  const bool ok = __all_sync(0xffffffffu, umma::mbar_wait(&mbar, 0, kMmaPolls));
-  umma::fence_after_sync();
-  if (!ok) {
-    if ((tid & 31) == 0) atomicOr(status, 1u);
-  } else if (warp < 4) {
-    // row m of plane z's accumulator is cell (m % 8, m / 8) of that plane
-    const int gx = x0 + tid % UX, gy = y0 + tid / UX;
+  // the epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (accumulator row m = cell
+  // (m % 8, m / 8) of a plane); the three warps of a lane quarter split its 16-column chunks
+  const int quarter = warp & 3, group = warp >> 2;
+  const int m = quarter * 32 + lane;
+  constexpr int HALVES = C::NP / 16;
+  for (int i = 0;; ++i) {
+    const int b = i & 1;
+    const int tn = t + (int)gridDim.x;
+    int nx0 = 0, ny0 = 0, nz0 = 0;
+    if (tn < ntiles) {
+      // the next tile's input, into the buffer its MMAs will read (free: the MMAs
+      // that last read it were waited for in the previous iteration)
+      tile_origin(tn, g, nx0, ny0, nz0);
+      gather_tile<CI, C::KC, TI, ICL>(xs[b ^ 1], in, g, nx0, ny0, nz0);
+    }
+    const bool ok = umma::mbar_wait(&mbar[b], (uint32_t)((i >> 1) & 1), kMmaPolls);
+    umma::fence_smem_for_mma();
+    umma::fence_before_sync();
+    const int all_ok = __syncthreads_and(ok);
+    umma::fence_after_sync();
+    if (!all_ok) {
+      if (tid == 0) atomicOr(status, 1u);
+      // let this tile's MMAs drain (bounded) before the accumulators are freed
+      umma::mbar_wait(&mbar[b], (uint32_t)((i >> 1) & 1), kMmaPolls);
+      break;
+    }
+    if (tid == 0 && tn < ntiles) {
+      tile_mmas<CI, CO>(xa[b ^ 1], wa, tmem + (uint32_t)(b ^ 1) * C::acc_cols);
+      umma::commit(&mbar[b ^ 1]);
+    }
+    const uint32_t acc = tmem + (uint32_t)b * C::acc_cols + ((uint32_t)(quarter * 32) << 16);
+    const int gx = x0 + m % UX, gy = y0 + m / UX;
 #pragma unroll 1
-    for (int z = 0; z < UZ; ++z) {
-      float v[32];
-      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + z * C::NP;
-      umma::ld16(ta, v);
-      if (C::NP > 16) umma::ld16(ta + 16, v + 16);
+    for (int c = group; c < UZ * HALVES; c += 3) {
+      const int z = c / HALVES, h = c % HALVES;
+      float v[16];
+      umma::ld16(acc + z * C::NP + h * 16, v);
       const int gz = z0 + z;
       if (gx < g.nx && gy < g.ny && gz < g.nz) {
         const long long cell = ((long long)gz * g.ny + gy) * g.nx + gx;
 #pragma unroll
-        for (int co = 0; co < CO; ++co) {
-          const float a = v[co] + (bias ? bias[co] : 0.0f);
-          v[co] = TANH ? tanhf(a) : a;
+        for (int j = 0; j < 16; ++j) {
+          const int co = h * 16 + j;
+          if (co < CO) {
+            const float a = v[j] + (bias ? bias[co] : 0.0f);
+            v[j] = TANH ? tanhf(a) : a;
+          }
         }
         if constexpr (OCL) {
-          // the row's channels as 16-byte stores ([cell][pitch], zero pads)
+          // the chunk's channels as 16-byte stores ([cell][pitch], zero pads)
           static_assert(sizeof(TO) == 2 || sizeof(TO) == 4, "output type");
           constexpr int P = pitch8<CO>(), PER = 16 / (int)sizeof(TO);
-          uint4* dst = reinterpret_cast<uint4*>(out + cell * P);
+          const int nch = min(16, P - h * 16);
+          uint4* dst = reinterpret_cast<uint4*>(out + cell * P + h * 16);
 #pragma unroll
-          for (int q = 0; q < P / PER; ++q) {
-            __align__(16) TO w[PER];
+          for (int q = 0; q < 16 / PER; ++q) {
+            if (q * PER < nch) {
+              __align__(16) TO w[PER];
 #pragma unroll
-            for (int e = 0; e < PER; ++e)
-              w[e] = from_f<TO>(q * PER + e < CO ? v[q * PER + e] : 0.0f);
-            dst[q] = *reinterpret_cast<const uint4*>(w);
+              for (int e = 0; e < PER; ++e)
+                w[e] = from_f<TO>(h * 16 + q * PER + e < CO ? v[q * PER + e] : 0.0f);
+              dst[q] = *reinterpret_cast<const uint4*>(w);
+            }
           }
         } else {
 #pragma unroll
-          for (int co = 0; co < CO; ++co) out[co * g.n + cell] = from_f<TO>(v[co]);
+          for (int j = 0; j < 16; ++j)
+            if (h * 16 + j < CO) out[(h * 16 + j) * g.n + cell] = from_f<TO>(v[j]);
         }
       }
     }
+    if (tn >= ntiles) break;
+    t = tn;
+    x0 = nx0;
+    y0 = ny0;
+    z0 = nz0;
   }
   umma::fence_before_sync();
   __syncthreads();
@@ -252,7 +322,10 @@ k_conv_umma(const TI* __restrict__ in, const uint4* __restrict__ wl,
 // by each offset, so every 8-row group of M is one 2 KB slab of 128 cells;
 // B is the tile's output gradient as BF16 slabs [co slab][cell][8 co].  The
 // accumulators of all offset groups stay in TMEM for the tile's four planes.
-// Bias gradients (sum of gout over the tile) are summed in FP32.
+// A is double-buffered: while the tensor cores run one (group, plane)'s MMAs,
+// the threads build the next one's A in the other buffer, waiting only for
+// the MMAs that last read that buffer.  Bias gradients (sum of gout over the
+// tile) are summed in FP32.
 template <int CI, int CO>
 struct UWgrad {
   static constexpr int CIP = (CI + 7) / 8 * 8;     // M rows per offset
@@ -265,7 +338,7 @@ struct UWgrad {
   static constexpr size_t x_bytes = (size_t)KC * UHN * 16;
   static constexpr size_t g_bytes = (size_t)(NP / 8) * TC * 16;
   static constexpr size_t a_bytes = (size_t)G * KC * PC * 16;   // 128 rows x 128 cells
-  static constexpr size_t smem = x_bytes + g_bytes + a_bytes;
+  static constexpr size_t smem = x_bytes + g_bytes + 2 * a_bytes;
   static constexpr uint32_t tmem_cols = NG * NP <= 32 ? 32 : NG * NP <= 64 ? 64 :
                                         NG * NP <= 128 ? 128 : 256;
   static_assert(G * CIP == 128 && NG * NP <= 256, "accumulator layout");
@@ -279,8 +352,9 @@ k_wgrad_umma(const TI* __restrict__ in, const float* __restrict__ gout,
   extern __shared__ __align__(1024) unsigned char smem[];
   uint4* xs = reinterpret_cast<uint4*>(smem);
   uint4* gs = reinterpret_cast<uint4*>(smem + C::x_bytes);
-  uint4* as = reinterpret_cast<uint4*>(smem + C::x_bytes + C::g_bytes);
-  __shared__ __align__(8) uint64_t mbar;
+  uint4* as2[2] = {reinterpret_cast<uint4*>(smem + C::x_bytes + C::g_bytes),
+                    reinterpret_cast<uint4*>(smem + C::x_bytes + C::g_bytes + C::a_bytes)};
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ float bsum[UThreads / 32][32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -320,17 +394,28 @@ k_wgrad_umma(const TI* __restrict__ in, const float* __restrict__ gout,
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) bsum[warp][co / (UThreads / 32)] = acc;
   }
-  if (tid == 0) umma::mbar_init(&mbar, 1);
+  if (tid == 0) {
+    umma::mbar_init(&mbar[0], 1);
+    umma::mbar_init(&mbar[1], 1);
+  }
   if (warp == 0) umma::tmem_alloc(&tmem_slot, C::tmem_cols);
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = tmem_slot;
   constexpr uint32_t idesc = umma::idesc_bf16(128, C::NP) | (1u << 15) | (1u << 16);  // MN-major
+  constexpr int NIT = C::NG * UZ;   // (group, plane) steps; step it uses A buffer it & 1
   bool ok = true;
-  int phase = 0;
-  for (int gi = 0; gi < C::NG; ++gi) {
-    for (int z = 0; z < UZ; ++z) {
+  int issued = 0;                   // steps whose MMAs were issued
+  for (int it = 0; it < NIT; ++it) {
+    const int gi = it / UZ, z = it % UZ, buf = it & 1;
+    uint4* as = as2[buf];
+    {
+      // the MMAs of step it - 2 read this buffer: wait for them (mbarrier
+      // use (it >> 1) - 1 of this buffer)
+      bool w = true;
+      if (it >= 2) w = umma::mbar_wait(&mbar[buf], (uint32_t)(((it >> 1) - 1) & 1), kMmaPolls);
+      umma::fence_after_sync();
       // A for (group gi, plane z): slab (j, kc) holds channels kc*8.. of the
       // plane's cells shifted by offset o = gi * G + j (zero past 26)
 #pragma unroll 4
@@ -347,8 +432,11 @@ k_wgrad_umma(const TI* __restrict__ in, const float* __restrict__ gout,
       }
       umma::fence_smem_for_mma();
       umma::fence_before_sync();
-      __syncthreads();
+      // the whole block agrees on the outcome (a wait that ran out ends the
+      // loop for all)
+      ok = __syncthreads_and(w) != 0;
       umma::fence_after_sync();
+      if (!ok) break;
       if (tid == 0) {
         const uint32_t aa = umma::smem_addr(as), ga = umma::smem_addr(gs);
 #pragma unroll
@@ -357,16 +445,20 @@ k_wgrad_umma(const TI* __restrict__ in, const float* __restrict__ gout,
           const uint64_t b = umma::desc(ga + (z * C::PC + ks * 16) * 16, 128, C::TC * 16);
           umma::mma_bf16(tmem + gi * C::NP, a, b, idesc, (z > 0 || ks > 0) ? 1u : 0u);
         }
-        umma::commit(&mbar);
+        umma::commit(&mbar[buf]);
       }
-      // the MMAs must finish reading A before it is rebuilt; the whole block
-      // agrees on the outcome (a wait that ran out ends the loop for all)
-      ok = __syncthreads_and(umma::mbar_wait(&mbar, (uint32_t)(phase & 1), kMmaPolls)) != 0;
-      ++phase;
-      umma::fence_after_sync();
-      if (!ok) break;
+      issued = it + 1;
     }
-    if (!ok) break;
+  }
+  // the last two issued steps' MMAs (bounded waits) before TMEM is read or
+  // freed
+  {
+    bool w = true;
+    for (int it = issued - 2; it < issued; ++it)
+      if (it >= 0) w = umma::mbar_wait(&mbar[it & 1], (uint32_t)((it >> 1) & 1), kMmaPolls) && w;
+    umma::fence_before_sync();
+    ok = __syncthreads_and(w && ok) != 0;
+    umma::fence_after_sync();
   }
   float* dst = partial + (size_t)blockIdx.x * (CI * 27 + 1) * CO;
   if (!ok) {
@@ -692,7 +784,8 @@ cudaError_t conv_fwd(const TI* in, const bf16* w, const float* bias, TO* out, co
   auto k = k_conv_umma<CI, CO, TI, TO, TANH, ICL, OCL>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int nb = tiles(g.nx, UX) * tiles(g.ny, UY) * tiles(g.nz, UZ);
+  const int nt = tiles(g.nx, UX) * tiles(g.ny, UY) * tiles(g.nz, UZ);
+  const int nb = nt < fv_sm_count() ? nt : fv_sm_count();   // persistent: one CTA per SM
   k<<<nb, UThreads, smem, s>>>(in, wl, bias, out, g, status);
   return cudaGetLastError();
 }
