@@ -83,7 +83,8 @@ FF_OPS_CELL = 380
 FUSED_TRAFFIC = {
     "fp32_bulk": (1.714e9, "ncu capture 2026-12-04 of k_stage32<., 16, 8, 4, 1>: "
                            "1.393 GB (stage 1) and 2.036 GB (stage 2)"),
-    "fp64_ff": None,
+    "fp64_ff": (1.950e9, "ncu capture 2026-12-04 of k_stageff<., MC, 8, 2>: "
+                         "1.590 GB (stage 1) and 2.310 GB (stage 2)"),
     "fp64_fma": None,
     "fp64": None,
 }

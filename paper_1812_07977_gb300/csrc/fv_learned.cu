@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <unordered_set>
 #include <vector>
 
@@ -45,6 +46,9 @@ template <> __device__ __forceinline__ float from_f<float>(float v) { return v; 
 template <> __device__ __forceinline__ bf16 from_f<bf16>(float v) { return __float2bfloat16_rn(v); }
 
 __device__ __forceinline__ int wrap(int v, int n) {
+  // the tile halos reach at most a few cells past either end: one add or
+  // subtract; the remainder (a division) only for meshes shorter than that
+  if (v >= -n && v < 2 * n) return v < 0 ? v + n : (v >= n ? v - n : v);
   v %= n;
   return v < 0 ? v + n : v;
 }
@@ -158,36 +162,64 @@ __device__ __forceinline__ void tile_origin(int t, const Grid3& g, int& x0, int&
   z0 = (t / (ntx * nty)) * UZ;
 }
 
+// Asynchronous 16-byte copy global -> shared (L2 only), and the wait for all
+// of this thread's copies.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(umma::smem_addr(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // The input tile at (x0, y0, z0) with its periodic one-cell halo, as BF16 slabs.
+// Channel-last BF16 inputs are copied asynchronously (16 bytes per cell and
+// slab, already in the slab layout): the caller waits with cp_async_wait_all
+// before the tile is used; other inputs are converted on the way, in place.
 template <int CI, int KC, class TI, bool ICL>
 __device__ __forceinline__ void gather_tile(uint4* xs, const TI* __restrict__ in, const Grid3& g,
                                             int x0, int y0, int z0) {
+  constexpr bool async = ICL && std::is_same<TI, bf16>::value;
 #pragma unroll 4
   for (int t = threadIdx.x; t < KC * UHN; t += UThreads) {
     const int c = t % UHN, kc = t / UHN;
     const int lz = c / (UHX * UHY), ly = (c / UHX) % UHY, lx = c % UHX;
     const long long cell = ((long long)wrap(z0 + lz - 1, g.nz) * g.ny + wrap(y0 + ly - 1, g.ny)) *
                                g.nx + wrap(x0 + lx - 1, g.nx);
-    xs[t] = gather8<CI, ICL>(in, g.n, cell, kc);
+    if constexpr (async) {
+      if (kc * 8 < CI)
+        cp_async16(&xs[t], in + cell * pitch8<CI>() + kc * 8);
+      else
+        xs[t] = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+      xs[t] = gather8<CI, ICL>(in, g.n, cell, kc);
+    }
   }
 }
 
 // One tile's MMAs (one thread): plane z accumulates into columns acc + z * NP.
+// The descriptors are formed once; a shifted operand is the base descriptor
+// plus its byte offset / 16 (the start-address field is the low 14 bits, and
+// every address here is below 256 KB), so the issuing thread spends one add
+// per operand on each MMA.
 template <int CI, int CO>
 __device__ __forceinline__ void tile_mmas(uint32_t xa, uint32_t wa, uint32_t acc) {
   using C = UConv<CI, CO>;
   constexpr uint32_t idesc = umma::idesc_bf16(128, C::NP);
+  const uint64_t a0 = umma::desc(xa, UHN * 16, UHX * 16);
+  const uint64_t b0 = umma::desc(wa, C::NP * 16, 128);
+#pragma unroll 1
   for (int z = 0; z < UZ; ++z) {
-    uint32_t accumulate = 0;
+    const uint64_t az = a0 + (uint64_t)(z * UHY * UHX);
+#pragma unroll
     for (int o = 0; o < 27; ++o) {
       const int dz = o / 9, dy = (o / 3) % 3, dx = o % 3;
-      const uint32_t cell0 = ((z + dz) * UHY + dy) * UHX + dx;
 #pragma unroll
       for (int kk = 0; kk < C::CIP / 16; ++kk) {
-        const uint64_t a = umma::desc(xa + ((2 * kk) * UHN + cell0) * 16, UHN * 16, UHX * 16);
-        const uint64_t b = umma::desc(wa + ((o * C::KC + 2 * kk) * C::NP) * 16, C::NP * 16, 128);
-        umma::mma_bf16(acc + z * C::NP, a, b, idesc, accumulate);
-        accumulate = 1;
+        const uint64_t a = az + (uint64_t)((2 * kk) * UHN + (dz * UHY + dy) * UHX + dx);
+        const uint64_t b = b0 + (uint64_t)((o * C::KC + 2 * kk) * C::NP);
+        umma::mma_bf16(acc + z * C::NP, a, b, idesc, (o > 0 || kk > 0) ? 1u : 0u);
       }
     }
   }
@@ -213,6 +245,7 @@ k_conv_umma(const TI* __restrict__ in, const uint4* __restrict__ wl,
   int x0, y0, z0;
   tile_origin(t, g, x0, y0, z0);
   gather_tile<CI, C::KC, TI, ICL>(xs[0], in, g, x0, y0, z0);
+  cp_async_wait_all();
   if (tid == 0) {
     umma::mbar_init(&mbar[0], 1);
     umma::mbar_init(&mbar[1], 1);
@@ -245,6 +278,7 @@ k_conv_umma(const TI* __restrict__ in, const uint4* __restrict__ wl,
       gather_tile<CI, C::KC, TI, ICL>(xs[b ^ 1], in, g, nx0, ny0, nz0);
     }
     const bool ok = umma::mbar_wait(&mbar[b], (uint32_t)((i >> 1) & 1), kMmaPolls);
+    cp_async_wait_all();   // this thread's copies of the next tile have landed
     umma::fence_smem_for_mma();
     umma::fence_before_sync();
     const int all_ok = __syncthreads_and(ok);
@@ -313,35 +347,39 @@ k_conv_umma(const TI* __restrict__ in, const uint4* __restrict__ wl,
 
 // ---------------------------------------------------------------- tcgen05 weight gradient
 // Per tile of the convolution's 8 x 16 x 4 output cells, the partial weight
-// gradients partial[tile][p][co], p = ci * 27 + o (layout of k_conv_wgrad),
+// gradients partial[tile][p][co], p = ci * 27 + o,
 //   sum over the tile's cells c of gout[co][c] * in[ci][c + o - 1],
-// as MMAs D[(o, ci)][co] += A[(o, ci)][c] B[c][co] with MN-major operands:
-// G offsets stacked along M (128 rows = G x CIP channels), K = the cells of
-// one plane (128), N = CO.  A is built per (offset group, plane) in shared
-// memory from the input tile (channel-last slabs, as in k_conv_umma) shifted
-// by each offset, so every 8-row group of M is one 2 KB slab of 128 cells;
-// B is the tile's output gradient as BF16 slabs [co slab][cell][8 co].  The
-// accumulators of all offset groups stay in TMEM for the tile's four planes.
-// A is double-buffered: while the tensor cores run one (group, plane)'s MMAs,
-// the threads build the next one's A in the other buffer, waiting only for
-// the MMAs that last read that buffer.  Bias gradients (sum of gout over the
-// tile) are summed in FP32.
+// as one GEMM per offset o on the tensor cores, D_o[co][ci] += A[co][c] B_o[c][ci],
+// K = the 128 cells of a plane, 16 per MMA, over the tile's four planes:
+//   A = the tile's output gradient, BF16 slabs [co slab][cell][8 co] (MN-major:
+//       8 output channels of a cell are one 16-byte row), M = 128 rows of which
+//       the first CO are the output channels (the rest read whatever follows
+//       in shared memory and land in TMEM lanes that are never read);
+//   B_o = the input tile in the convolution's layout [ci slab][halo cell][8 ci]
+//       (MN-major) at the start shifted by the offset: 8 x-consecutive cells
+//       are 16 bytes apart and the next 8 cells of the plane are one halo row
+//       (160 B) further, so every offset's operand is addressed in place, with
+//       no copy.
+// The 27 accumulators (N = CI padded to 16 or 32 columns each) take at most
+// two passes over TMEM's 512 columns; one thread issues every MMA of a pass,
+// commits them to an mbarrier, and warps 0, 4 and 8 (TMEM lanes 0..31, the
+// output channels) write the pass's partials.  Bias gradients (sum of gout
+// over the tile) are summed in FP32.
 template <int CI, int CO>
 struct UWgrad {
-  static constexpr int CIP = (CI + 7) / 8 * 8;     // M rows per offset
-  static constexpr int KC = CIP / 8;               // input slabs
-  static constexpr int G = 128 / CIP;              // offsets per MMA
-  static constexpr int NG = (27 + G - 1) / G;      // offset groups
-  static constexpr int NP = (CO + 15) / 16 * 16;   // N
+  static constexpr int NPC = CI <= 16 ? 16 : 32;   // N: input channels, padded
+  static constexpr int KC = NPC / 8;               // input slabs
   static constexpr int PC = UX * UY;               // cells of a plane (K of a plane)
   static constexpr int TC = PC * UZ;               // cells of the tile
+  static constexpr int GS = (CO + 7) / 8;          // output-gradient slabs
+  static constexpr size_t g_slab = (size_t)TC * 16;
+  static constexpr size_t x_off = (size_t)GS * g_slab;        // input tile after the slabs
   static constexpr size_t x_bytes = (size_t)KC * UHN * 16;
-  static constexpr size_t g_bytes = (size_t)(NP / 8) * TC * 16;
-  static constexpr size_t a_bytes = (size_t)G * KC * PC * 16;   // 128 rows x 128 cells
-  static constexpr size_t smem = x_bytes + g_bytes + 2 * a_bytes;
-  static constexpr uint32_t tmem_cols = NG * NP <= 32 ? 32 : NG * NP <= 64 ? 64 :
-                                        NG * NP <= 128 ? 128 : 256;
-  static_assert(G * CIP == 128 && NG * NP <= 256, "accumulator layout");
+  static constexpr size_t a_span = 16 * g_slab;                // what M = 128 rows address
+  static constexpr size_t smem = x_off + x_bytes > a_span ? x_off + x_bytes : a_span;
+  static constexpr int OPP = 512 / NPC;            // offsets per pass
+  static constexpr int NPASS = (27 + OPP - 1) / OPP;
+  static_assert(CO <= 32 && CI <= 32 && smem <= 227 * 1024, "layout");
 };
 
 template <int CI, int CO, class TI, bool ICL, bool GCL>
@@ -350,30 +388,20 @@ k_wgrad_umma(const TI* __restrict__ in, const float* __restrict__ gout,
              float* __restrict__ partial, Grid3 g, unsigned* __restrict__ status) {
   using C = UWgrad<CI, CO>;
   extern __shared__ __align__(1024) unsigned char smem[];
-  uint4* xs = reinterpret_cast<uint4*>(smem);
-  uint4* gs = reinterpret_cast<uint4*>(smem + C::x_bytes);
-  uint4* as2[2] = {reinterpret_cast<uint4*>(smem + C::x_bytes + C::g_bytes),
-                    reinterpret_cast<uint4*>(smem + C::x_bytes + C::g_bytes + C::a_bytes)};
-  __shared__ __align__(8) uint64_t mbar[2];
+  uint4* gs = reinterpret_cast<uint4*>(smem);
+  uint4* xs = reinterpret_cast<uint4*>(smem + C::x_off);
+  __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   __shared__ float bsum[UThreads / 32][32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ntx = tiles(g.nx, UX), nty = tiles(g.ny, UY);
-  const int x0 = (blockIdx.x % ntx) * UX, y0 = ((blockIdx.x / ntx) % nty) * UY,
-            z0 = (blockIdx.x / (ntx * nty)) * UZ;
+  int x0, y0, z0;
+  tile_origin(blockIdx.x, g, x0, y0, z0);
   // input halo tile (periodic) as BF16 slabs [kc][halo cell][8 ch]
-#pragma unroll 4
-  for (int t = tid; t < C::KC * UHN; t += UThreads) {
-    const int c = t % UHN, kc = t / UHN;
-    const int lz = c / (UHX * UHY), ly = (c / UHX) % UHY, lx = c % UHX;
-    const long long cell = ((long long)wrap(z0 + lz - 1, g.nz) * g.ny + wrap(y0 + ly - 1, g.ny)) *
-                               g.nx + wrap(x0 + lx - 1, g.nx);
-    xs[t] = gather8<CI, ICL>(in, g.n, cell, kc);
-  }
+  gather_tile<CI, C::KC, TI, ICL>(xs, in, g, x0, y0, z0);
   // output gradients of the tile's cells (0 outside the mesh) as BF16 slabs
   // [co slab][cell][8 co]; cell = (z * UY + y) * UX + x
 #pragma unroll 4
-  for (int t = tid; t < (C::NP / 8) * C::TC; t += UThreads) {
+  for (int t = tid; t < C::GS * C::TC; t += UThreads) {
     const int c = t % C::TC, cs = t / C::TC;
     const int gx = x0 + c % UX, gy = y0 + (c / UX) % UY, gz = z0 + c / C::PC;
     const bool in_mesh = gx < g.nx && gy < g.ny && gz < g.nz;
@@ -394,95 +422,75 @@ k_wgrad_umma(const TI* __restrict__ in, const float* __restrict__ gout,
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) bsum[warp][co / (UThreads / 32)] = acc;
   }
-  if (tid == 0) {
-    umma::mbar_init(&mbar[0], 1);
-    umma::mbar_init(&mbar[1], 1);
-  }
-  if (warp == 0) umma::tmem_alloc(&tmem_slot, C::tmem_cols);
+  cp_async_wait_all();
+  if (tid == 0) umma::mbar_init(&mbar, 1);
+  if (warp == 0) umma::tmem_alloc(&tmem_slot, 512);
+  umma::fence_smem_for_mma();
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = tmem_slot;
-  constexpr uint32_t idesc = umma::idesc_bf16(128, C::NP) | (1u << 15) | (1u << 16);  // MN-major
-  constexpr int NIT = C::NG * UZ;   // (group, plane) steps; step it uses A buffer it & 1
+  constexpr uint32_t idesc = umma::idesc_bf16(128, C::NPC) | (1u << 15) | (1u << 16);  // MN-major
+  float* dst = partial + (size_t)blockIdx.x * (CI * 27 + 1) * CO;
   bool ok = true;
-  int issued = 0;                   // steps whose MMAs were issued
-  for (int it = 0; it < NIT; ++it) {
-    const int gi = it / UZ, z = it % UZ, buf = it & 1;
-    uint4* as = as2[buf];
-    {
-      // the MMAs of step it - 2 read this buffer: wait for them (mbarrier
-      // use (it >> 1) - 1 of this buffer)
-      bool w = true;
-      if (it >= 2) w = umma::mbar_wait(&mbar[buf], (uint32_t)(((it >> 1) - 1) & 1), kMmaPolls);
-      umma::fence_after_sync();
-      // A for (group gi, plane z): slab (j, kc) holds channels kc*8.. of the
-      // plane's cells shifted by offset o = gi * G + j (zero past 26)
-#pragma unroll 4
-      for (int t = tid; t < C::G * C::KC * C::PC; t += UThreads) {
-        const int c = t % C::PC, jk = t / C::PC, kc = jk % C::KC, j = jk / C::KC;
-        const int o = gi * C::G + j;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (o < 27) {
-          const int dz = o / 9, dy = (o / 3) % 3, dx = o % 3;
-          const int hc = ((z + dz) * UHY + (c / UX + dy)) * UHX + (c % UX + dx);
-          v = xs[kc * UHN + hc];
-        }
-        as[t] = v;
-      }
-      umma::fence_smem_for_mma();
-      umma::fence_before_sync();
-      // the whole block agrees on the outcome (a wait that ran out ends the
-      // loop for all)
-      ok = __syncthreads_and(w) != 0;
-      umma::fence_after_sync();
-      if (!ok) break;
-      if (tid == 0) {
-        const uint32_t aa = umma::smem_addr(as), ga = umma::smem_addr(gs);
+  int issued = 0;   // passes whose MMAs were issued
+  for (int pass = 0; pass < C::NPASS; ++pass) {
+    const int o0 = pass * C::OPP, o1 = min(27, o0 + C::OPP);
+    if (tid == 0) {
+      // base descriptors plus byte offsets / 16 (see tile_mmas)
+      const uint64_t a0 = umma::desc(umma::smem_addr(gs), 128, C::TC * 16);
+      const uint64_t b0 = umma::desc(umma::smem_addr(xs), UHX * 16, UHN * 16);
+#pragma unroll 1
+      for (int o = o0; o < o1; ++o) {
+        const int dz = o / 9, dy = (o / 3) % 3, dx = o % 3;
+        const uint64_t bo = b0 + (uint64_t)((dz * UHY + dy) * UHX + dx);
+        const uint32_t d = tmem + (uint32_t)((o - o0) * C::NPC);
 #pragma unroll
-        for (int ks = 0; ks < C::PC / 16; ++ks) {
-          const uint64_t a = umma::desc(aa + ks * 256, 128, C::PC * 16);
-          const uint64_t b = umma::desc(ga + (z * C::PC + ks * 16) * 16, 128, C::TC * 16);
-          umma::mma_bf16(tmem + gi * C::NP, a, b, idesc, (z > 0 || ks > 0) ? 1u : 0u);
+        for (int z = 0; z < UZ; ++z) {
+#pragma unroll
+          for (int ks = 0; ks < C::PC / 16; ++ks) {
+            // cells ks*16 .. +15 of plane z: rows y = 2 ks, 2 ks + 1 of the tile
+            const uint64_t a = a0 + (uint64_t)(z * C::PC + ks * 16);
+            const uint64_t b = bo + (uint64_t)((z * UHY + 2 * ks) * UHX);
+            umma::mma_bf16(d, a, b, idesc, (z > 0 || ks > 0) ? 1u : 0u);
+          }
         }
-        umma::commit(&mbar[buf]);
       }
-      issued = it + 1;
+      umma::commit(&mbar);
     }
-  }
-  // the last two issued steps' MMAs (bounded waits) before TMEM is read or
-  // freed
-  {
-    bool w = true;
-    for (int it = issued - 2; it < issued; ++it)
-      if (it >= 0) w = umma::mbar_wait(&mbar[it & 1], (uint32_t)((it >> 1) & 1), kMmaPolls) && w;
+    issued = pass + 1;
+    ok = __syncthreads_and(umma::mbar_wait(&mbar, (uint32_t)(pass & 1), kMmaPolls)) != 0;
+    umma::fence_after_sync();
+    if (!ok) break;
+    if ((warp & 3) == 0) {
+      // lane = output channel; column (o - o0) * NPC + ci
+      const int q = warp >> 2;   // 0, 1, 2: offsets o0 + q, o0 + q + 3, ...
+#pragma unroll 1
+      for (int o = o0 + q; o < o1; o += 3) {
+        float v[32];
+        const uint32_t ta = tmem + (uint32_t)((o - o0) * C::NPC);
+        umma::ld16(ta, v);
+        if (C::NPC > 16) umma::ld16(ta + 16, v + 16);
+        if (lane < CO) {
+#pragma unroll
+          for (int ci = 0; ci < CI; ++ci) dst[(ci * 27 + o) * CO + lane] = v[ci];
+        }
+      }
+    }
+    // the pass's accumulators are read before the next pass overwrites them
     umma::fence_before_sync();
-    ok = __syncthreads_and(w && ok) != 0;
+    __syncthreads();
     umma::fence_after_sync();
   }
-  float* dst = partial + (size_t)blockIdx.x * (CI * 27 + 1) * CO;
   if (!ok) {
-    if (lane == 0) atomicOr(status, 1u);
-  } else if (warp < 4) {
-    // TMEM lane m = (j, ci) of group gi holds D[(o, ci)][0 .. NP)
-    const int m = tid, j = m / C::CIP, ci = m % C::CIP;
-#pragma unroll 1
-    for (int gi = 0; gi < C::NG; ++gi) {
-      float v[32];
-      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + gi * C::NP;
-      umma::ld16(ta, v);
-      if (C::NP > 16) umma::ld16(ta + 16, v + 16);
-      const int o = gi * C::G + j;
-      if (o < 27 && ci < CI) {
-#pragma unroll
-        for (int co = 0; co < CO; ++co) dst[(ci * 27 + o) * CO + co] = v[co];
-      }
-    }
+    if (tid == 0) atomicOr(status, 1u);
+    // let the MMAs of the last issued pass drain (bounded) before TMEM is freed
+    umma::mbar_wait(&mbar, (uint32_t)((issued - 1) & 1), kMmaPolls);
   }
   if (tid < CO) dst[(CI * 27) * CO + tid] = bsum[tid % (UThreads / 32)][tid / (UThreads / 32)];
   umma::fence_before_sync();
   __syncthreads();
-  if (warp == 0) umma::tmem_free(tmem, C::tmem_cols);
+  if (warp == 0) umma::tmem_free(tmem, 512);
 }
 
 // Sums the per-tile partials in tile order and scatters them into the flat
@@ -493,8 +501,18 @@ __global__ void k_wgrad_reduce(const float* __restrict__ partial, int ntiles,
   constexpr int NP = CI * 27 + 1;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= NP * CO) return;
-  float s = 0.0f;
-  for (int b = 0; b < ntiles; ++b) s += partial[(size_t)b * NP * CO + t];
+  // eight interleaved partial sums (tiles b = r mod 8), added in a fixed
+  // order: the same bits every call, eight loads in flight per thread
+  float a[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  int b = 0;
+  for (; b + 8 <= ntiles; b += 8) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) a[r] += partial[(size_t)(b + r) * NP * CO + t];
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+    if (b + r < ntiles) a[r] += partial[(size_t)(b + r) * NP * CO + t];
+  const float s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
   const int p = t / CO, co = t % CO;
   if (p == CI * 27) grads[boff + co] = s;
   else grads[woff + co * CI * 27 + p] = s;
@@ -548,6 +566,26 @@ __device__ __forceinline__ float correction(const float* __restrict__ o, float s
   return -dt * scale * ((inv[0] * sx + inv[1] * sy) + inv[2] * sz);
 }
 
+// (channel q, cell i, j, k) of flat index t = q n + (k ny + j) nx + i, in 32-bit
+// arithmetic when every index fits (the 64-bit divisions are long sequences)
+__device__ __forceinline__ void split_index(long long t, const Grid3& g, int& q, int& i, int& j,
+                                            int& k) {
+  if (5LL * g.n <= 0x7FFFFFFFLL) {
+    const unsigned u = (unsigned)t, n = (unsigned)g.n, nx = (unsigned)g.nx, ny = (unsigned)g.ny;
+    const unsigned qq = u / n, m = u - qq * n, r = m / nx, kk = r / ny;
+    q = (int)qq;
+    i = (int)(m - r * nx);
+    j = (int)(r - kk * ny);
+    k = (int)kk;
+  } else {
+    q = (int)(t / g.n);
+    const long long m = t - q * g.n;
+    i = (int)(m % g.nx);
+    j = (int)((m / g.nx) % g.ny);
+    k = (int)(m / ((long long)g.nx * g.ny));
+  }
+}
+
 // Loss terms: e = (dU - r) / sigma; per-block partial sums of e^2 (FP64);
 // g = dL/d(dU) = 2 e / (sigma N).
 __global__ void __launch_bounds__(256)
@@ -559,9 +597,8 @@ k_loss(const float* __restrict__ o, const double* __restrict__ r, const float* _
   double acc = 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(t / g.n);
-    const long long m = t - q * g.n;
-    const int i = (int)(m % g.nx), j = (int)((m / g.nx) % g.ny), k = (int)(m / ((long long)g.nx * g.ny));
+    int q, i, j, k;
+    split_index(t, g, q, i, j, k);
     const float du = correction(o, scales[q], q, i, j, k, g, dt, inv);
     const float sig = scales[5 + q];
     const float e = (du - (float)r[t]) / sig;
@@ -586,9 +623,8 @@ k_loss_adjoint(const float* __restrict__ gdu, const float* __restrict__ scales, 
   const long long total = 5 * g.n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(t / g.n);
-    const long long m = t - q * g.n;
-    const int i = (int)(m % g.nx), j = (int)((m / g.nx) % g.ny), k = (int)(m / ((long long)g.nx * g.ny));
+    int q, i, j, k;
+    split_index(t, g, q, i, j, k);
     go[t] = correction(gdu, scales[q], q, i, j, k, g, dt, inv);
   }
 }
@@ -633,9 +669,8 @@ k_apply_correction(double* __restrict__ U, fvd::Params P, const float* __restric
   const long long total = 5 * g.n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(t / g.n);
-    const long long m = t - q * g.n;
-    const int i = (int)(m % g.nx), j = (int)((m / g.nx) % g.ny), k = (int)(m / ((long long)g.nx * g.ny));
+    int q, i, j, k;
+    split_index(t, g, q, i, j, k);
     const float du = correction(o, scales[q], q, i, j, k, g, dt, inv);
     U[q * P.nfield + (k + 2) * P.sz + (j + 2) * P.sy + (i + 2)] += fvd32::f2d(du);
   }
