@@ -354,9 +354,17 @@ FV_API fv_status fv_net_forward(fv_net_t n, fv_mesh_t m, float* o_out);
  * solution averaged to the mesh minus the mesh's own RK2 step over dt),
  * gradients by the backward kernels, then Adam (beta 0.9, 0.999, eps 1e-8)
  * with learning rate lr (lr = 0: gradients only).  *loss_out = L before the
- * update.  Synchronising. */
+ * update; synchronising.  With loss_out NULL the step is asynchronous (no
+ * host wait, so a loop of steps keeps the GPU busy): L is added to a
+ * device-side sum that fv_net_take_loss returns, and a convolution's wait
+ * that ran out is reported by the next synchronising net call. */
 FV_API fv_status fv_net_train_step(fv_net_t n, fv_mesh_t m, const double* residual, double dt,
                                    double lr, double* loss_out);
+/* The sum of the losses of the asynchronous train steps since the last
+ * call, and their number (either pointer may be NULL); clears both.
+ * Synchronising (waits for the net's last stream); FV_ERR_TIMEOUT if one of
+ * those steps' convolutions ran out of its wait limit. */
+FV_API fv_status fv_net_take_loss(fv_net_t n, double* loss_sum, long long* steps);
 /* One corrected step: phi from the current state, fv_step(m, dt), then
  * U += dU(phi) on the interior and a ghost fill.  Asynchronous. */
 FV_API fv_status fv_step_learned(fv_mesh_t m, fv_net_t n, double dt);

@@ -393,34 +393,68 @@ k_wgrad_umma(const TI* __restrict__ in, const float* __restrict__ gout,
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   __shared__ float bsum[UThreads / 32][32];
+  __shared__ float bthr[GCL ? UThreads : 1][8];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int x0, y0, z0;
   tile_origin(blockIdx.x, g, x0, y0, z0);
   // input halo tile (periodic) as BF16 slabs [kc][halo cell][8 ch]
   gather_tile<CI, C::KC, TI, ICL>(xs, in, g, x0, y0, z0);
   // output gradients of the tile's cells (0 outside the mesh) as BF16 slabs
-  // [co slab][cell][8 co]; cell = (z * UY + y) * UX + x
+  // [co slab][cell][8 co]; cell = (z * UY + y) * UX + x.  Channel-last
+  // gradients: item t is slab t % GS of cell t / GS, so a thread always
+  // handles the same slab (UThreads is a multiple of GS) and neighbouring
+  // threads read neighbouring 32-byte pieces; the thread also sums its 8
+  // channels in FP32 for the bias gradients.
+  static_assert(UThreads % C::GS == 0, "slab per thread");
+  float bpart[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll 4
   for (int t = tid; t < C::GS * C::TC; t += UThreads) {
-    const int c = t % C::TC, cs = t / C::TC;
+    const int c = GCL ? t / C::GS : t % C::TC, cs = GCL ? t % C::GS : t / C::TC;
     const int gx = x0 + c % UX, gy = y0 + (c / UX) % UY, gz = z0 + c / C::PC;
     const bool in_mesh = gx < g.nx && gy < g.ny && gz < g.nz;
     const long long cell = ((long long)gz * g.ny + gy) * g.nx + gx;
-    gs[t] = in_mesh ? gather8<CO, GCL>(gout, g.n, cell, cs) : make_uint4(0u, 0u, 0u, 0u);
-  }
-  // bias gradients in FP32: warp w sums outputs co = w, w + 12, ... over the tile
-  for (int co = warp; co < CO; co += UThreads / 32) {
-    float acc = 0.0f;
-    for (int c = lane; c < C::TC; c += 32) {
-      const int gx = x0 + c % UX, gy = y0 + (c / UX) % UY, gz = z0 + c / C::PC;
-      if (gx < g.nx && gy < g.ny && gz < g.nz) {
-        const long long cell = ((long long)gz * g.ny + gy) * g.nx + gx;
-        acc += gout[GCL ? cell * pitch8<CO>() + co : co * g.n + cell];
-      }
-    }
+    if constexpr (GCL) {
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (in_mesh) {
+        const float* p = gout + cell * pitch8<CO>() + cs * 8;
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        const float4 b = *reinterpret_cast<const float4*>(p + 4);
+        const float f[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        __align__(16) bf16 h[8];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) bsum[warp][co / (UThreads / 32)] = acc;
+        for (int j = 0; j < 8; ++j) {
+          bpart[j] += f[j];
+          h[j] = to_bf(f[j]);
+        }
+        v = *reinterpret_cast<const uint4*>(h);
+      }
+      gs[cs * C::TC + c] = v;
+    } else {
+      gs[t] = in_mesh ? gather8<CO, GCL>(gout, g.n, cell, cs) : make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+  // bias gradients in FP32, in a fixed order.  Channel-last gradients: each
+  // thread's 8 channel sums go to shared memory, and the threads of a slab
+  // are added in thread order below.  Channel-first: warp w sums output
+  // co = w, w + 12, ... over the tile's cells (lanes along the cells, then a
+  // shuffle tree).
+  if constexpr (GCL) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) bthr[tid][j] = bpart[j];
+  } else {
+    for (int co = warp; co < CO; co += UThreads / 32) {
+      float acc = 0.0f;
+      for (int c = lane; c < C::TC; c += 32) {
+        const int gx = x0 + c % UX, gy = y0 + (c / UX) % UY, gz = z0 + c / C::PC;
+        if (gx < g.nx && gy < g.ny && gz < g.nz) {
+          const long long cell = ((long long)gz * g.ny + gy) * g.nx + gx;
+          acc += gout[co * g.n + cell];
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) bsum[warp][co / (UThreads / 32)] = acc;
+    }
   }
   cp_async_wait_all();
   if (tid == 0) umma::mbar_init(&mbar, 1);
@@ -487,35 +521,59 @@ k_wgrad_umma(const TI* __restrict__ in, const float* __restrict__ gout,
     // let the MMAs of the last issued pass drain (bounded) before TMEM is freed
     umma::mbar_wait(&mbar, (uint32_t)((issued - 1) & 1), kMmaPolls);
   }
-  if (tid < CO) dst[(CI * 27) * CO + tid] = bsum[tid % (UThreads / 32)][tid / (UThreads / 32)];
+  if (tid < CO) {
+    float b;
+    if constexpr (GCL) {
+      // output co is channel co % 8 of slab co / 8: threads co / 8, + GS, ...
+      b = 0.0f;
+      for (int r = tid / 8; r < UThreads; r += C::GS) b += bthr[r][tid % 8];
+    } else {
+      b = bsum[tid % (UThreads / 32)][tid / (UThreads / 32)];
+    }
+    dst[(CI * 27) * CO + tid] = b;
+  }
   umma::fence_before_sync();
   __syncthreads();
   if (warp == 0) umma::tmem_free(tmem, 512);
 }
 
-// Sums the per-tile partials in tile order and scatters them into the flat
-// gradient: weights at woff + (co * CI + ci) * 27 + o, biases at boff + co.
+// Sums the per-tile partials and scatters them into the flat gradient:
+// weights at woff + (co * CI + ci) * 27 + o, biases at boff + co.  A block
+// covers 32 outputs with 8 warps; warp w sums tiles w, w + 8, ... (in order,
+// one coalesced row of 32 outputs per load) and the 8 warp sums are added in
+// warp order: the same bits every call.
 template <int CI, int CO>
-__global__ void k_wgrad_reduce(const float* __restrict__ partial, int ntiles,
-                               float* __restrict__ grads, int woff, int boff) {
+__global__ void __launch_bounds__(256)
+k_wgrad_reduce(const float* __restrict__ partial, int ntiles, float* __restrict__ grads,
+               int woff, int boff) {
   constexpr int NP = CI * 27 + 1;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= NP * CO) return;
-  // eight interleaved partial sums (tiles b = r mod 8), added in a fixed
-  // order: the same bits every call, eight loads in flight per thread
-  float a[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-  int b = 0;
-  for (; b + 8 <= ntiles; b += 8) {
+  __shared__ float ws[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int t = blockIdx.x * 32 + lane;
+  float a = 0.0f;
+  if (t < NP * CO)
+    for (int b = w; b < ntiles; b += 8) a += partial[(size_t)b * NP * CO + t];
+  ws[w][lane] = a;
+  __syncthreads();
+  if (w == 0 && t < NP * CO) {
+    float s = ws[0][lane];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) a[r] += partial[(size_t)(b + r) * NP * CO + t];
+    for (int r = 1; r < 8; ++r) s += ws[r][lane];
+    const int p = t / CO, co = t % CO;
+    if (p == CI * 27) grads[boff + co] = s;
+    else grads[woff + co * CI * 27 + p] = s;
   }
-#pragma unroll
-  for (int r = 0; r < 8; ++r)
-    if (b + r < ntiles) a[r] += partial[(size_t)(b + r) * NP * CO + t];
-  const float s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
-  const int p = t / CO, co = t % CO;
-  if (p == CI * 27) grads[boff + co] = s;
-  else grads[woff + co * CI * 27 + p] = s;
+}
+
+// acc += (sum of the loss kernel's block partials, in block order) / denom:
+// the value a synchronous step reports, added to the running sum.
+__global__ void k_loss_accumulate(const double* __restrict__ partial, int n, double denom,
+                                  double* __restrict__ acc) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double L = 0.0;
+    for (int b = 0; b < n; ++b) L += partial[b];
+    *acc += L / denom;
+  }
 }
 
 // Weights of the adjoint convolution: wt[ci][co][26 - o] = w[co][ci][o].
@@ -714,6 +772,8 @@ struct fv_net_s {
   float* partial = nullptr;
   double* loss_partial = nullptr;
   double* host_loss = nullptr;
+  double* loss_acc = nullptr;       // device: losses of the asynchronous steps, summed
+  long long acc_steps = 0;          // steps in loss_acc
   uint4* wlay = nullptr;            // laid-out weights of the convolution being run
   unsigned* status = nullptr;       // device: set by a convolution whose MMA wait ran out
   unsigned* host_status = nullptr;  // pinned mirror
@@ -771,6 +831,7 @@ void free_net(fv_net_s* n) {
   cudaFree(n->norm);
   cudaFree(n->loss_partial);
   cudaFreeHost(n->host_loss);
+  cudaFree(n->loss_acc);
   cudaFree(n->status);
   cudaFreeHost(n->host_status);
   cudaFree(n->wlay);
@@ -837,7 +898,7 @@ cudaError_t conv_wgrad(const TI* in, const float* gout, float* partial, float* g
   const int nb = tiles(g.nx, UX) * tiles(g.ny, UY) * tiles(g.nz, UZ);
   k<<<nb, UThreads, smem, s>>>(in, gout, partial, g, status);
   constexpr int NW = (CI * 27 + 1) * CO;
-  k_wgrad_reduce<CI, CO><<<(NW + 255) / 256, 256, 0, s>>>(partial, nb, grads, woff, boff);
+  k_wgrad_reduce<CI, CO><<<(NW + 31) / 32, 256, 0, s>>>(partial, nb, grads, woff, boff);
   return cudaGetLastError();
 }
 
@@ -899,6 +960,8 @@ fv_status fv_net_create(fv_net_t* out) {
   if (e == cudaSuccess) e = cudaMalloc(&n->scales, 10 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&n->norm, 10 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&n->loss_partial, kLossBlocks * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&n->loss_acc, sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(n->loss_acc, 0, sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&n->host_loss, kLossBlocks * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&n->status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMalloc(&n->wlay, UConv<CH, CH>::w_bytes);
@@ -1053,6 +1116,16 @@ fv_status fv_net_train_step(fv_net_t n, fv_mesh_t m, const double* residual, dou
                                                 NPARAM, (float)lr, b1, b2, 1e-8f, c1, c2);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess && !loss_out) {
+    // asynchronous step: the loss joins the device sum (fv_net_take_loss)
+    k_loss_accumulate<<<1, 32, 0, s>>>(n->loss_partial, kLossBlocks, 5.0 * (double)g.n,
+                                       n->loss_acc);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "network training step");
+    n->acc_steps += 1;
+    n->have_grads = true;
+    return FV_OK;
+  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(n->host_loss, n->loss_partial, kLossBlocks * sizeof(double),
                         cudaMemcpyDeviceToHost, s);
@@ -1068,6 +1141,23 @@ fv_status fv_net_train_step(fv_net_t n, fv_mesh_t m, const double* residual, dou
     *loss_out = L / (5.0 * (double)g.n);
   }
   return FV_OK;
+}
+
+fv_status fv_net_take_loss(fv_net_t n, double* loss_sum, long long* steps) {
+  fv_status st = check(n);
+  if (st != FV_OK) return st;
+  cudaStream_t s = n->last_stream;
+  double sum = 0.0;
+  cudaError_t e = cudaMemcpyAsync(&sum, n->loss_acc, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(n->host_status, n->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->loss_acc, 0, sizeof(double), s);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the training loss");
+  if (loss_sum) *loss_sum = sum;
+  if (steps) *steps = n->acc_steps;
+  n->acc_steps = 0;
+  return take_status(n, s);
 }
 
 fv_status fv_step_learned(fv_mesh_t m, fv_net_t n, double dt) {

@@ -94,6 +94,10 @@ __device__ __forceinline__ void halo_cell(int h, int& row, int& col) {
 // window) and the halo cells of plane k, each copied by the thread that uses
 // it, so a slot is reused without a barrier.
 constexpr int kStageDepth = FV32_STAGE_DEPTH;
+#ifndef FV32_EQ_SKIP
+#define FV32_EQ_SKIP 0
+#endif
+static_assert(!FV32_EQ_SKIP || FV32_STAGE_DEPTH == 1, "the equal-state skip stages one plane ahead");
 constexpr int kRing = kStageDepth + 1;
 
 template <class S>
@@ -305,8 +309,14 @@ __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
   for (int k = k0; k < k1; ++k) {
     if (owner && !physical(w0)) ++bad;   // each interior cell once per substep
     if (NEXT && STAGE == 2) refresh_max(gmax, smax_next, smax_next_f);
+#if FV32_EQ_SKIP
+    // the next plane is staged after this plane's input has been compared
+    // with the previous plane's (still in the other slot)
+    cp_async_wait<0>();
+#else
     stage_in(k + kStageDepth);
     cp_async_wait<kStageDepth>();        // this iteration's group has landed
+#endif
     const int slot = k % kRing;
     double cur_col[NF];
 #pragma unroll
@@ -326,7 +336,17 @@ __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
     // equal, its slopes are +0 and its face states are those of face k-1/2:
     // its flux and fallback are the previous face's, bit for bit (reused when
     // the whole warp can).
+#if FV32_EQ_SKIP
+    // a column cell whose FP64 state equals the previous plane's has its
+    // primitives (the same bits): skipped when the whole warp can
+    bool eqc = k > k0;
+#pragma unroll
+    for (int q = 0; q < NF; ++q)
+      eqc = eqc && fvd::bits(cur_col[q]) == fvd::bits(s.col[(k + 1) % kRing][q][tid]);
+    const Prim32 w2 = __all_sync(0xffffffffu, eqc) ? w1 : prim_from_state(cur_col, Q);
+#else
     const Prim32 w2 = prim_from_state(cur_col, Q);
+#endif
     run = same32(w2, w1) ? run + 1 : 1;
     Prim32 d2, h1;
     float fz_hi[NF];
@@ -356,13 +376,35 @@ __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
 #pragma unroll
     for (int e = 0; e < kHaloPer; ++e) {
       const int h = tid + e * kThreads;
+#if FV32_EQ_SKIP
+      // a halo cell whose FP64 state equals the previous plane's keeps its
+      // primitives in shared memory (the same bits), decided per warp
+      double uh[NF];
+      bool eqh = k > k0;
+#pragma unroll
+      for (int q = 0; q < NF; ++q) {
+        uh[q] = h < kHalo ? s.halo[slot][q][h] : 0.0;
+        eqh = eqh && (h >= kHalo || fvd::bits(uh[q]) == fvd::bits(s.halo[(k + 1) % kRing][q][h]));
+      }
+      const bool all_eq = __all_sync(0xffffffffu, eqh);
+      if (h < kHalo) {
+        if (all_eq)
+          s.same[hrow[e] + 2][hcol[e] + 2] = 1;
+        else
+          smem_store_flag(s, hrow[e] + 2, hcol[e] + 2, prim_from_state(uh, Q), k > k0);
+      }
+#else
       if (h < kHalo) {
         double uh[NF];
 #pragma unroll
         for (int q = 0; q < NF; ++q) uh[q] = s.halo[slot][q][h];
         smem_store_flag(s, hrow[e] + 2, hcol[e] + 2, prim_from_state(uh, Q), k > k0);
       }
+#endif
     }
+#if FV32_EQ_SKIP
+    stage_in(k + 1);   // into the other slot, now compared
+#endif
     __syncthreads();
     // (c) x faces: face fi (between columns fi-1 and fi) of row r.  A face
     // whose four cells all equal the previous plane's has that plane's

@@ -33,6 +33,7 @@ ABI_SYMBOLS = (
     "fv_batch_get_class_tuning",
     "fv_net_param_count", "fv_net_create", "fv_net_destroy", "fv_net_set_params",
     "fv_net_get_params", "fv_net_set_scales", "fv_net_forward", "fv_net_train_step",
+    "fv_net_take_loss",
     "fv_step_learned", "fv_net_get_buffer",
 )
 KERNEL_CLASSES = ("prim", "sweep_x", "sweep_y", "sweep_z", "fused", "ghost", "dt", "other")
@@ -114,6 +115,7 @@ def load_library(path: str | None = None):
         "fv_net_set_scales": ([vp, dp, dp, dp, dp], i),
         "fv_net_forward": ([vp, vp, vp], i),
         "fv_net_train_step": ([vp, vp, vp, d, d, dp], i),
+        "fv_net_take_loss": ([vp, dp, ctypes.POINTER(ctypes.c_longlong)], i),
         "fv_step_learned": ([vp, vp, d], i),
         "fv_net_get_buffer": ([vp, i, vp, ctypes.c_size_t], i),
         "fv_status_string": ([i], ctypes.c_char_p),
@@ -509,15 +511,26 @@ class Net:
                "fv_net_forward")
         return out
 
-    def train_step(self, mesh, residual, dt, lr):
+    def train_step(self, mesh, residual, dt, lr, sync=True):
+        """One training step; returns its loss (sync), or None and adds the
+        loss to the device-side sum that take_loss() returns (sync=False: no
+        host wait)."""
         torch = _torch()
         assert isinstance(residual, torch.Tensor) and residual.is_cuda
         assert residual.dtype == torch.float64 and tuple(residual.shape) == mesh.shape
         loss = ctypes.c_double()
         _check(self._lib.fv_net_train_step(self._h, mesh.handle,
                                            ctypes.c_void_p(residual.data_ptr()), float(dt),
-                                           float(lr), ctypes.byref(loss)), "fv_net_train_step")
-        return loss.value
+                                           float(lr), ctypes.byref(loss) if sync else None),
+               "fv_net_train_step")
+        return loss.value if sync else None
+
+    def take_loss(self):
+        """(sum of the asynchronous steps' losses, their number); clears."""
+        total, n = ctypes.c_double(), ctypes.c_longlong()
+        _check(self._lib.fv_net_take_loss(self._h, ctypes.byref(total), ctypes.byref(n)),
+               "fv_net_take_loss")
+        return total.value, n.value
 
     def step(self, mesh, dt):
         _check(self._lib.fv_step_learned(mesh.handle, self._h, float(dt)), "fv_step_learned")

@@ -118,6 +118,36 @@ def test_training_reduces_the_loss():
     net.close()
 
 
+def test_asynchronous_steps_match_synchronous_steps():
+    """Train steps without a loss read (no host wait) compute the same
+    parameters bit for bit, and fv_net_take_loss returns the sum of the
+    losses the synchronous steps report (the same operations, the same
+    order), then zero."""
+    shape = (16, 16, 8)
+    r = None
+    out = []
+    for sync in (True, False):
+        U0, p, mesh, net = _setup(shape, seed=6)
+        phi, _ = L.forward(p, _prims(U0), NORM, PER)
+        r = L.laplacian_update(1.2 * phi, 0.01, _inv_d(shape), PER)
+        rt = torch.from_numpy(r).cuda()
+        total = 0.0
+        for _ in range(5):
+            v = net.train_step(mesh, rt, 0.01, 2e-3, sync=sync)
+            if sync:
+                total += v
+        if not sync:
+            total, n = net.take_loss()
+            assert n == 5
+            assert net.take_loss() == (0.0, 0)
+        params, grads = net.params(), net.grads()
+        out.append((total, params, grads))
+        mesh.close()
+        net.close()
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+
+
 def test_zero_network_gives_the_plain_step_bitwise():
     shape = (12, 10, 9)
     U0 = problems.random_smooth_periodic(*shape, seed=2)
