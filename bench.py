@@ -81,10 +81,10 @@ FF_OPS_CELL = 380
 # `python -m paper_1812_07977_gb300.run_case PRECISION 256 oblique 3`) of the
 # kernels as they are now; None where the kernel has changed since.
 FUSED_TRAFFIC = {
-    "fp32_bulk": (1.714e9, "ncu capture 2026-12-04 of k_stage32<., 16, 8, 4, 1>: "
-                           "1.393 GB (stage 1) and 2.036 GB (stage 2)"),
-    "fp64_ff": (1.950e9, "ncu capture 2026-12-04 of k_stageff<., MC, 8, 2>: "
-                         "1.590 GB (stage 1) and 2.310 GB (stage 2)"),
+    "fp32_bulk": (1.736e9, "ncu capture 2026-12-04 of k_stage32<., 16, 8, 4, 1> (equal-state "
+                           "skip): 1.418 GB (stage 1) and 2.054 GB (stage 2)"),
+    "fp64_ff": (1.966e9, "ncu capture 2026-12-04 of k_stageff<., MC, 16, 16, 2>: "
+                         "1.606 GB (stage 1) and 2.326 GB (stage 2)"),
     "fp64_fma": None,
     "fp64": None,
 }

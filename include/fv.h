@@ -444,15 +444,18 @@ FV_API fv_status fv_conserved_sums_noalloc(const double* U, int nx, int ny, int 
  *                        (8 warps, up to 255 registers); the same bits
  *  FV_TUNE_TILE_Y        tile height of the fused FP32-bulk kernel: 4, 8
  *                        (default) or 16 (CTAs of TX x TY threads, one per
- *                        column; 4 and 16 at width 32 only); for FP64_FF
- *                        meshes 8 (default), or 12 or 16 at occupancy 1
- *                        (set the occupancy first); the same bits
+ *                        column; 4 and 16 at width 32 only); the same bits
  *  FV_TUNE_TILE_X        tile width of the fused FP32-bulk kernel: 16
  *                        (default), 32, 64 or 128.  (tile x, tile y,
  *                        occupancy) must be one of (32, 4|8|16, 2),
  *                        (32, 8, 3), (16, 8, 2), (64, 4|8, 2), (128, 4, 2)
  *                        after each change, so change them in an order that
- *                        passes through built shapes; the same bits
+ *                        passes through built shapes; the same bits.
+ *                        FP64_FF meshes: (tile x, tile y, CTAs per SM) one
+ *                        of (16, 16, 2) (the default), (16, 16, 1),
+ *                        (32, 8, 1 | 2), (32, 16, 1) after each change (to
+ *                        32 x 8: occupancy 1, tile_x 32, tile_y 8, then
+ *                        occupancy 2 if wanted); the same bits
  *  FV_TUNE_SWEEP_SEGMENTS  FP64 sweeps: pieces each grid line of a sweep is
  *                        cut into, to run more, shorter work items (integer
  *                        in [0, 4096], capped at the line's length; 0, the

@@ -64,7 +64,7 @@ struct fv_mesh_s {
   int segments;             // pieces per grid line of the FP64 sweeps (0: automatic)
   bool fused64;             // FP64: one fused kernel per substep (else the per-axis sweeps)
   int ff_ctas_per_sm;       // FP64_FF: CTAs per SM its fused kernel is built for (1 or 2)
-  int ff_tile_y;            // FP64_FF: tile height of its fused kernel (8, 12 or 16)
+  int ff_tile_x, ff_tile_y; // FP64_FF: tile of its fused kernel (16 x 16; 32 x 8, 16)
   bool w_current;           // FP64 sweeps: W holds the primitives of U (from the dt pass)
   bool smax_current;        // fused paths: ctr->smax_next is the CFL maximum of U
   // profiling
@@ -269,8 +269,8 @@ cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
     if (e == cudaSuccess)
       e = timed(m, FV_KERNEL_FUSED, 1, [&] {
         if (ff)
-          return fv_fp64_ff::launch_fused(stage, m->buf, m->P, dt, m->kchunk, m->ff_tile_y,
-                                          m->ff_ctas_per_sm, m->stream);
+          return fv_fp64_ff::launch_fused(stage, m->buf, m->P, dt, m->kchunk, m->ff_tile_x,
+                                          m->ff_tile_y, m->ff_ctas_per_sm, m->stream);
         return fma ? fv_fp64_fma::launch_fused(stage, m->buf, m->P, dt, m->kchunk, m->stream)
                    : fv_fp64_exact::launch_fused(stage, m->buf, m->P, dt, m->kchunk,
                                                  m->stream);
@@ -356,7 +356,8 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   m->segments = 0;
   m->fused64 = false;
   m->ff_ctas_per_sm = 2;
-  m->ff_tile_y = 8;
+  m->ff_tile_x = 16;   // 16 x 16 at 2 CTAs per SM (see fv_fused_ff_kernels.cu)
+  m->ff_tile_y = 16;
   m->w_current = false;
   m->smax_current = false;
   for (int c = 0; c < FV_KERNEL_NCLASS; ++c) m->launches[c] = 0;
@@ -646,24 +647,25 @@ fv_status fv_set_tuning(fv_mesh_t m, int key, double value) {
     m->vacuum_ratio = value;
     return FV_OK;
   }
-  if (key == FV_TUNE_OCCUPANCY && m->desc.precision == FV_PREC_FP64_FF) {
-    if ((value != 1.0 && value != 2.0) ||
-        !fv_fp64_ff::valid_fused_config(m->ff_tile_y, (int)value)) {
-      set_error("FV_TUNE_OCCUPANCY of the float-float kernel must be 1, or 2 with tile height "
-                "8 (got %g, tile height %d)", value, m->ff_tile_y);
+  if ((key == FV_TUNE_OCCUPANCY || key == FV_TUNE_TILE_Y || key == FV_TUNE_TILE_X) &&
+      m->desc.precision == FV_PREC_FP64_FF) {
+    // the float-float kernel's (tile x, tile y, CTAs per SM) must stay one of
+    // its built shapes after the change
+    const int v = (int)value;
+    const bool integral = value == (double)v;
+    const int tx = key == FV_TUNE_TILE_X ? v : m->ff_tile_x;
+    const int ty = key == FV_TUNE_TILE_Y ? v : m->ff_tile_y;
+    const int oc = key == FV_TUNE_OCCUPANCY ? v : m->ff_ctas_per_sm;
+    if (!integral || !fv_fp64_ff::valid_fused_config(tx, ty, oc)) {
+      set_error("tuning key %d = %g would make (tile_x, tile_y, CTAs per SM) = (%d, %d, %d), "
+                "not a built shape of the float-float kernel: (16, 16, 1 | 2), (32, 8, 1 | 2), "
+                "(32, 16, 1)",
+                (int)key, value, tx, ty, oc);
       return FV_ERR_INVALID_ARG;
     }
-    m->ff_ctas_per_sm = (int)value;
-    return FV_OK;
-  }
-  if (key == FV_TUNE_TILE_Y && m->desc.precision == FV_PREC_FP64_FF) {
-    if ((value != 8.0 && value != 12.0 && value != 16.0) ||
-        !fv_fp64_ff::valid_fused_config((int)value, m->ff_ctas_per_sm)) {
-      set_error("FV_TUNE_TILE_Y of the float-float kernel must be 8, or 12 or 16 at occupancy 1 "
-                "(got %g, occupancy %d)", value, m->ff_ctas_per_sm);
-      return FV_ERR_INVALID_ARG;
-    }
-    m->ff_tile_y = (int)value;
+    m->ff_tile_x = tx;
+    m->ff_tile_y = ty;
+    m->ff_ctas_per_sm = oc;
     return FV_OK;
   }
   if (key == FV_TUNE_OCCUPANCY || key == FV_TUNE_TILE_Y || key == FV_TUNE_TILE_X) {

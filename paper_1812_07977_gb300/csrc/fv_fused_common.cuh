@@ -7,8 +7,9 @@ namespace fvfused {
 
 constexpr int TX = 32;   // tile width: one warp per tile row
 
-template <int TY_>
+template <int TY_, int TX_ = TX>
 struct Shape64 {
+  static constexpr int TX = TX_;   // the float-float kernel also takes 16
   static constexpr int TY = TY_;
   static constexpr int kThreads = TX * TY;
   static constexpr int PX = TX + 4;
@@ -43,7 +44,7 @@ __device__ __forceinline__ void halo_cell(int h, int& row, int& col) {
     const int u = h - 4 * PX;
     row = u / 4;
     const int c = u % 4;
-    col = c < 2 ? c - 2 : TX + c - 2;
+    col = c < 2 ? c - 2 : S::TX + c - 2;
   }
 }
 

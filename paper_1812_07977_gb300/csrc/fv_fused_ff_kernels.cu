@@ -40,10 +40,10 @@ struct SmemFF {
   double col[2][NF][S::kThreads];   // staged input: the column cell of plane t+2
   double halo[2][NF][S::kHalo];     // staged input: the halo cells of plane t
   ff w[NF][S::PY][S::PX];           // primitives of the plane, tile and halo
-  ff hx[NF][S::TY][TX + 2];         // x half slopes of cells -1 .. TX
-  ff hy[NF][S::TY + 2][TX];         // y half slopes of rows -1 .. TY
-  ff fx[NF][S::TY][TX + 1];         // x face fluxes
-  ff fy[NF][S::TY + 1][TX];         // y face fluxes
+  ff hx[NF][S::TY][S::TX + 2];         // x half slopes of cells -1 .. TX
+  ff hy[NF][S::TY + 2][S::TX];         // y half slopes of rows -1 .. TY
+  ff fx[NF][S::TY][S::TX + 1];         // x face fluxes
+  ff fy[NF][S::TY + 1][S::TX];         // y face fluxes
   unsigned char same[S::PY][S::PX]; // the cell equals (bits) the cell a plane below
   double last[NF][S::kThreads];     // stage 2: the state of the column's last cell written
 };
@@ -117,6 +117,7 @@ __device__ __forceinline__ void stageff_tile(SmemFF<S>& s, double* __restrict__ 
   const double* __restrict__ src = STAGE == 1 ? U : U1;
   constexpr int kThreads = S::kThreads, kHalo = S::kHalo, kHaloPer = S::kHaloPer;
   constexpr int TY = S::TY;
+  constexpr int TX = S::TX;
   const int tid = threadIdx.x;
   const int ti = tid % TX, tj = tid / TX;
   const long long nf = P.nfield;
@@ -431,16 +432,17 @@ __device__ __forceinline__ void max_to(unsigned long long* dst, double smax) {
   if ((threadIdx.x & 31u) == 0u && b) atomicMax(dst, b);
 }
 
-// TY: tile height (tiles of 32 x TY columns, one thread per column); MINB:
-// CTAs per SM the kernel is built for.  Built as 32 x 8 at 1 CTA per SM (8
-// warps, up to 255 registers) or 2 (16 warps, 128 registers, with spills),
-// 32 x 12 at 1 (12 warps, 168 registers) and 32 x 16 at 1 (16 warps, 128
-// registers): more columns per CTA share each halo cell's conversion.
-template <int STAGE, bool MC, int TY, int MINB>
-__global__ void __launch_bounds__(TX * TY, MINB)
+// TXV x TY: the tile (one thread per column); MINB: CTAs per SM the kernel
+// is built for.  Built as 16 x 16 at 2 CTAs per SM (the default: 16 warps,
+// 128 registers with spills; a warp covers 16 x 2 cells, so its reuse
+// decisions hold more often next to the waves, and a halo cell serves 1.8
+// columns) or 1 (8 warps, up to 255 registers); 32 x 8 at 2 or 1; and 32 x 16
+// at 1 (16 warps, 128 registers).
+template <int STAGE, bool MC, int TXV, int TY, int MINB>
+__global__ void __launch_bounds__(TXV * TY, MINB)
 k_stageff(double* __restrict__ U, double* __restrict__ U1, Params P, fvd32::Params32 Q32,
           ConstFF C, double dt, int kchunk, DevCounters* ctr) {
-  using S = Shape64<TY>;
+  using S = Shape64<TY, TXV>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmemFF<S>& s = *reinterpret_cast<SmemFF<S>*>(smem_raw);
   unsigned fallbacks = 0, evaluated = 0;
@@ -448,7 +450,7 @@ k_stageff(double* __restrict__ U, double* __restrict__ U1, Params P, fvd32::Para
   double smax = 0.0;
   float smax_f = 0.0f;
   const int k0 = blockIdx.z * kchunk;
-  stageff_tile<S, STAGE, MC>(s, U, U1, P, Q32, C, dt, blockIdx.x * TX, blockIdx.y * TY, k0,
+  stageff_tile<S, STAGE, MC>(s, U, U1, P, Q32, C, dt, blockIdx.x * TXV, blockIdx.y * TY, k0,
                              min(k0 + kchunk, P.nz), fallbacks, bad, range, evaluated, smax,
                              smax_f, bad_next, &ctr->smax_next);
   if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
@@ -520,66 +522,70 @@ ConstFF make_const(const Params& P) {
   return C;
 }
 
-template <int STAGE, bool MC, int TY, int MINB>
+template <int STAGE, bool MC, int TXV, int TY, int MINB>
 cudaError_t launch_mc(const StepBuffers& b, const Params& P, double dt, int kchunk,
                       cudaStream_t s) {
-  using S = Shape64<TY>;
-  const dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + kchunk - 1) / kchunk);
-  k_stageff<STAGE, MC, TY, MINB><<<grid, S::kThreads, sizeof(SmemFF<S>), s>>>(
+  using S = Shape64<TY, TXV>;
+  const dim3 grid((P.nx + TXV - 1) / TXV, (P.ny + TY - 1) / TY, (P.nz + kchunk - 1) / kchunk);
+  k_stageff<STAGE, MC, TXV, TY, MINB><<<grid, S::kThreads, sizeof(SmemFF<S>), s>>>(
       b.U, b.U1, P, fv_fp32::make_params32(P, 2.0), make_const(P), dt, kchunk, b.ctr);
   return cudaGetLastError();
 }
 
-template <bool MC, int TY, int MINB>
+template <bool MC, int TXV, int TY, int MINB>
 cudaError_t raise_smem() {
-  const int bytes = (int)sizeof(SmemFF<Shape64<TY>>);
-  cudaError_t e = cudaFuncSetAttribute(k_stageff<1, MC, TY, MINB>,
+  const int bytes = (int)sizeof(SmemFF<Shape64<TY, TXV>>);
+  cudaError_t e = cudaFuncSetAttribute(k_stageff<1, MC, TXV, TY, MINB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_stageff<2, MC, TY, MINB>,
+    e = cudaFuncSetAttribute(k_stageff<2, MC, TXV, TY, MINB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   return e;
 }
 
-template <int TY, int MINB>
+template <int TXV, int TY, int MINB>
 cudaError_t raise_both() {
-  cudaError_t e = raise_smem<true, TY, MINB>();
-  return e == cudaSuccess ? raise_smem<false, TY, MINB>() : e;
+  cudaError_t e = raise_smem<true, TXV, TY, MINB>();
+  return e == cudaSuccess ? raise_smem<false, TXV, TY, MINB>() : e;
 }
 
-template <int TY, int MINB>
+template <int TXV, int TY, int MINB>
 cudaError_t launch_shape(int stage, const StepBuffers& b, const Params& P, double dt,
                          int kchunk, cudaStream_t s) {
   const bool mc = P.theta == 2.0;
-  if (stage == 1) return mc ? launch_mc<1, true, TY, MINB>(b, P, dt, kchunk, s)
-                            : launch_mc<1, false, TY, MINB>(b, P, dt, kchunk, s);
-  return mc ? launch_mc<2, true, TY, MINB>(b, P, dt, kchunk, s)
-            : launch_mc<2, false, TY, MINB>(b, P, dt, kchunk, s);
+  if (stage == 1) return mc ? launch_mc<1, true, TXV, TY, MINB>(b, P, dt, kchunk, s)
+                            : launch_mc<1, false, TXV, TY, MINB>(b, P, dt, kchunk, s);
+  return mc ? launch_mc<2, true, TXV, TY, MINB>(b, P, dt, kchunk, s)
+            : launch_mc<2, false, TXV, TY, MINB>(b, P, dt, kchunk, s);
 }
 
 }  // namespace
 
-bool valid_fused_config(int tile_y, int ctas_per_sm) {
-  return (tile_y == 8 && (ctas_per_sm == 1 || ctas_per_sm == 2)) ||
-         ((tile_y == 12 || tile_y == 16) && ctas_per_sm == 1);
+bool valid_fused_config(int tile_x, int tile_y, int ctas_per_sm) {
+  if (tile_x == 16) return tile_y == 16 && (ctas_per_sm == 1 || ctas_per_sm == 2);
+  return tile_x == 32 && ((tile_y == 8 && (ctas_per_sm == 1 || ctas_per_sm == 2)) ||
+                          (tile_y == 16 && ctas_per_sm == 1));
 }
 
 cudaError_t prepare_fused() {
-  cudaError_t e = raise_both<8, 1>();
-  if (e == cudaSuccess) e = raise_both<8, 2>();
-  if (e == cudaSuccess) e = raise_both<12, 1>();
-  if (e == cudaSuccess) e = raise_both<16, 1>();
+  cudaError_t e = raise_both<32, 8, 1>();
+  if (e == cudaSuccess) e = raise_both<32, 8, 2>();
+  if (e == cudaSuccess) e = raise_both<32, 16, 1>();
+  if (e == cudaSuccess) e = raise_both<16, 16, 2>();
+  if (e == cudaSuccess) e = raise_both<16, 16, 1>();
   return e;
 }
 
 cudaError_t launch_fused(int stage, const StepBuffers& b, const Params& P, double dt,
-                         int kchunk, int tile_y, int ctas_per_sm, cudaStream_t s) {
+                         int kchunk, int tile_x, int tile_y, int ctas_per_sm, cudaStream_t s) {
   if (kchunk < 1) kchunk = 1;
-  if (!valid_fused_config(tile_y, ctas_per_sm)) return cudaErrorInvalidValue;
-  if (tile_y == 12) return launch_shape<12, 1>(stage, b, P, dt, kchunk, s);
-  if (tile_y == 16) return launch_shape<16, 1>(stage, b, P, dt, kchunk, s);
-  return ctas_per_sm >= 2 ? launch_shape<8, 2>(stage, b, P, dt, kchunk, s)
-                          : launch_shape<8, 1>(stage, b, P, dt, kchunk, s);
+  if (!valid_fused_config(tile_x, tile_y, ctas_per_sm)) return cudaErrorInvalidValue;
+  if (tile_x == 16)
+    return ctas_per_sm >= 2 ? launch_shape<16, 16, 2>(stage, b, P, dt, kchunk, s)
+                            : launch_shape<16, 16, 1>(stage, b, P, dt, kchunk, s);
+  if (tile_y == 16) return launch_shape<32, 16, 1>(stage, b, P, dt, kchunk, s);
+  return ctas_per_sm >= 2 ? launch_shape<32, 8, 2>(stage, b, P, dt, kchunk, s)
+                          : launch_shape<32, 8, 1>(stage, b, P, dt, kchunk, s);
 }
 
 cudaError_t launch_dt(const double* U, const StepBuffers& b, const Params& P, cudaStream_t s) {

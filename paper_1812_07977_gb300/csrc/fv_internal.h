@@ -77,11 +77,12 @@ FV_DECLARE_STEP_VARIANT(fv_fp64_fma)
 // same contracts as the fused FP64 variants above.
 namespace fv_fp64_ff {
 cudaError_t prepare_fused();
-// tiles of 32 x tile_y columns at ctas_per_sm CTAs per SM: 8 at 2 (16 warps
-// per SM, 128 registers) or 1 (8 warps, 255); 12 or 16 at 1
-bool valid_fused_config(int tile_y, int ctas_per_sm);
+// tiles of tile_x x tile_y columns at ctas_per_sm CTAs per SM: 16 x 16 or
+// 32 x 8 at 2 (16 warps per SM, 128 registers) or 1 (8 warps, 255); 32 x 16
+// at 1
+bool valid_fused_config(int tile_x, int tile_y, int ctas_per_sm);
 cudaError_t launch_fused(int stage, const StepBuffers& b, const fvd::Params& P, double dt,
-                         int kchunk, int tile_y, int ctas_per_sm, cudaStream_t s);
+                         int kchunk, int tile_x, int tile_y, int ctas_per_sm, cudaStream_t s);
 cudaError_t launch_dt(const double* U, const StepBuffers& b, const fvd::Params& P,
                       cudaStream_t s);
 }

@@ -203,24 +203,23 @@ __device__ __forceinline__ void gather_tile(uint4* xs, const TI* __restrict__ in
 // plus its byte offset / 16 (the start-address field is the low 14 bits, and
 // every address here is below 256 KB), so the issuing thread spends one add
 // per operand on each MMA.
+// Planes are issued by UZ threads (lane 0 of warps 0 .. UZ-1, one per SM
+// sub-partition), each committing to the tile's mbarrier (arrival count UZ).
 template <int CI, int CO>
-__device__ __forceinline__ void tile_mmas(uint32_t xa, uint32_t wa, uint32_t acc) {
+__device__ __forceinline__ void plane_mmas(uint32_t xa, uint32_t wa, uint32_t acc, int z) {
   using C = UConv<CI, CO>;
   constexpr uint32_t idesc = umma::idesc_bf16(128, C::NP);
   const uint64_t a0 = umma::desc(xa, UHN * 16, UHX * 16);
   const uint64_t b0 = umma::desc(wa, C::NP * 16, 128);
-#pragma unroll 1
-  for (int z = 0; z < UZ; ++z) {
-    const uint64_t az = a0 + (uint64_t)(z * UHY * UHX);
+  const uint64_t az = a0 + (uint64_t)(z * UHY * UHX);
 #pragma unroll
-    for (int o = 0; o < 27; ++o) {
-      const int dz = o / 9, dy = (o / 3) % 3, dx = o % 3;
+  for (int o = 0; o < 27; ++o) {
+    const int dz = o / 9, dy = (o / 3) % 3, dx = o % 3;
 #pragma unroll
-      for (int kk = 0; kk < C::CIP / 16; ++kk) {
-        const uint64_t a = az + (uint64_t)((2 * kk) * UHN + (dz * UHY + dy) * UHX + dx);
-        const uint64_t b = b0 + (uint64_t)((o * C::KC + 2 * kk) * C::NP);
-        umma::mma_bf16(acc + z * C::NP, a, b, idesc, (o > 0 || kk > 0) ? 1u : 0u);
-      }
+    for (int kk = 0; kk < C::CIP / 16; ++kk) {
+      const uint64_t a = az + (uint64_t)((2 * kk) * UHN + (dz * UHY + dy) * UHX + dx);
+      const uint64_t b = b0 + (uint64_t)((o * C::KC + 2 * kk) * C::NP);
+      umma::mma_bf16(acc + z * C::NP, a, b, idesc, (o > 0 || kk > 0) ? 1u : 0u);
     }
   }
 }
@@ -247,8 +246,8 @@ k_conv_umma(const TI* __restrict__ in, const uint4* __restrict__ wl,
   gather_tile<CI, C::KC, TI, ICL>(xs[0], in, g, x0, y0, z0);
   cp_async_wait_all();
   if (tid == 0) {
-    umma::mbar_init(&mbar[0], 1);
-    umma::mbar_init(&mbar[1], 1);
+    umma::mbar_init(&mbar[0], UZ);
+    umma::mbar_init(&mbar[1], UZ);
   }
   if (warp == 0) umma::tmem_alloc(&tmem_slot, C::tmem_cols);
   umma::fence_smem_for_mma();
@@ -258,8 +257,9 @@ k_conv_umma(const TI* __restrict__ in, const uint4* __restrict__ wl,
   const uint32_t tmem = tmem_slot;
   const uint32_t wa = umma::smem_addr(ws);
   const uint32_t xa[2] = {umma::smem_addr(xs[0]), umma::smem_addr(xs[1])};
-  if (tid == 0) {
-    tile_mmas<CI, CO>(xa[0], wa, tmem);
+  const bool issuer = lane == 0 && warp < UZ;
+  if (issuer) {
+    plane_mmas<CI, CO>(xa[0], wa, tmem, warp);
     umma::commit(&mbar[0]);
   }
   // the epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (accumulator row m = cell
@@ -289,8 +289,8 @@ k_conv_umma(const TI* __restrict__ in, const uint4* __restrict__ wl,
       umma::mbar_wait(&mbar[b], (uint32_t)((i >> 1) & 1), kMmaPolls);
       break;
     }
-    if (tid == 0 && tn < ntiles) {
-      tile_mmas<CI, CO>(xa[b ^ 1], wa, tmem + (uint32_t)(b ^ 1) * C::acc_cols);
+    if (issuer && tn < ntiles) {
+      plane_mmas<CI, CO>(xa[b ^ 1], wa, tmem + (uint32_t)(b ^ 1) * C::acc_cols, warp);
       umma::commit(&mbar[b ^ 1]);
     }
     const uint32_t acc = tmem + (uint32_t)b * C::acc_cols + ((uint32_t)(quarter * 32) << 16);
@@ -457,7 +457,8 @@ k_wgrad_umma(const TI* __restrict__ in, const float* __restrict__ gout,
     }
   }
   cp_async_wait_all();
-  if (tid == 0) umma::mbar_init(&mbar, 1);
+  constexpr int kIssuers = 4;   // lane 0 of warps 0 .. 3 issue the offsets o0 + w, + 4, ...
+  if (tid == 0) umma::mbar_init(&mbar, kIssuers);
   if (warp == 0) umma::tmem_alloc(&tmem_slot, 512);
   umma::fence_smem_for_mma();
   umma::fence_before_sync();
@@ -470,12 +471,12 @@ k_wgrad_umma(const TI* __restrict__ in, const float* __restrict__ gout,
   int issued = 0;   // passes whose MMAs were issued
   for (int pass = 0; pass < C::NPASS; ++pass) {
     const int o0 = pass * C::OPP, o1 = min(27, o0 + C::OPP);
-    if (tid == 0) {
-      // base descriptors plus byte offsets / 16 (see tile_mmas)
+    if (lane == 0 && warp < kIssuers) {
+      // base descriptors plus byte offsets / 16 (see plane_mmas)
       const uint64_t a0 = umma::desc(umma::smem_addr(gs), 128, C::TC * 16);
       const uint64_t b0 = umma::desc(umma::smem_addr(xs), UHX * 16, UHN * 16);
 #pragma unroll 1
-      for (int o = o0; o < o1; ++o) {
+      for (int o = o0 + warp; o < o1; o += kIssuers) {
         const int dz = o / 9, dy = (o / 3) % 3, dx = o % 3;
         const uint64_t bo = b0 + (uint64_t)((dz * UHY + dy) * UHX + dx);
         const uint32_t d = tmem + (uint32_t)((o - o0) * C::NPC);
@@ -565,15 +566,40 @@ k_wgrad_reduce(const float* __restrict__ partial, int ntiles, float* __restrict_
   }
 }
 
-// acc += (sum of the loss kernel's block partials, in block order) / denom:
-// the value a synchronous step reports, added to the running sum.
-__global__ void k_loss_accumulate(const double* __restrict__ partial, int n, double denom,
-                                  double* __restrict__ acc) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+// The loss from the loss kernel's N block partials, in a fixed order that
+// the host (loss_from_partials) and the device (k_loss_accumulate) share: 32
+// runs of N / 32 consecutive partials, each summed in order, then the 32 run
+// sums in order.
+constexpr int kLossRuns = 32;
+
+// acc += loss / denom: the value a synchronous step reports, added to the
+// running sum; one warp, lane l summing run l.
+template <int N>
+__global__ void __launch_bounds__(32)
+k_loss_accumulate(const double* __restrict__ partial, double denom, double* __restrict__ acc) {
+  static_assert(N % kLossRuns == 0, "runs");
+  constexpr int R = N / kLossRuns;
+  __shared__ double run[kLossRuns];
+  double t = 0.0;
+  for (int j = 0; j < R; ++j) t += partial[threadIdx.x * R + j];
+  run[threadIdx.x] = t;
+  __syncwarp();
+  if (threadIdx.x == 0) {
     double L = 0.0;
-    for (int b = 0; b < n; ++b) L += partial[b];
+    for (int l = 0; l < kLossRuns; ++l) L += run[l];
     *acc += L / denom;
   }
+}
+
+double loss_from_partials(const double* p, int n) {
+  const int R = n / kLossRuns;
+  double L = 0.0;
+  for (int l = 0; l < kLossRuns; ++l) {
+    double t = 0.0;
+    for (int j = 0; j < R; ++j) t += p[l * R + j];
+    L += t;
+  }
+  return L;
 }
 
 // Weights of the adjoint convolution: wt[ci][co][26 - o] = w[co][ci][o].
@@ -1118,8 +1144,8 @@ fv_status fv_net_train_step(fv_net_t n, fv_mesh_t m, const double* residual, dou
   }
   if (e == cudaSuccess && !loss_out) {
     // asynchronous step: the loss joins the device sum (fv_net_take_loss)
-    k_loss_accumulate<<<1, 32, 0, s>>>(n->loss_partial, kLossBlocks, 5.0 * (double)g.n,
-                                       n->loss_acc);
+    k_loss_accumulate<kLossBlocks><<<1, kLossRuns, 0, s>>>(n->loss_partial, 5.0 * (double)g.n,
+                                                           n->loss_acc);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "network training step");
     n->acc_steps += 1;
@@ -1136,9 +1162,7 @@ fv_status fv_net_train_step(fv_net_t n, fv_mesh_t m, const double* residual, dou
   n->have_grads = true;
   if ((st = take_status(n, s)) != FV_OK) return st;
   if (loss_out) {
-    double L = 0.0;
-    for (int b = 0; b < kLossBlocks; ++b) L += n->host_loss[b];
-    *loss_out = L / (5.0 * (double)g.n);
+    *loss_out = loss_from_partials(n->host_loss, kLossBlocks) / (5.0 * (double)g.n);
   }
   return FV_OK;
 }

@@ -94,11 +94,17 @@ __device__ __forceinline__ void halo_cell(int h, int& row, int& col) {
 // window) and the halo cells of plane k, each copied by the thread that uses
 // it, so a slot is reused without a barrier.
 constexpr int kStageDepth = FV32_STAGE_DEPTH;
+// FV32_EQ_SKIP (default 1): a cell whose FP64 input equals the previous
+// plane's keeps its primitives, decided per warp; the next plane is then
+// staged after this plane's input has been compared with the previous one
+// (two slots).  On the 256^3 oblique problem 8% faster, on a state with no
+// equal neighbours 3% slower (the compares, and the later staging).
 #ifndef FV32_EQ_SKIP
-#define FV32_EQ_SKIP 0
+#define FV32_EQ_SKIP 1
 #endif
 static_assert(!FV32_EQ_SKIP || FV32_STAGE_DEPTH == 1, "the equal-state skip stages one plane ahead");
 constexpr int kRing = kStageDepth + 1;
+constexpr bool kLateStage = FV32_EQ_SKIP != 0;
 
 template <class S>
 struct Smem {
@@ -309,15 +315,16 @@ __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
   for (int k = k0; k < k1; ++k) {
     if (owner && !physical(w0)) ++bad;   // each interior cell once per substep
     if (NEXT && STAGE == 2) refresh_max(gmax, smax_next, smax_next_f);
-#if FV32_EQ_SKIP
-    // the next plane is staged after this plane's input has been compared
-    // with the previous plane's (still in the other slot)
-    cp_async_wait<0>();
-#else
-    stage_in(k + kStageDepth);
-    cp_async_wait<kStageDepth>();        // this iteration's group has landed
-#endif
+    if (kLateStage) {
+      // the next plane is staged after this plane's input has been compared
+      // with the previous plane's (still in the other slot)
+      cp_async_wait<0>();
+    } else {
+      stage_in(k + kStageDepth);
+      cp_async_wait<kStageDepth>();      // this iteration's group has landed
+    }
     const int slot = k % kRing;
+    const int pslot = (k + kRing - 1) % kRing;   // the previous plane's input
     double cur_col[NF];
 #pragma unroll
     for (int q = 0; q < NF; ++q) cur_col[q] = s.col[slot][q][tid];
@@ -342,7 +349,7 @@ __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
     bool eqc = k > k0;
 #pragma unroll
     for (int q = 0; q < NF; ++q)
-      eqc = eqc && fvd::bits(cur_col[q]) == fvd::bits(s.col[(k + 1) % kRing][q][tid]);
+      eqc = eqc && fvd::bits(cur_col[q]) == fvd::bits(s.col[pslot][q][tid]);
     const Prim32 w2 = __all_sync(0xffffffffu, eqc) ? w1 : prim_from_state(cur_col, Q);
 #else
     const Prim32 w2 = prim_from_state(cur_col, Q);
@@ -384,7 +391,7 @@ __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
 #pragma unroll
       for (int q = 0; q < NF; ++q) {
         uh[q] = h < kHalo ? s.halo[slot][q][h] : 0.0;
-        eqh = eqh && (h >= kHalo || fvd::bits(uh[q]) == fvd::bits(s.halo[(k + 1) % kRing][q][h]));
+        eqh = eqh && (h >= kHalo || fvd::bits(uh[q]) == fvd::bits(s.halo[pslot][q][h]));
       }
       const bool all_eq = __all_sync(0xffffffffu, eqh);
       if (h < kHalo) {
@@ -402,9 +409,7 @@ __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
       }
 #endif
     }
-#if FV32_EQ_SKIP
-    stage_in(k + 1);   // into the other slot, now compared
-#endif
+    if (kLateStage) stage_in(k + 1);   // into the other slot, now compared
     __syncthreads();
     // (c) x faces: face fi (between columns fi-1 and fi) of row r.  A face
     // whose four cells all equal the previous plane's has that plane's

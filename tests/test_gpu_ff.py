@@ -182,16 +182,20 @@ def test_ff_operand_range_is_guarded():
 
 def test_ff_launch_settings_same_bits():
     """The float-float kernel built for one or two CTAs per SM, with tiles of
-    8, 12 or 16 rows and z chunks of several sizes, computes the same
-    operations: the same bits (45 x 29 x 30: ragged tiles of every height)."""
+    32 x 8, 12 or 16 and 16 x 16 columns and z chunks of several sizes,
+    computes the same operations: the same bits (45 x 29 x 30: ragged tiles
+    of every shape)."""
     n = (45, 29, 30)
     U0 = problems.riemann_oblique(*n)
     out = []
-    for occ, ty, kc in ((2, 8, 64), (1, 8, 64), (2, 8, 7), (1, 8, 1), (1, 12, 64),
-                        (1, 16, 5)):
+    for occ, ty, tx, kc in ((2, 16, 16, 64), (1, 16, 16, 64), (2, 16, 16, 7), (2, 8, 32, 64),
+                            (1, 8, 32, 1), (2, 8, 32, 9), (1, 16, 32, 5)):
         m = _mesh(n)
-        m.set_tuning("occupancy", occ)
+        # through built shapes only: occupancy 1, the width, the height
+        m.set_tuning("occupancy", 1)
+        m.set_tuning("tile_x", tx)
         m.set_tuning("tile_y", ty)
+        m.set_tuning("occupancy", occ)
         m.set_tuning("kchunk", kc)
         m.set_state(U0)
         for _ in range(3):
@@ -203,17 +207,22 @@ def test_ff_launch_settings_same_bits():
         assert ct == out[0][1]
 
 
-def test_ff_tile_height_needs_occupancy_one():
-    """Tiles of 12 or 16 rows exist only at one CTA per SM: the other orders
-    of setting them are rejected and leave the mesh as it was."""
+def test_ff_tile_changes_must_stay_built():
+    """Shape changes that would leave the built (tile x, tile y, CTAs per SM)
+    are rejected and leave the mesh as it was: from the default 16 x 16 at 2
+    CTAs per SM, 32 x 16 exists only at one CTA per SM."""
     from paper_1812_07977_gb300.fv import FvError
     m = _mesh((16, 16, 16))
     with pytest.raises(FvError):
-        m.set_tuning("tile_y", 12)      # occupancy is 2
+        m.set_tuning("tile_x", 32)      # (32, 16, 2) is not built
+    with pytest.raises(FvError):
+        m.set_tuning("tile_y", 8)       # (16, 8, 2) is not built
     m.set_tuning("occupancy", 1)
-    m.set_tuning("tile_y", 16)
+    m.set_tuning("tile_x", 32)
     with pytest.raises(FvError):
-        m.set_tuning("occupancy", 2)    # tile height is 16
+        m.set_tuning("occupancy", 2)    # (32, 16, 2)
     with pytest.raises(FvError):
-        m.set_tuning("tile_y", 4)
+        m.set_tuning("tile_y", 12)
+    m.set_tuning("tile_y", 8)
+    m.set_tuning("occupancy", 2)
     m.close()
