@@ -400,8 +400,9 @@ def run_shear(args, dev):
     """512^3 periodic shear layer (rho 2/1, vx +-0.5, p 2.5, gamma 5/3, an
     8-mode seeded perturbation of amplitude 0.01 on vy and vz): the FP32-bulk
     fused step replayed from a CUDA graph (a batch of one mesh) versus the
-    FP64 step, `shear_steps` steps each on the same dt sequence (the FP64
-    run's CFL steps), with the mass and energy drift of each."""
+    FP64-class step of --precision (held to the FP64 oracle), `shear_steps`
+    steps each with its own CFL time steps, with the mass and energy drift of
+    each."""
     import torch
 
     from paper_1812_07977_gb300 import problems
@@ -440,13 +441,13 @@ def run_shear(args, dev):
     m64.close()
     scale = [float(v) for v in U0.abs().reshape(5, -1).sum(1) / U0[0].numel()]
     return {"cells": n ** 3, "steps": K,
-            "fp64": {"ms_per_step": ms64, "value": n ** 3 / (ms64 / 1e3),
+            args.precision: {"ms_per_step": ms64, "value": n ** 3 / (ms64 / 1e3),
                      "mass_drift": abs(s64[0] - s0[0]) / scale[0],
                      "energy_drift": abs(s64[4] - s0[4]) / scale[4]},
             "fp32_graph": {"ms_per_step": ms32, "value": n ** 3 / (ms32 / 1e3),
                            "mass_drift": abs(s32[0] - s0[0]) / scale[0],
                            "energy_drift": abs(s32[4] - s0[4]) / scale[4]},
-            "rho_l1_rel_fp32_vs_fp64": drho,
+            "rho_l1_rel_fp32_vs_" + args.precision: drho,
             "note": "drifts relative to the mean |U| per cell; the FP32 run takes its own "
                     "CFL steps, so the two end times agree to the dt difference"}
 
