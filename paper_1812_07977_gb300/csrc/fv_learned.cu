@@ -702,14 +702,32 @@ k_loss(const float* __restrict__ o, const double* __restrict__ r, const float* _
 // dL/do = out_scale * C^T(g); the periodic stencil is symmetric, C^T = C.
 __global__ void __launch_bounds__(256)
 k_loss_adjoint(const float* __restrict__ gdu, const float* __restrict__ scales, Grid3 g,
-               float dt, float ix, float iy, float iz, float* __restrict__ go) {
+               float dt, float ix, float iy, float iz, float* __restrict__ go,
+               bf16* __restrict__ gob) {
   const float inv[3] = {ix, iy, iz};
   const long long total = 5 * g.n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     int q, i, j, k;
     split_index(t, g, q, i, j, k);
-    go[t] = correction(gdu, scales[q], q, i, j, k, g, dt, inv);
+    const float v = correction(gdu, scales[q], q, i, j, k, g, dt, inv);
+    go[t] = v;
+    // the BF16 channel-last copy the adjoint convolution reads ([cell][8],
+    // pads zero from allocation): the value its gather would round to
+    gob[(t - (long long)q * g.n) * pitch8<5>() + q] = to_bf(v);
+  }
+}
+
+// g *= 1 - h^2 (tanh backward), h the layer's BF16 output; gb (if given):
+// the result rounded to BF16 in the same layout, for the next convolution
+__global__ void k_tanh_bwd_bf(float* __restrict__ g, const bf16* __restrict__ h,
+                              bf16* __restrict__ gb, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const float y = __bfloat162float(h[t]);
+    const float v = g[t] * (1.0f - y * y);
+    g[t] = v;
+    gb[t] = to_bf(v);
   }
 }
 
@@ -795,6 +813,7 @@ struct fv_net_s {
   long long cap = 0, cap_tiles = 0;
   bf16 *x = nullptr, *h1 = nullptr, *h2 = nullptr;
   float *o = nullptr, *gdu = nullptr, *go = nullptr, *g2 = nullptr, *g1 = nullptr;
+  bf16 *gob = nullptr, *g2b = nullptr;   // BF16 channel-last copies for the adjoint convs
   float* partial = nullptr;
   double* loss_partial = nullptr;
   double* host_loss = nullptr;
@@ -839,9 +858,12 @@ void free_act(fv_net_s* n) {
   cudaFree(n->go);
   cudaFree(n->g2);
   cudaFree(n->g1);
+  cudaFree(n->gob);
+  cudaFree(n->g2b);
   cudaFree(n->partial);
   n->x = n->h1 = n->h2 = nullptr;
   n->o = n->gdu = n->go = n->g2 = n->g1 = n->partial = nullptr;
+  n->gob = n->g2b = nullptr;
 }
 
 void free_net(fv_net_s* n) {
@@ -884,6 +906,9 @@ fv_status ensure_capacity(fv_net_s* n, const Grid3& g) {
       (e = cudaMalloc(&n->go, COUT * cc * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&n->g2, CH * cc * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&n->g1, CH * cc * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&n->gob, pitch8<COUT>() * cc * sizeof(bf16))) != cudaSuccess ||
+      (e = cudaMemset(n->gob, 0, pitch8<COUT>() * cc * sizeof(bf16))) != cudaSuccess ||
+      (e = cudaMalloc(&n->g2b, CH * cc * sizeof(bf16))) != cudaSuccess ||
       (e = cudaMalloc(&n->partial, tt * (CH * 27 + 1) * CH * sizeof(float))) != cudaSuccess) {
     cudaGetLastError();
     free_act(n);
@@ -1111,23 +1136,24 @@ fv_status fv_net_train_step(fv_net_t n, fv_mesh_t m, const double* residual, dou
               iz = (float)v.P.inv_d[2];
   k_loss<<<kLossBlocks, 256, 0, s>>>(n->o, residual, n->scales, g, fdt, ix, iy, iz, n->gdu,
                                      n->loss_partial);
-  k_loss_adjoint<<<grid_for(5 * g.n), 256, 0, s>>>(n->gdu, n->scales, g, fdt, ix, iy, iz, n->go);
+  k_loss_adjoint<<<grid_for(5 * g.n), 256, 0, s>>>(n->gdu, n->scales, g, fdt, ix, iy, iz, n->go,
+                                                   n->gob);
   cudaError_t e = cudaGetLastError();
   // layer 3: o = conv(h2; w3, b3)
   if (e == cudaSuccess)
     e = conv_wgrad<CH, COUT, bf16, true, false>(n->h2, n->go, n->partial, n->grads, OW3, OB3, g, n->status, s);
   if (e == cudaSuccess) {
     k_flip_weights<<<(COUT * CH * 27 + 255) / 256, 256, 0, s>>>(n->wb + OW3, n->wt3, COUT, CH);
-    e = conv_fwd<COUT, CH, float, float, false, false, true>(n->go, n->wt3, nullptr, n->g2, g, n->wlay,
+    e = conv_fwd<COUT, CH, bf16, float, false, true, true>(n->gob, n->wt3, nullptr, n->g2, g, n->wlay,
                                                 n->status, s);
   }
   if (e == cudaSuccess) {
-    k_tanh_bwd<<<grid_for(CH * g.n), 256, 0, s>>>(n->g2, n->h2, CH * g.n);
+    k_tanh_bwd_bf<<<grid_for(CH * g.n), 256, 0, s>>>(n->g2, n->h2, n->g2b, CH * g.n);
     e = conv_wgrad<CH, CH, bf16, true, true>(n->h1, n->g2, n->partial, n->grads, OW2, OB2, g, n->status, s);
   }
   if (e == cudaSuccess) {
     k_flip_weights<<<(CH * CH * 27 + 255) / 256, 256, 0, s>>>(n->wb + OW2, n->wt2, CH, CH);
-    e = conv_fwd<CH, CH, float, float, false, true, true>(n->g2, n->wt2, nullptr, n->g1, g, n->wlay,
+    e = conv_fwd<CH, CH, bf16, float, false, true, true>(n->g2b, n->wt2, nullptr, n->g1, g, n->wlay,
                                               n->status, s);
   }
   if (e == cudaSuccess) {
