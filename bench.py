@@ -661,6 +661,12 @@ def run_ours(args):
                          "note": "whole step vs the algorithmic minimum traffic, of measured"},
         "kernel_ms_per_step": {c: v[0] / args.steps for c, v in prof.items()},
         "variants": variants,
+        # the same precision with every face evaluated (nothing to reuse): the
+        # kernels' rate without the workload's uniform regions
+        "every_face_evaluated": ({k: variants[args.precision + "_no_reuse"].get(k)
+                                  for k in ("value", "unit", "ms_per_step", "steps",
+                                            "faces_evaluated_fraction", "workload")}
+                                 if args.precision + "_no_reuse" in variants else None),
         "gpu_launches": launches,
         "fp64_probe": probe,
         "e2e": e2e,

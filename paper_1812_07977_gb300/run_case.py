@@ -12,6 +12,8 @@ STATE      oblique  -- the oblique Sod problem (plane normal (1,1,1)/sqrt 3,
                        faces reuse their neighbour's flux
            smooth   -- a seeded random smooth periodic state: no two
                        neighbours equal, every face evaluated
+           uniform  -- the Sod left state everywhere (outflow): every face
+                       reuses its neighbour's flux, the per-cell floor
 STEPS      RK2 steps, each with its CFL time step (Courant number 0.4), timed
            with CUDA events on the mesh's stream
 FUSED      for fp64 / fp64_fma: 1 = the fused per-tile substep kernel,
@@ -36,7 +38,7 @@ def main(argv=None) -> int:
     ap = argparse.ArgumentParser(usage=__doc__)
     ap.add_argument("precision")
     ap.add_argument("n", type=int)
-    ap.add_argument("state", choices=["oblique", "smooth"])
+    ap.add_argument("state", choices=["oblique", "smooth", "uniform"])
     ap.add_argument("steps", type=int)
     ap.add_argument("fused", type=int, nargs="?", default=1)
     ap.add_argument("--warmup", type=int, default=0)
@@ -47,6 +49,9 @@ def main(argv=None) -> int:
     if a.state == "smooth":
         U0 = problems.random_smooth_periodic(n, n, n, seed=12345)
         bc = ("periodic",) * 3
+    elif a.state == "uniform":
+        U0 = problems.uniform(n, n, n, 1.0, (0.0, 0.0, 0.0), 1.0)
+        bc = ("outflow",) * 3
     else:
         U0 = problems.riemann_oblique(n, n, n)
         bc = ("outflow",) * 3
