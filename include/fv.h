@@ -432,7 +432,10 @@ FV_API fv_status fv_conserved_sums_noalloc(const double* U, int nx, int ny, int 
 /* Tuning knobs (not part of the paper).
  *  FV_TUNE_KCHUNK        z planes per CTA of the fused kernels (FP32-bulk
  *                        and FP64; integer >= 1; default 32, or nz when
- *                        nz < 64; 64 for FP64_FF meshes with nz >= 128)
+ *                        nz < 64).  FP64_FF meshes by default pick it per
+ *                        launch shape: the chunk (>= 16 planes, or nz) that
+ *                        minimises rounds of resident CTAs x (chunk + 4)
+ *                        (37 at 256^3); setting the key fixes it
  *  FV_TUNE_VACUUM_RATIO  FP32-bulk: recover the pressure in FP64 where the
  *                        kinetic energy exceeds this fraction of E (default
  *                        0.99; a value > 1 turns the recovery off)

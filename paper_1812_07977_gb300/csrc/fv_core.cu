@@ -255,6 +255,33 @@ long long faces_normal_to(const fvd::Params& P, int axis) {
   return axis == 0 ? (nx + 1) * ny * nz : axis == 1 ? nx * (ny + 1) * nz : nx * ny * (nz + 1);
 }
 
+// The float-float kernel's z chunk: each CTA marches over `chunk` planes after
+// a 4-plane window prologue, and the launch runs in rounds of (SMs x CTAs per
+// SM) resident CTAs, so its time is about rounds x (chunk + 4) plane steps.
+// The chunk (16 planes at least, or the whole column) minimising that: at
+// 256^3 with 16 x 16 tiles at 2 CTAs per SM, 7 chunks of 37 planes (5.9
+// rounds) against 4 of 64 (3.4 rounds, the last one a third full): 5.93 ->
+// 5.68 ms per step over the 200-step oblique workload (same bits; chunks do
+// not change the arithmetic).
+int ff_auto_kchunk(const fvd::Params& P, int tile_x, int tile_y, int ctas_per_sm) {
+  const long long tiles = (long long)((P.nx + tile_x - 1) / tile_x) * ((P.ny + tile_y - 1) / tile_y);
+  const long long resident = (long long)fv_sm_count() * ctas_per_sm;
+  int best = P.nz;
+  long long best_cost = -1;
+  for (int n = 1; n <= P.nz; ++n) {
+    const int chunk = (P.nz + n - 1) / n;
+    if (n > 1 && chunk < 16) break;
+    if (n > 1 && (P.nz + chunk - 1) / chunk != n) continue;   // the same chunk as a smaller n
+    const long long rounds = (tiles * n + resident - 1) / resident;
+    const long long cost = rounds * (chunk + 4);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = chunk;
+    }
+  }
+  return best;
+}
+
 cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
   for (int axis = 0; axis < 3; ++axis) m->faces_defined += faces_normal_to(m->P, axis);
   const bool fma = m->desc.precision == FV_PREC_FP64_FMA;
@@ -269,7 +296,12 @@ cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
     if (e == cudaSuccess)
       e = timed(m, FV_KERNEL_FUSED, 1, [&] {
         if (ff)
-          return fv_fp64_ff::launch_fused(stage, m->buf, m->P, dt, m->kchunk, m->ff_tile_x,
+          return fv_fp64_ff::launch_fused(stage, m->buf, m->P, dt,
+                                          m->kchunk > 0 ? m->kchunk
+                                                        : ff_auto_kchunk(m->P, m->ff_tile_x,
+                                                                         m->ff_tile_y,
+                                                                         m->ff_ctas_per_sm),
+                                          m->ff_tile_x,
                                           m->ff_tile_y, m->ff_ctas_per_sm, m->stream);
         return fma ? fv_fp64_fma::launch_fused(stage, m->buf, m->P, dt, m->kchunk, m->stream)
                    : fv_fp64_exact::launch_fused(stage, m->buf, m->P, dt, m->kchunk,
@@ -345,10 +377,10 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   m->stream = (cudaStream_t)cuda_stream;
   m->stage_pending = 0;
   m->prof_on = false;
-  // z planes per CTA of the fused kernels: the float-float kernel measured
-  // fastest with 64 on the 256^3 workloads, the FP32-bulk one with 32
-  m->kchunk = desc->precision == FV_PREC_FP64_FF && desc->nz >= 128 ? 64
-              : desc->nz >= 64 ? 32 : desc->nz;
+  // z planes per CTA of the fused kernels: the FP32-bulk one measured
+  // fastest with 32 at 256^3; the float-float one picks its chunk per launch
+  // shape (0: ff_auto_kchunk) unless FV_TUNE_KCHUNK sets one
+  m->kchunk = desc->precision == FV_PREC_FP64_FF ? 0 : desc->nz >= 64 ? 32 : desc->nz;
   m->vacuum_ratio = 0.99;
   m->occupancy = 2;
   m->tile_x = 16;   // 16 x 8: per-warp reuse decisions over 16 x 2 cells
