@@ -476,6 +476,15 @@ FV_API fv_status fv_conserved_sums_noalloc(const double* U, int nx, int ny, int 
  *                        FP64 pipe decides, and the sweeps are faster).
  *                        Both give the same bits.  Not between the two
  *                        substeps.  FP64_FF always runs fused.
+ *  FV_TUNE_PLANE_SKIP    FP64_FF and FP32-bulk fused kernels: 1 (default)
+ *                        lets a tile skip the x / y slope and face passes of
+ *                        a plane (and two of its barriers) when every cell of
+ *                        the tile and its two-cell halo equals, bit for bit,
+ *                        the cell one plane below: each of those slopes and
+ *                        fluxes would keep its previous value, and the
+ *                        float-float update's zero-divergence test carries
+ *                        over.  0 runs every pass.  The same bits and face
+ *                        counts either way.
  * Errors: INVALID_ARG for an unknown key or a value out of range. */
 typedef enum {
   FV_TUNE_KCHUNK = 0,
@@ -484,7 +493,8 @@ typedef enum {
   FV_TUNE_SWEEP_SEGMENTS = 3,
   FV_TUNE_TILE_Y = 4,
   FV_TUNE_FP64_FUSED = 5,
-  FV_TUNE_TILE_X = 6
+  FV_TUNE_TILE_X = 6,
+  FV_TUNE_PLANE_SKIP = 7
 } fv_tuning_key;
 FV_API fv_status fv_set_tuning(fv_mesh_t m, int key, double value);
 

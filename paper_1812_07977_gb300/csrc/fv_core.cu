@@ -65,6 +65,7 @@ struct fv_mesh_s {
   bool fused64;             // FP64: one fused kernel per substep (else the per-axis sweeps)
   int ff_ctas_per_sm;       // FP64_FF: CTAs per SM its fused kernel is built for (1 or 2)
   int ff_tile_x, ff_tile_y; // FP64_FF: tile of its fused kernel (16 x 16; 32 x 8, 16)
+  bool plane_skip;          // fused FP64_FF / FP32-bulk: skip the passes of unchanged planes
   bool w_current;           // FP64 sweeps: W holds the primitives of U (from the dt pass)
   bool smax_current;        // fused paths: ctr->smax_next is the CFL maximum of U
   // profiling
@@ -302,7 +303,8 @@ cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
                                                                          m->ff_tile_y,
                                                                          m->ff_ctas_per_sm),
                                           m->ff_tile_x,
-                                          m->ff_tile_y, m->ff_ctas_per_sm, m->stream);
+                                          m->ff_tile_y, m->ff_ctas_per_sm, m->plane_skip,
+                                          m->stream);
         return fma ? fv_fp64_fma::launch_fused(stage, m->buf, m->P, dt, m->kchunk, m->stream)
                    : fv_fp64_exact::launch_fused(stage, m->buf, m->P, dt, m->kchunk,
                                                  m->stream);
@@ -322,7 +324,8 @@ cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
     if (e == cudaSuccess)
       e = timed(m, FV_KERNEL_FUSED, 1, [&] {
         return fv_fp32::launch_stage(stage, m->buf, m->P, dt, m->kchunk, m->vacuum_ratio,
-                                     m->occupancy, m->tile_x, m->tile_y, m->stream);
+                                     m->occupancy, m->tile_x, m->tile_y, m->plane_skip,
+                                     m->stream);
       });
     if (e != cudaSuccess) return e;
     double* dst = stage == 1 ? m->buf.U1 : m->buf.U;
@@ -390,6 +393,7 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   m->ff_ctas_per_sm = 2;
   m->ff_tile_x = 16;   // 16 x 16 at 2 CTAs per SM (see fv_fused_ff_kernels.cu)
   m->ff_tile_y = 16;
+  m->plane_skip = true;
   m->w_current = false;
   m->smax_current = false;
   for (int c = 0; c < FV_KERNEL_NCLASS; ++c) m->launches[c] = 0;
@@ -740,6 +744,14 @@ fv_status fv_set_tuning(fv_mesh_t m, int key, double value) {
       return FV_ERR_INVALID_ARG;
     }
     m->segments = (int)value;
+    return FV_OK;
+  }
+  if (key == FV_TUNE_PLANE_SKIP) {
+    if (value != 0.0 && value != 1.0) {
+      set_error("FV_TUNE_PLANE_SKIP must be 0 or 1 (got %g)", value);
+      return FV_ERR_INVALID_ARG;
+    }
+    m->plane_skip = value != 0.0;
     return FV_OK;
   }
   set_error("unknown tuning key %d", key);

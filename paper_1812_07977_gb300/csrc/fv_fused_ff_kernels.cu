@@ -113,7 +113,7 @@ __device__ __forceinline__ void stageff_tile(SmemFF<S>& s, double* __restrict__ 
                                              unsigned long long& range_out, unsigned& evaluated,
                                              double& smax, float& smax_f,
                                              unsigned long long& bad_next,
-                                             unsigned long long* gmax) {
+                                             unsigned long long* gmax, bool plane_skip) {
   const double* __restrict__ src = STAGE == 1 ? U : U1;
   constexpr int kThreads = S::kThreads, kHalo = S::kHalo, kHaloPer = S::kHaloPer;
   constexpr int TY = S::TY;
@@ -150,6 +150,10 @@ __device__ __forceinline__ void stageff_tile(SmemFF<S>& s, double* __restrict__ 
   unsigned fallbacks = 0, xyfb = 0;
   unsigned long long bad = 0, range = 0;
   unsigned last_bad = 0;   // stage 2: whether the column's last cell written was non-physical
+  // the x / y part of the last update's zero-divergence test (every x and y
+  // flux difference of the column's cell zero and finite); a skipped plane
+  // (below) has the same x and y fluxes, so the part carries over
+  bool zxy_prev = false;
 
   // z window prologue: planes k0-2 .. k0+1 of the column; per plane whether
   // its cell is physical and inside the float-float range (counted at k)
@@ -265,9 +269,12 @@ __device__ __forceinline__ void stageff_tile(SmemFF<S>& s, double* __restrict__ 
 #pragma unroll
       for (int q = 0; q < NF; ++q) prefetch_l2(pu + q * nf);
     }
-    // (d) the plane's primitives into shared memory
-    smem_w_store(s, tj + 2, ti + 2, w0);
-    s.same[tj + 2][ti + 2] = later && same0;
+    // (d) the plane's primitives into shared memory (a cell equal to the one a
+    // plane below is there already, bit for bit)
+    const bool col_same = later && same0;
+    if (!col_same) smem_w_store(s, tj + 2, ti + 2, w0);
+    s.same[tj + 2][ti + 2] = col_same;
+    bool plane_same = col_same;
 #pragma unroll
     for (int e = 0; e < kHaloPer; ++e) {
       const int h = tid + e * kThreads;
@@ -278,9 +285,16 @@ __device__ __forceinline__ void stageff_tile(SmemFF<S>& s, double* __restrict__ 
           smem_w_store(s, hrow[e] + 2, hcol[e] + 2, prim_ff(uh[e], P, ph, ok));
         }
         s.same[hrow[e] + 2][hcol[e] + 2] = eqh[e];
+        plane_same = plane_same && eqh[e];
       }
     }
-    __syncthreads();
+    // every cell of the tile and its halo equals the cell a plane below: each
+    // slope and x / y face of this plane would keep its value (the passes
+    // below would only read flags), so the CTA skips them and their barriers
+    const bool skip = __syncthreads_and(plane_skip && plane_same) != 0;
+    if (skip) {
+      fallbacks += __popc(xyfb & counted & ((1u << S::kFacePer) - 1u));
+    } else {
     // (e) half slopes along x and y
 #pragma unroll 1
     for (int p = 0; p < S::kSlopePer; ++p) {
@@ -356,19 +370,26 @@ __device__ __forceinline__ void stageff_tile(SmemFF<S>& s, double* __restrict__ 
       fallbacks += (xyfb >> p) & (counted >> p) & 1u;
     }
     __syncthreads();
+    }
     // (g) update: float-float divergence, the RK combine in FP64 on the FP64
     // state (a copy / half sum where every flux difference is zero)
     if (owner) {
       // first the zero test over all components, then the arithmetic one
       // component at a time (few values live at once)
-      bool zero = true;
+      bool zxy = zxy_prev, zz = true;
+      if (!skip) {
+        zxy = true;
 #pragma unroll
-      for (int q = 0; q < NF; ++q) {
-        const ff xr = s.fx[q][tj][ti + 1], yr = s.fy[q][tj + 1][ti];
-        zero = zero && same_ff(s.fx[q][tj][ti], xr) && same_ff(s.fy[q][tj][ti], yr) &&
-               same_ff(fz_lo[q], fz_hi[q]) && finite_ff(xr) && finite_ff(yr) &&
-               finite_ff(fz_hi[q]);
+        for (int q = 0; q < NF; ++q) {
+          const ff xr = s.fx[q][tj][ti + 1], yr = s.fy[q][tj + 1][ti];
+          zxy = zxy && same_ff(s.fx[q][tj][ti], xr) && same_ff(s.fy[q][tj][ti], yr) &&
+                finite_ff(xr) && finite_ff(yr);
+        }
+        zxy_prev = zxy;
       }
+#pragma unroll
+      for (int q = 0; q < NF; ++q) zz = zz && same_ff(fz_lo[q], fz_hi[q]) && finite_ff(fz_hi[q]);
+      const bool zero = zxy && zz;
       double un[NF];
       if (__all_sync(__activemask(), zero)) {
 #pragma unroll
@@ -441,7 +462,7 @@ __device__ __forceinline__ void max_to(unsigned long long* dst, double smax) {
 template <int STAGE, bool MC, int TXV, int TY, int MINB>
 __global__ void __launch_bounds__(TXV * TY, MINB)
 k_stageff(double* __restrict__ U, double* __restrict__ U1, Params P, fvd32::Params32 Q32,
-          ConstFF C, double dt, int kchunk, DevCounters* ctr) {
+          ConstFF C, double dt, int kchunk, DevCounters* ctr, bool plane_skip) {
   using S = Shape64<TY, TXV>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmemFF<S>& s = *reinterpret_cast<SmemFF<S>*>(smem_raw);
@@ -452,7 +473,7 @@ k_stageff(double* __restrict__ U, double* __restrict__ U1, Params P, fvd32::Para
   const int k0 = blockIdx.z * kchunk;
   stageff_tile<S, STAGE, MC>(s, U, U1, P, Q32, C, dt, blockIdx.x * TXV, blockIdx.y * TY, k0,
                              min(k0 + kchunk, P.nz), fallbacks, bad, range, evaluated, smax,
-                             smax_f, bad_next, &ctr->smax_next);
+                             smax_f, bad_next, &ctr->smax_next, plane_skip);
   if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
   if (bad) atomicAdd(&ctr->np_step, bad);
   if (range) atomicAdd(&ctr->ff_range, range);
@@ -524,11 +545,12 @@ ConstFF make_const(const Params& P) {
 
 template <int STAGE, bool MC, int TXV, int TY, int MINB>
 cudaError_t launch_mc(const StepBuffers& b, const Params& P, double dt, int kchunk,
-                      cudaStream_t s) {
+                      bool plane_skip, cudaStream_t s) {
   using S = Shape64<TY, TXV>;
   const dim3 grid((P.nx + TXV - 1) / TXV, (P.ny + TY - 1) / TY, (P.nz + kchunk - 1) / kchunk);
   k_stageff<STAGE, MC, TXV, TY, MINB><<<grid, S::kThreads, sizeof(SmemFF<S>), s>>>(
-      b.U, b.U1, P, fv_fp32::make_params32(P, 2.0), make_const(P), dt, kchunk, b.ctr);
+      b.U, b.U1, P, fv_fp32::make_params32(P, 2.0), make_const(P), dt, kchunk, b.ctr,
+      plane_skip);
   return cudaGetLastError();
 }
 
@@ -551,12 +573,12 @@ cudaError_t raise_both() {
 
 template <int TXV, int TY, int MINB>
 cudaError_t launch_shape(int stage, const StepBuffers& b, const Params& P, double dt,
-                         int kchunk, cudaStream_t s) {
+                         int kchunk, bool skip, cudaStream_t s) {
   const bool mc = P.theta == 2.0;
-  if (stage == 1) return mc ? launch_mc<1, true, TXV, TY, MINB>(b, P, dt, kchunk, s)
-                            : launch_mc<1, false, TXV, TY, MINB>(b, P, dt, kchunk, s);
-  return mc ? launch_mc<2, true, TXV, TY, MINB>(b, P, dt, kchunk, s)
-            : launch_mc<2, false, TXV, TY, MINB>(b, P, dt, kchunk, s);
+  if (stage == 1) return mc ? launch_mc<1, true, TXV, TY, MINB>(b, P, dt, kchunk, skip, s)
+                            : launch_mc<1, false, TXV, TY, MINB>(b, P, dt, kchunk, skip, s);
+  return mc ? launch_mc<2, true, TXV, TY, MINB>(b, P, dt, kchunk, skip, s)
+            : launch_mc<2, false, TXV, TY, MINB>(b, P, dt, kchunk, skip, s);
 }
 
 }  // namespace
@@ -577,15 +599,17 @@ cudaError_t prepare_fused() {
 }
 
 cudaError_t launch_fused(int stage, const StepBuffers& b, const Params& P, double dt,
-                         int kchunk, int tile_x, int tile_y, int ctas_per_sm, cudaStream_t s) {
+                         int kchunk, int tile_x, int tile_y, int ctas_per_sm, bool plane_skip,
+                         cudaStream_t s) {
   if (kchunk < 1) kchunk = 1;
   if (!valid_fused_config(tile_x, tile_y, ctas_per_sm)) return cudaErrorInvalidValue;
+  const bool k = plane_skip;
   if (tile_x == 16)
-    return ctas_per_sm >= 2 ? launch_shape<16, 16, 2>(stage, b, P, dt, kchunk, s)
-                            : launch_shape<16, 16, 1>(stage, b, P, dt, kchunk, s);
-  if (tile_y == 16) return launch_shape<32, 16, 1>(stage, b, P, dt, kchunk, s);
-  return ctas_per_sm >= 2 ? launch_shape<32, 8, 2>(stage, b, P, dt, kchunk, s)
-                          : launch_shape<32, 8, 1>(stage, b, P, dt, kchunk, s);
+    return ctas_per_sm >= 2 ? launch_shape<16, 16, 2>(stage, b, P, dt, kchunk, k, s)
+                            : launch_shape<16, 16, 1>(stage, b, P, dt, kchunk, k, s);
+  if (tile_y == 16) return launch_shape<32, 16, 1>(stage, b, P, dt, kchunk, k, s);
+  return ctas_per_sm >= 2 ? launch_shape<32, 8, 2>(stage, b, P, dt, kchunk, k, s)
+                          : launch_shape<32, 8, 1>(stage, b, P, dt, kchunk, k, s);
 }
 
 cudaError_t launch_dt(const double* U, const StepBuffers& b, const Params& P, cudaStream_t s) {

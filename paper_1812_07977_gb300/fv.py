@@ -57,7 +57,7 @@ _lib = None
 
 # fv_tuning_key (include/fv.h) by short name
 TUNING_KEYS = {"kchunk": 0, "vacuum_ratio": 1, "occupancy": 2, "sweep_segments": 3,
-               "tile_y": 4, "fp64_fused": 5, "tile_x": 6}
+               "tile_y": 4, "fp64_fused": 5, "tile_x": 6, "plane_skip": 7}
 
 
 def load_library(path: str | None = None):
