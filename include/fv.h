@@ -476,15 +476,19 @@ FV_API fv_status fv_conserved_sums_noalloc(const double* U, int nx, int ny, int 
  *                        FP64 pipe decides, and the sweeps are faster).
  *                        Both give the same bits.  Not between the two
  *                        substeps.  FP64_FF always runs fused.
- *  FV_TUNE_PLANE_SKIP    FP64_FF and FP32-bulk fused kernels: 1 (default)
- *                        lets a tile skip the x / y slope and face passes of
- *                        a plane (and two of its barriers) when every cell of
- *                        the tile and its two-cell halo equals, bit for bit,
- *                        the cell one plane below: each of those slopes and
- *                        fluxes would keep its previous value, and the
- *                        float-float update's zero-divergence test carries
- *                        over.  0 runs every pass.  The same bits and face
- *                        counts either way.
+ *  FV_TUNE_PLANE_SKIP    FP64_FF's fused kernel at its default tile (16 x 16
+ *                        at 2 CTAs per SM): 1 (default) lets a tile skip
+ *                        the x / y slope and face passes of a plane (and
+ *                        their barriers) when every cell of the tile and its
+ *                        two-cell halo
+ *                        equals, bit for bit, the cell one plane below: each
+ *                        of those slopes and fluxes would keep its previous
+ *                        value, and the float-float update's zero-divergence
+ *                        test carries over.  0 runs the kernel built without
+ *                        the skip, as the other tiles always do.  The same
+ *                        bits and face counts either way.  (FP32-bulk
+ *                        meshes ignore the key: their kernel is built
+ *                        without the skip, which measured slower there.)
  * Errors: INVALID_ARG for an unknown key or a value out of range. */
 typedef enum {
   FV_TUNE_KCHUNK = 0,

@@ -65,7 +65,7 @@ struct fv_mesh_s {
   bool fused64;             // FP64: one fused kernel per substep (else the per-axis sweeps)
   int ff_ctas_per_sm;       // FP64_FF: CTAs per SM its fused kernel is built for (1 or 2)
   int ff_tile_x, ff_tile_y; // FP64_FF: tile of its fused kernel (16 x 16; 32 x 8, 16)
-  bool plane_skip;          // fused FP64_FF / FP32-bulk: skip the passes of unchanged planes
+  bool plane_skip;          // fused FP64_FF: skip the passes of unchanged planes
   bool w_current;           // FP64 sweeps: W holds the primitives of U (from the dt pass)
   bool smax_current;        // fused paths: ctr->smax_next is the CFL maximum of U
   // profiling
@@ -324,8 +324,7 @@ cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
     if (e == cudaSuccess)
       e = timed(m, FV_KERNEL_FUSED, 1, [&] {
         return fv_fp32::launch_stage(stage, m->buf, m->P, dt, m->kchunk, m->vacuum_ratio,
-                                     m->occupancy, m->tile_x, m->tile_y, m->plane_skip,
-                                     m->stream);
+                                     m->occupancy, m->tile_x, m->tile_y, m->stream);
       });
     if (e != cudaSuccess) return e;
     double* dst = stage == 1 ? m->buf.U1 : m->buf.U;

@@ -103,7 +103,10 @@ __device__ __forceinline__ bool same_ff(ff a, ff b) {
 
 __device__ __forceinline__ bool finite_ff(ff a) { return isfinite(a.hi) && isfinite(a.lo); }
 
-template <class S, int STAGE, bool MC>
+// SKIP: a plane whose tile and halo cells all equal the plane below skips its
+// slope and face passes (built for the default 16 x 16 tile at two CTAs per
+// SM, both ways; the other shapes run every pass).
+template <class S, int STAGE, bool MC, bool SKIP>
 __device__ __forceinline__ void stageff_tile(SmemFF<S>& s, double* __restrict__ U,
                                              double* __restrict__ U1, const Params& P,
                                              const fvd32::Params32& Q32, const ConstFF& C,
@@ -113,7 +116,7 @@ __device__ __forceinline__ void stageff_tile(SmemFF<S>& s, double* __restrict__ 
                                              unsigned long long& range_out, unsigned& evaluated,
                                              double& smax, float& smax_f,
                                              unsigned long long& bad_next,
-                                             unsigned long long* gmax, bool plane_skip) {
+                                             unsigned long long* gmax) {
   const double* __restrict__ src = STAGE == 1 ? U : U1;
   constexpr int kThreads = S::kThreads, kHalo = S::kHalo, kHaloPer = S::kHaloPer;
   constexpr int TY = S::TY;
@@ -291,7 +294,9 @@ __device__ __forceinline__ void stageff_tile(SmemFF<S>& s, double* __restrict__ 
     // every cell of the tile and its halo equals the cell a plane below: each
     // slope and x / y face of this plane would keep its value (the passes
     // below would only read flags), so the CTA skips them and their barriers
-    const bool skip = __syncthreads_and(plane_skip && plane_same) != 0;
+    bool skip = false;
+    if (SKIP) skip = __syncthreads_and(plane_same) != 0;
+    else __syncthreads();
     if (skip) {
       fallbacks += __popc(xyfb & counted & ((1u << S::kFacePer) - 1u));
     } else {
@@ -459,10 +464,10 @@ __device__ __forceinline__ void max_to(unsigned long long* dst, double smax) {
 // decisions hold more often next to the waves, and a halo cell serves 1.8
 // columns) or 1 (8 warps, up to 255 registers); 32 x 8 at 2 or 1; and 32 x 16
 // at 1 (16 warps, 128 registers).
-template <int STAGE, bool MC, int TXV, int TY, int MINB>
+template <int STAGE, bool MC, int TXV, int TY, int MINB, bool SKIP>
 __global__ void __launch_bounds__(TXV * TY, MINB)
 k_stageff(double* __restrict__ U, double* __restrict__ U1, Params P, fvd32::Params32 Q32,
-          ConstFF C, double dt, int kchunk, DevCounters* ctr, bool plane_skip) {
+          ConstFF C, double dt, int kchunk, DevCounters* ctr) {
   using S = Shape64<TY, TXV>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmemFF<S>& s = *reinterpret_cast<SmemFF<S>*>(smem_raw);
@@ -471,9 +476,9 @@ k_stageff(double* __restrict__ U, double* __restrict__ U1, Params P, fvd32::Para
   double smax = 0.0;
   float smax_f = 0.0f;
   const int k0 = blockIdx.z * kchunk;
-  stageff_tile<S, STAGE, MC>(s, U, U1, P, Q32, C, dt, blockIdx.x * TXV, blockIdx.y * TY, k0,
+  stageff_tile<S, STAGE, MC, SKIP>(s, U, U1, P, Q32, C, dt, blockIdx.x * TXV, blockIdx.y * TY, k0,
                              min(k0 + kchunk, P.nz), fallbacks, bad, range, evaluated, smax,
-                             smax_f, bad_next, &ctr->smax_next, plane_skip);
+                             smax_f, bad_next, &ctr->smax_next);
   if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
   if (bad) atomicAdd(&ctr->np_step, bad);
   if (range) atomicAdd(&ctr->ff_range, range);
@@ -543,26 +548,46 @@ ConstFF make_const(const Params& P) {
   return C;
 }
 
+// The shape built with the plane skip as well: 16 x 16 at two CTAs per SM
+// (the default).
+template <int TXV, int TY, int MINB>
+constexpr bool kSkipShape = TXV == 16 && TY == 16 && MINB == 2;
+
 template <int STAGE, bool MC, int TXV, int TY, int MINB>
 cudaError_t launch_mc(const StepBuffers& b, const Params& P, double dt, int kchunk,
                       bool plane_skip, cudaStream_t s) {
   using S = Shape64<TY, TXV>;
   const dim3 grid((P.nx + TXV - 1) / TXV, (P.ny + TY - 1) / TY, (P.nz + kchunk - 1) / kchunk);
-  k_stageff<STAGE, MC, TXV, TY, MINB><<<grid, S::kThreads, sizeof(SmemFF<S>), s>>>(
-      b.U, b.U1, P, fv_fp32::make_params32(P, 2.0), make_const(P), dt, kchunk, b.ctr,
-      plane_skip);
+  if constexpr (kSkipShape<TXV, TY, MINB>) {
+    if (plane_skip) {
+      k_stageff<STAGE, MC, TXV, TY, MINB, true><<<grid, S::kThreads, sizeof(SmemFF<S>), s>>>(
+          b.U, b.U1, P, fv_fp32::make_params32(P, 2.0), make_const(P), dt, kchunk, b.ctr);
+      return cudaGetLastError();
+    }
+  }
+  k_stageff<STAGE, MC, TXV, TY, MINB, false><<<grid, S::kThreads, sizeof(SmemFF<S>), s>>>(
+      b.U, b.U1, P, fv_fp32::make_params32(P, 2.0), make_const(P), dt, kchunk, b.ctr);
   return cudaGetLastError();
+}
+
+template <bool MC, int TXV, int TY, int MINB, bool SKIP>
+cudaError_t raise_smem_skip() {
+  const int bytes = (int)sizeof(SmemFF<Shape64<TY, TXV>>);
+  cudaError_t e = cudaFuncSetAttribute(k_stageff<1, MC, TXV, TY, MINB, SKIP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_stageff<2, MC, TXV, TY, MINB, SKIP>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
 }
 
 template <bool MC, int TXV, int TY, int MINB>
 cudaError_t raise_smem() {
-  const int bytes = (int)sizeof(SmemFF<Shape64<TY, TXV>>);
-  cudaError_t e = cudaFuncSetAttribute(k_stageff<1, MC, TXV, TY, MINB>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_stageff<2, MC, TXV, TY, MINB>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  return e;
+  if constexpr (kSkipShape<TXV, TY, MINB>) {
+    const cudaError_t e = raise_smem_skip<MC, TXV, TY, MINB, true>();
+    if (e != cudaSuccess) return e;
+  }
+  return raise_smem_skip<MC, TXV, TY, MINB, false>();
 }
 
 template <int TXV, int TY, int MINB>

@@ -81,8 +81,9 @@ cudaError_t prepare_fused();
 // 32 x 8 at 2 (16 warps per SM, 128 registers) or 1 (8 warps, 255); 32 x 16
 // at 1
 bool valid_fused_config(int tile_x, int tile_y, int ctas_per_sm);
-// plane_skip: a tile whose cells (with the halo) all equal those one plane
-// below skips that plane's slope and face passes (the same bits)
+// plane_skip: at the default tile, a tile whose cells (with the halo) all
+// equal those one plane below skips that plane's slope and face passes (the
+// same bits)
 cudaError_t launch_fused(int stage, const StepBuffers& b, const fvd::Params& P, double dt,
                          int kchunk, int tile_x, int tile_y, int ctas_per_sm, bool plane_skip,
                          cudaStream_t s);
@@ -136,10 +137,9 @@ constexpr int kShapes[8][3] = {{32, 4, 2}, {32, 8, 2}, {32, 8, 3}, {32, 16, 2},
 bool valid_config(int tile_x, int tile_y, int occupancy);
 // Size class of a mesh of nx cells along x: 0 up to 24, 1 up to 64, 2 above.
 inline int batch_class(int nx) { return nx <= 24 ? 0 : nx <= 64 ? 1 : 2; }
-// plane_skip as for the float-float kernel (batches always skip)
 cudaError_t launch_stage(int stage, const StepBuffers& b, const fvd::Params& P, double dt,
                          int kchunk, double vacuum_ratio, int occupancy, int tile_x, int tile_y,
-                         bool plane_skip, cudaStream_t s);
+                         cudaStream_t s);
 cudaError_t launch_reduce_dt(const double* U, const fvd::Params& P, double vacuum_ratio,
                              DevCounters* ctr, cudaStream_t s);
 // Batches: per-mesh CFL maxima of the current states (launch_batch_max), dt =

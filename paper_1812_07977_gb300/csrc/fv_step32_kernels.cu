@@ -159,19 +159,16 @@ __device__ __forceinline__ bool same32(const Prim32& a, const Prim32& b) {
 }
 
 // Stores the plane's primitives of one cell and whether they equal the
-// previous plane's in that slot (`valid`: the slot holds the previous plane);
-// returns that flag.
+// previous plane's in that slot (`valid`: the slot holds the previous plane).
 template <class SM>
-__device__ __forceinline__ bool smem_store_flag(SM& s, int row, int col, const Prim32& w,
+__device__ __forceinline__ void smem_store_flag(SM& s, int row, int col, const Prim32& w,
                                                 bool valid) {
-  const bool same = valid && same32(smem_prim(s, row, col), w);
-  s.same[row][col] = same;
+  s.same[row][col] = valid && same32(smem_prim(s, row, col), w);
   s.w[0][row][col] = w.r;
   s.w[1][row][col] = w.vx;
   s.w[2][row][col] = w.vy;
   s.w[3][row][col] = w.vz;
   s.w[4][row][col] = w.p;
-  return same;
 }
 
 // Folds a thread's CFL speed maximum (a double >= 0, ordered like its bits)
@@ -219,7 +216,7 @@ __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
                                              unsigned long long& bad_out, unsigned& evaluated,
                                              double& smax_next, float& smax_next_f,
                                              unsigned long long& bad_next,
-                                             unsigned long long* gmax, bool plane_skip) {
+                                             unsigned long long* gmax) {
   SpeedCache speed_cache;
   speed_cache.valid = false;
   const double* __restrict__ src = STAGE == 1 ? U : U1;
@@ -382,7 +379,7 @@ __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
     // (b) the plane's primitives into shared memory, each with a flag: equal
     // to the previous plane's in its slot (never on a chunk's first plane,
     // where the slot holds another tile's data)
-    bool plane_same = smem_store_flag(s, tj + 2, ti + 2, w0, k > k0);
+    smem_store_flag(s, tj + 2, ti + 2, w0, k > k0);
 #pragma unroll
     for (int e = 0; e < kHaloPer; ++e) {
       const int h = tid + e * kThreads;
@@ -401,27 +398,19 @@ __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
         if (all_eq)
           s.same[hrow[e] + 2][hcol[e] + 2] = 1;
         else
-          plane_same = smem_store_flag(s, hrow[e] + 2, hcol[e] + 2, prim_from_state(uh, Q),
-                                       k > k0) && plane_same;
+          smem_store_flag(s, hrow[e] + 2, hcol[e] + 2, prim_from_state(uh, Q), k > k0);
       }
 #else
       if (h < kHalo) {
         double uh[NF];
 #pragma unroll
         for (int q = 0; q < NF; ++q) uh[q] = s.halo[slot][q][h];
-        plane_same = smem_store_flag(s, hrow[e] + 2, hcol[e] + 2, prim_from_state(uh, Q),
-                                     k > k0) && plane_same;
+        smem_store_flag(s, hrow[e] + 2, hcol[e] + 2, prim_from_state(uh, Q), k > k0);
       }
 #endif
     }
     if (kLateStage) stage_in(k + 1);   // into the other slot, now compared
-    // every cell of the tile and its halo equals the cell a plane below: each
-    // x and y face of this plane would keep its flux (the passes below would
-    // only read flags), so the CTA skips them and a barrier
-    const bool skip = __syncthreads_and(plane_skip && plane_same) != 0;
-    if (skip) {
-      fallbacks += __popc(xyfb & counted);
-    } else {
+    __syncthreads();
     // (c) x faces: face fi (between columns fi-1 and fi) of row r.  A face
     // whose four cells all equal the previous plane's has that plane's
     // inputs, so its flux (still in s.fx) and fallback stand.
@@ -465,7 +454,6 @@ __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
       fallbacks += fb & (counted >> pass);
     }
     __syncthreads();
-    }
     // (e) update of cell (i, j, k): FP32 divergence, FP64 RK combine
     if (owner) {
       double un[NF];
@@ -499,7 +487,7 @@ __device__ __forceinline__ void stage32_tile(Smem<S>& s, double* __restrict__ U,
 template <int STAGE, int TX, int TY, int MINB, bool MC>
 __global__ void __launch_bounds__(TX * TY, MINB)
 k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params32 Q, float dt,
-          int kchunk, DevCounters* ctr, bool plane_skip) {
+          int kchunk, DevCounters* ctr) {
   using S = Shape<TX, TY>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<S>& s = *reinterpret_cast<Smem<S>*>(smem_raw);
@@ -510,8 +498,7 @@ k_stage32(double* __restrict__ U, double* __restrict__ U1, fvd::Params P, Params
   const int k0 = blockIdx.z * kchunk;
   stage32_tile<S, STAGE, MC, STAGE == 2>(s, U, U1, P, Q, dt, blockIdx.x * TX, blockIdx.y * TY,
                                          k0, min(k0 + kchunk, P.nz), fallbacks, bad, evaluated,
-                                         smax_next, smax_next_f, bad_next, &ctr->smax_next,
-                                         plane_skip);
+                                         smax_next, smax_next_f, bad_next, &ctr->smax_next);
   if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
   if (bad) atomicAdd(&ctr->np_step, bad);
   warp_count(&ctr->faces, evaluated);
@@ -551,8 +538,7 @@ k_stage32_batch(double* __restrict__ U, double* __restrict__ U1, BatchMesh* __re
     stage32_tile<S, STAGE, MC, STAGE == 2>(s, U + m.offset, U1 + m.offset, m.P, m.Q,
                                            (float)m.dt, w.y * TX, w.z * TY, k0,
                                            min(k0 + kchunk, m.P.nz), fallbacks, bad, evaluated,
-                                           smax_next, smax_next_f, bad_next, &m.smax_bits,
-                                           true);
+                                           smax_next, smax_next_f, bad_next, &m.smax_bits);
     if (STAGE == 2) max_speed_to(&m.smax_bits, smax_next);
   }
   if (fallbacks) atomicAdd(&ctr->fallback, (unsigned long long)fallbacks);
@@ -731,14 +717,13 @@ struct LaunchMesh {
   Params32 Q;
   float dt;
   int kchunk;
-  bool plane_skip;
   cudaStream_t s;
   template <int STAGE, int TX, int TY, int MINB, bool MC>
   cudaError_t run() {
     using S = Shape<TX, TY>;
     const dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + kchunk - 1) / kchunk);
     k_stage32<STAGE, TX, TY, MINB, MC><<<grid, S::kThreads, sizeof(Smem<S>), s>>>(
-        b.U, b.U1, P, Q, dt, kchunk, b.ctr, plane_skip);
+        b.U, b.U1, P, Q, dt, kchunk, b.ctr);
     return cudaGetLastError();
   }
 };
@@ -787,9 +772,8 @@ bool valid_config(int tile_x, int tile_y, int occupancy) {
 
 cudaError_t launch_stage(int stage, const StepBuffers& b, const fvd::Params& P, double dt,
                          int kchunk, double vacuum_ratio, int occupancy, int tile_x, int tile_y,
-                         bool plane_skip, cudaStream_t s) {
-  LaunchMesh fn{b, P, make_params32(P, vacuum_ratio), (float)dt, kchunk < 1 ? 1 : kchunk,
-                plane_skip, s};
+                         cudaStream_t s) {
+  LaunchMesh fn{b, P, make_params32(P, vacuum_ratio), (float)dt, kchunk < 1 ? 1 : kchunk, s};
   return dispatch(stage, tile_x, tile_y, occupancy, fn.Q.theta == 2.0f, fn);
 }
 

@@ -376,35 +376,3 @@ def test_tile_shape_changes_must_stay_built():
         m.set_tuning("tile_x", 48)
     m.close()
 
-
-@pytest.mark.parametrize("state", ["oblique", "z_invariant", "planar_x"])
-def test_fp32_plane_skip_same_bits(state):
-    """Skipping the x / y face passes of tile planes equal to the plane
-    below changes nothing: the same state bits, dt, counters and face counts
-    as running every pass (ragged mesh, z chunks of 11 planes; a z-invariant
-    state skips every plane after a chunk's first with non-zero x / y flux
-    differences)."""
-    n = (45, 29, 30)
-    if state == "oblique":
-        U0, bc = problems.riemann_oblique(*n), (OUT, OUT, OUT)
-    elif state == "z_invariant":
-        U2 = problems.random_smooth_periodic(n[0], n[1], 1, seed=5)
-        U0, bc = np.ascontiguousarray(np.repeat(U2, n[2], axis=1)), (PER, PER, PER)
-    else:
-        U0, bc = problems.riemann_planar(*n), (OUT, OUT, OUT)
-    out = []
-    for skip in (1, 0):
-        m = _mesh32(n, bc)
-        m.set_tuning("kchunk", 11)
-        m.set_tuning("plane_skip", skip)
-        m.set_state(U0)
-        dts = []
-        for _ in range(4):
-            dts.append(m.reduce_dt(0.4))
-            m.step(dts[-1])
-        out.append((dts, m.get_state().cpu().numpy(), m.counters(), m.face_counts()))
-        m.close()
-    assert out[0][0] == out[1][0]
-    assert np.array_equal(out[0][1].view(np.uint64), out[1][1].view(np.uint64))
-    assert out[0][2] == out[1][2]
-    assert out[0][3] == out[1][3]
