@@ -35,7 +35,10 @@ namespace {
 
 constexpr int kPrefetch = 2;   // planes ahead for the stage-2 RK operand prefetch
 
-template <class S>
+// STAGE 1 leaves out `last` (stage 2's CFL cache): 10 KB less shared memory
+// per CTA, so that more of the multiprocessor's L1 stays free for the
+// register spills.
+template <class S, int STAGE>
 struct SmemFF {
   double col[2][NF][S::kThreads];   // staged input: the column cell of plane t+2
   double halo[2][NF][S::kHalo];     // staged input: the halo cells of plane t
@@ -45,7 +48,7 @@ struct SmemFF {
   ff fx[NF][S::TY][S::TX + 1];         // x face fluxes
   ff fy[NF][S::TY + 1][S::TX];         // y face fluxes
   unsigned char same[S::PY][S::PX]; // the cell equals (bits) the cell a plane below
-  double last[NF][S::kThreads];     // stage 2: the state of the column's last cell written
+  double last[NF][STAGE == 2 ? S::kThreads : 1];   // stage 2: the column's last cell written
 };
 
 struct ConstFF {
@@ -107,7 +110,7 @@ __device__ __forceinline__ bool finite_ff(ff a) { return isfinite(a.hi) && isfin
 // slope and face passes (built for the default 16 x 16 tile at two CTAs per
 // SM, both ways; the other shapes run every pass).
 template <class S, int STAGE, bool MC, bool SKIP>
-__device__ __forceinline__ void stageff_tile(SmemFF<S>& s, double* __restrict__ U,
+__device__ __forceinline__ void stageff_tile(SmemFF<S, STAGE>& s, double* __restrict__ U,
                                              double* __restrict__ U1, const Params& P,
                                              const fvd32::Params32& Q32, const ConstFF& C,
                                              double dt, int i0, int j0, int k0, int k1,
@@ -470,7 +473,7 @@ k_stageff(double* __restrict__ U, double* __restrict__ U1, Params P, fvd32::Para
           ConstFF C, double dt, int kchunk, DevCounters* ctr) {
   using S = Shape64<TY, TXV>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  SmemFF<S>& s = *reinterpret_cast<SmemFF<S>*>(smem_raw);
+  SmemFF<S, STAGE>& s = *reinterpret_cast<SmemFF<S, STAGE>*>(smem_raw);
   unsigned fallbacks = 0, evaluated = 0;
   unsigned long long bad = 0, range = 0, bad_next = 0;
   double smax = 0.0;
@@ -558,26 +561,29 @@ cudaError_t launch_mc(const StepBuffers& b, const Params& P, double dt, int kchu
                       bool plane_skip, cudaStream_t s) {
   using S = Shape64<TY, TXV>;
   const dim3 grid((P.nx + TXV - 1) / TXV, (P.ny + TY - 1) / TY, (P.nz + kchunk - 1) / kchunk);
+  constexpr size_t bytes = sizeof(SmemFF<S, STAGE>);
   if constexpr (kSkipShape<TXV, TY, MINB>) {
     if (plane_skip) {
-      k_stageff<STAGE, MC, TXV, TY, MINB, true><<<grid, S::kThreads, sizeof(SmemFF<S>), s>>>(
+      k_stageff<STAGE, MC, TXV, TY, MINB, true><<<grid, S::kThreads, bytes, s>>>(
           b.U, b.U1, P, fv_fp32::make_params32(P, 2.0), make_const(P), dt, kchunk, b.ctr);
       return cudaGetLastError();
     }
   }
-  k_stageff<STAGE, MC, TXV, TY, MINB, false><<<grid, S::kThreads, sizeof(SmemFF<S>), s>>>(
+  k_stageff<STAGE, MC, TXV, TY, MINB, false><<<grid, S::kThreads, bytes, s>>>(
       b.U, b.U1, P, fv_fp32::make_params32(P, 2.0), make_const(P), dt, kchunk, b.ctr);
   return cudaGetLastError();
 }
 
 template <bool MC, int TXV, int TY, int MINB, bool SKIP>
 cudaError_t raise_smem_skip() {
-  const int bytes = (int)sizeof(SmemFF<Shape64<TY, TXV>>);
+  using S = Shape64<TY, TXV>;
   cudaError_t e = cudaFuncSetAttribute(k_stageff<1, MC, TXV, TY, MINB, SKIP>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(SmemFF<S, 1>));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_stageff<2, MC, TXV, TY, MINB, SKIP>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SmemFF<S, 2>));
   return e;
 }
 
