@@ -465,9 +465,14 @@ fv_status fv_batch_autotune(fv_batch_t b, double cfl, int* kchunk_out, int* occu
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  // times three whole steps (after one to warm up) with the current tuning
+  // times three whole steps (after one to warm up) with the current tuning,
+  // each candidate from the snapshot: stepping on from the previous
+  // candidate's state would time later candidates on a more evolved (and
+  // costlier) state and bias the search toward the shapes tried first
   auto time_step = [&](double& ms_out) -> cudaError_t {
-    cudaError_t r = launch_step(b, cfl);
+    cudaError_t r = cudaMemcpyAsync(b->dev.U, b->backup, sb, cudaMemcpyDeviceToDevice, b->stream);
+    b->smax_current = false;
+    if (r == cudaSuccess) r = launch_step(b, cfl);
     cudaEventRecord(e0, b->stream);
     for (int i = 0; i < 3 && r == cudaSuccess; ++i) r = launch_step(b, cfl);
     cudaEventRecord(e1, b->stream);
