@@ -480,15 +480,18 @@ FV_API fv_status fv_conserved_sums_noalloc(const double* U, int nx, int ny, int 
  *                        at 2 CTAs per SM): 1 (default) lets a tile skip
  *                        the x / y slope and face passes of a plane (and
  *                        their barriers) when every cell of the tile and its
- *                        two-cell halo
- *                        equals, bit for bit, the cell one plane below: each
- *                        of those slopes and fluxes would keep its previous
- *                        value, and the float-float update's zero-divergence
- *                        test carries over.  0 runs the kernel built without
- *                        the skip, as the other tiles always do.  The same
- *                        bits and face counts either way.  (FP32-bulk
- *                        meshes ignore the key: their kernel is built
- *                        without the skip, which measured slower there.)
+ *                        two-cell halo equals, bit for bit, the cell one
+ *                        plane below: each of those slopes and fluxes would
+ *                        keep its previous value, and the float-float
+ *                        update's zero-divergence test carries over.  After
+ *                        an fv_reduce_dt that finds 90% or more of the faces
+ *                        defined since the previous one evaluated (no plane
+ *                        repeats), the next steps run the kernel built
+ *                        without the skip.  0 always runs that kernel, as
+ *                        the other tiles do.  The same bits and face counts
+ *                        either way.  (FP32-bulk meshes ignore the key:
+ *                        their kernel is built without the skip, which
+ *                        measured slower there.)
  * Errors: INVALID_ARG for an unknown key or a value out of range. */
 typedef enum {
   FV_TUNE_KCHUNK = 0,

@@ -66,6 +66,9 @@ struct fv_mesh_s {
   int ff_ctas_per_sm;       // FP64_FF: CTAs per SM its fused kernel is built for (1 or 2)
   int ff_tile_x, ff_tile_y; // FP64_FF: tile of its fused kernel (16 x 16; 32 x 8, 16)
   bool plane_skip;          // fused FP64_FF: skip the passes of unchanged planes
+  bool ff_dense;            // FP64_FF: the last step evaluated >= 90% of its faces
+  long long faces_seen;     // evaluated / defined faces at the last fv_reduce_dt
+  long long defined_seen;
   bool w_current;           // FP64 sweeps: W holds the primitives of U (from the dt pass)
   bool smax_current;        // fused paths: ctr->smax_next is the CFL maximum of U
   // profiling
@@ -303,8 +306,8 @@ cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
                                                                          m->ff_tile_y,
                                                                          m->ff_ctas_per_sm),
                                           m->ff_tile_x,
-                                          m->ff_tile_y, m->ff_ctas_per_sm, m->plane_skip,
-                                          m->stream);
+                                          m->ff_tile_y, m->ff_ctas_per_sm,
+                                          m->plane_skip && !m->ff_dense, m->stream);
         return fma ? fv_fp64_fma::launch_fused(stage, m->buf, m->P, dt, m->kchunk, m->stream)
                    : fv_fp64_exact::launch_fused(stage, m->buf, m->P, dt, m->kchunk,
                                                  m->stream);
@@ -393,6 +396,8 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   m->ff_tile_x = 16;   // 16 x 16 at 2 CTAs per SM (see fv_fused_ff_kernels.cu)
   m->ff_tile_y = 16;
   m->plane_skip = true;
+  m->ff_dense = false;
+  m->faces_seen = m->defined_seen = 0;
   m->w_current = false;
   m->smax_current = false;
   for (int c = 0; c < FV_KERNEL_NCLASS; ++c) m->launches[c] = 0;
@@ -488,6 +493,8 @@ fv_status fv_set_state(fv_mesh_t m, const double* U, int on_device) {
   if ((e = cudaMemsetAsync(m->buf.ctr, 0, sizeof(DevCounters), m->stream)) != cudaSuccess)
     return cuda_fail(e, "clearing counters");
   m->faces_defined = 0;
+  m->faces_seen = m->defined_seen = 0;
+  m->ff_dense = false;
   m->stage_pending = 0;
   m->w_current = false;
   m->smax_current = false;
@@ -566,6 +573,16 @@ fv_status fv_reduce_dt(fv_mesh_t m, double cfl, double* dt_out) {
     m->w_current = !fused;
   }
   if ((st = read_counters(m)) != FV_OK) return st;
+  if (ffp) {
+    // where the steps since the last read evaluated nearly every face, no tile
+    // plane repeats and the plane skip only costs its flags: the next steps
+    // run the float-float kernel built without it (the same bits)
+    const long long ev = (long long)m->host_ctr->faces - m->faces_seen;
+    const long long de = m->faces_defined - m->defined_seen;
+    if (de > 0 && ev >= 0) m->ff_dense = 10 * ev >= 9 * de;
+    m->faces_seen = (long long)m->host_ctr->faces;
+    m->defined_seen = m->faces_defined;
+  }
   double smax;
   std::memcpy(&smax, cached ? &m->host_ctr->smax_next : &m->host_ctr->smax_bits, sizeof smax);
   *dt_out = cfl / smax;

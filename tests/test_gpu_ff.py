@@ -261,19 +261,23 @@ def _runs_with_plane_skip(make_mesh, n, U0, bc, steps):
     return out
 
 
-@pytest.mark.parametrize("state", ["oblique", "z_invariant", "planar_x"])
+@pytest.mark.parametrize("state", ["oblique", "z_invariant", "planar_x", "smooth"])
 def test_ff_plane_skip_same_bits(state):
     """Skipping the slope and face passes of tile planes equal to the plane
     below changes nothing: the same state bits, dt, counters and face counts
     as running every pass, on a ragged mesh with short z chunks (transitions
     between skipped and evaluated planes: the oblique problem; every plane
     after a chunk's first skipped with non-zero x / y divergence: a
-    z-invariant state; a planar tube along x)."""
+    z-invariant state; a planar tube along x; a smooth state, where every
+    face is evaluated and the steps after the first switch to the kernel
+    built without the skip)."""
     n = (45, 29, 30)
     if state == "oblique":
         U0, bc = problems.riemann_oblique(*n), (OUT, OUT, OUT)
     elif state == "z_invariant":
         U0, bc = _z_invariant(n, 5), (PER, PER, PER)
+    elif state == "smooth":
+        U0, bc = problems.random_smooth_periodic(*n, seed=8), (PER, PER, PER)
     else:
         U0, bc = problems.riemann_planar(*n), (OUT, OUT, OUT)
     out = _runs_with_plane_skip(_short_chunks(_mesh), n, U0, bc, 4)
