@@ -342,6 +342,35 @@ __host__ __device__ __forceinline__ long long ring_cells(const Params& P) {
   return 4 * Y * X + 4 * (long long)P.nz * X + 4 * (long long)P.nz * P.ny;
 }
 
+// The (i, j, k) of ring cell t, in the integer type I (32-bit unsigned
+// division is a short sequence, 64-bit a long emulated one).
+template <class I>
+__device__ __forceinline__ void ghost_ijk(const Params& P, I t, int& i, int& j, int& k) {
+  const I X = (I)P.nx + 4, Y = (I)P.ny + 4, nz = (I)P.nz, ny = (I)P.ny;
+  const I nz_slab = 4 * Y * X;
+  const I ny_slab = 4 * nz * X;
+  if (t < nz_slab) {
+    const I s = t / (Y * X), r = t - s * (Y * X);
+    k = s < 2 ? (int)s - 2 : P.nz + (int)s - 2;
+    j = (int)(r / X) - 2;
+    i = (int)(r % X) - 2;
+  } else if (t < nz_slab + ny_slab) {
+    const I u = t - nz_slab;
+    const I kk = u / (4 * X), r = u - kk * (4 * X);
+    const int s = (int)(r / X);
+    k = (int)kk;
+    j = s < 2 ? s - 2 : P.ny + s - 2;
+    i = (int)(r % X) - 2;
+  } else {
+    const I u = t - nz_slab - ny_slab;
+    const I row = u / 4;
+    const int s = (int)(u - row * 4);
+    k = (int)(row / ny);
+    j = (int)(row % ny);
+    i = s < 2 ? s - 2 : P.nx + s - 2;
+  }
+}
+
 // Ghost fill of ring cell t (0 <= t < ring_cells) of all five fields.  The
 // axis-by-axis fill (x, then y, then z, each over the full ghosted extent of
 // the other axes) leaves every ghost cell equal to the interior cell
@@ -351,30 +380,11 @@ __host__ __device__ __forceinline__ long long ring_cells(const Params& P) {
 // interior rows.
 __device__ __forceinline__ void fill_ghost_cell(double* __restrict__ U, const Params& P,
                                                 long long t) {
-  const long long X = P.nx + 4, Y = P.ny + 4;
-  const long long nz_slab = 4 * Y * X;
-  const long long ny_slab = 4 * (long long)P.nz * X;
   int i, j, k;
-  if (t < nz_slab) {
-    const long long s = t / (Y * X), r = t - s * (Y * X);
-    k = s < 2 ? (int)s - 2 : P.nz + (int)s - 2;
-    j = (int)(r / X) - 2;
-    i = (int)(r % X) - 2;
-  } else if (t < nz_slab + ny_slab) {
-    const long long u = t - nz_slab;
-    const long long kk = u / (4 * X), r = u - kk * (4 * X);
-    const int s = (int)(r / X);
-    k = (int)kk;
-    j = s < 2 ? s - 2 : P.ny + s - 2;
-    i = (int)(r % X) - 2;
-  } else {
-    const long long u = t - nz_slab - ny_slab;
-    const long long row = u / 4;
-    const int s = (int)(u - row * 4);
-    k = (int)(row / P.ny);
-    j = (int)(row % P.ny);
-    i = s < 2 ? s - 2 : P.nx + s - 2;
-  }
+  // every mesh that fits in memory has far fewer than 2^31 ring cells; the
+  // 64-bit form stays for any other
+  if (ring_cells(P) < (1LL << 31)) ghost_ijk<unsigned>(P, (unsigned)t, i, j, k);
+  else ghost_ijk<long long>(P, t, i, j, k);
   const int si = ghost_source(i, P.nx, P.bc[0]);
   const int sj = ghost_source(j, P.ny, P.bc[1]);
   const int sk = ghost_source(k, P.nz, P.bc[2]);
