@@ -435,7 +435,10 @@ FV_API fv_status fv_conserved_sums_noalloc(const double* U, int nx, int ny, int 
  *                        nz < 64).  FP64_FF meshes by default pick it per
  *                        launch shape: the chunk (>= 16 planes, or nz) that
  *                        minimises rounds of resident CTAs x (chunk + 4)
- *                        (37 at 256^3); setting the key fixes it
+ *                        (37 at 256^3), or one chunk of nz planes after an
+ *                        fv_reduce_dt that finds under 15% of the faces
+ *                        defined since the previous one evaluated; setting
+ *                        the key fixes it
  *  FV_TUNE_VACUUM_RATIO  FP32-bulk: recover the pressure in FP64 where the
  *                        kinetic energy exceeds this fraction of E (default
  *                        0.99; a value > 1 turns the recovery off)

@@ -67,6 +67,7 @@ struct fv_mesh_s {
   int ff_tile_x, ff_tile_y; // FP64_FF: tile of its fused kernel (16 x 16; 32 x 8, 16)
   bool plane_skip;          // fused FP64_FF: skip the passes of unchanged planes
   bool ff_dense;            // FP64_FF: the last step evaluated >= 90% of its faces
+  bool ff_sparse;           // FP64_FF: the last step evaluated < 15% of its faces
   long long faces_seen;     // evaluated / defined faces at the last fv_reduce_dt
   long long defined_seen;
   bool w_current;           // FP64 sweeps: W holds the primitives of U (from the dt pass)
@@ -302,9 +303,10 @@ cudaError_t launch_substep(fv_mesh_t m, int stage, double dt) {
         if (ff)
           return fv_fp64_ff::launch_fused(stage, m->buf, m->P, dt,
                                           m->kchunk > 0 ? m->kchunk
-                                                        : ff_auto_kchunk(m->P, m->ff_tile_x,
-                                                                         m->ff_tile_y,
-                                                                         m->ff_ctas_per_sm),
+                                          : m->ff_sparse ? m->P.nz
+                                                         : ff_auto_kchunk(m->P, m->ff_tile_x,
+                                                                          m->ff_tile_y,
+                                                                          m->ff_ctas_per_sm),
                                           m->ff_tile_x,
                                           m->ff_tile_y, m->ff_ctas_per_sm,
                                           m->plane_skip && !m->ff_dense, m->stream);
@@ -397,6 +399,7 @@ fv_status fv_create_mesh(const fv_mesh_desc* desc, void* cuda_stream, fv_mesh_t*
   m->ff_tile_y = 16;
   m->plane_skip = true;
   m->ff_dense = false;
+  m->ff_sparse = false;
   m->faces_seen = m->defined_seen = 0;
   m->w_current = false;
   m->smax_current = false;
@@ -495,6 +498,7 @@ fv_status fv_set_state(fv_mesh_t m, const double* U, int on_device) {
   m->faces_defined = 0;
   m->faces_seen = m->defined_seen = 0;
   m->ff_dense = false;
+  m->ff_sparse = false;
   m->stage_pending = 0;
   m->w_current = false;
   m->smax_current = false;
@@ -579,7 +583,13 @@ fv_status fv_reduce_dt(fv_mesh_t m, double cfl, double* dt_out) {
     // run the float-float kernel built without it (the same bits)
     const long long ev = (long long)m->host_ctr->faces - m->faces_seen;
     const long long de = m->faces_defined - m->defined_seen;
-    if (de > 0 && ev >= 0) m->ff_dense = 10 * ev >= 9 * de;
+    if (de > 0 && ev >= 0) {
+      m->ff_dense = 10 * ev >= 9 * de;
+      // few faces evaluated: most tile planes repeat the plane below, and
+      // one z chunk per tile column (no chunk starts past the first) beats
+      // shorter chunks' balance
+      m->ff_sparse = 20 * ev < 3 * de;
+    }
     m->faces_seen = (long long)m->host_ctr->faces;
     m->defined_seen = m->faces_defined;
   }
