@@ -83,8 +83,10 @@ FF_OPS_CELL = 380
 FUSED_TRAFFIC = {
     "fp32_bulk": (1.736e9, "ncu capture 2026-12-04 of k_stage32<., 16, 8, 4, 1> (equal-state "
                            "skip): 1.418 GB (stage 1) and 2.054 GB (stage 2)"),
-    "fp64_ff": (1.959e9, "ncu capture 2026-12-04 of k_stageff<., MC, 16, 16, 2, plane skip> "
-                         "with 37-plane chunks: 1.611 GB (stage 1) and 2.307 GB (stage 2)"),
+    "fp64_ff": (2.011e9, "ncu capture 2026-12-04 of k_stageff<., MC, 16, 16, 2, plane skip> "
+                         "with one z chunk per column (the early steps' launch shape): 1.659 GB "
+                         "(stage 1) and 2.364 GB (stage 2); with 37-plane chunks (later steps) "
+                         "1.611 and 2.307 GB"),
     "fp64_fma": None,
     "fp64": None,
 }
